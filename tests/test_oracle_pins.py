@@ -1,0 +1,317 @@
+"""Pins for the CPU oracle against facts the paper and mathematics fix.
+
+Each group below targets a plausible oracle mistake: a dropped term or transposed
+operand (dense brute force on a non-symmetric integer matrix), a wrong sign or scale
+(closed-form eigenpairs), an off-by-one power (permutation powers), a wrong level rule
+(Fig. 1, grid closed forms, symmetrisation), a wrong traversal (Fig. 2).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from conftest import read_golden
+
+
+# ----------------------------------------------------------------------------- SpMV / MPK
+def _dense_int_powers(A, x, p):
+    """Exact A^k x with Python integers (values and x are integers)."""
+    D = [[0] * A.n for _ in range(A.n)]
+    for i in range(A.n):
+        for e in range(A.row_ptr[i], A.row_ptr[i + 1]):
+            D[i][A.col[e]] += int(A.val[e])
+    out = [list(map(int, x))]
+    for _ in range(p):
+        prev = out[-1]
+        out.append([sum(D[i][j] * prev[j] for j in range(A.n)) for i in range(A.n)])
+    return out
+
+
+@pytest.mark.parametrize("n,per_row,p,stream", [(1, 1, 3, 11), (7, 3, 5, 12), (40, 4, 6, 13), (64, 2, 8, 14)])
+def test_mpk_dense_bruteforce_exact(n, per_row, p, stream):
+    A = gen.random_int_matrix(n, per_row, stream)
+    D = A.to_dense()
+    assert n == 1 or not np.array_equal(D, D.T)  # non-symmetric: catches A vs A^T
+    x = (gen.splitmix64(gen.derive_seed(stream + 100), n) % np.uint64(7)).astype(np.int64) - 3
+    Y = oracle.mpk(A, x.astype(np.float64), p)
+    ref = _dense_int_powers(A, x, p)
+    for k in range(p + 1):
+        assert np.array_equal(Y[k, :, 0], np.array(ref[k], dtype=np.float64)), k
+
+
+def test_mpk_multiple_rhs_columns_independent():
+    A = gen.random_int_matrix(30, 3, 21)
+    X = (gen.splitmix64(gen.derive_seed(22), 30 * 3) % np.uint64(5)).astype(np.float64).reshape(30, 3) - 2
+    Y = oracle.mpk(A, X, 4)
+    for r in range(3):
+        ref = _dense_int_powers(A, X[:, r].astype(np.int64), 4)
+        for k in range(5):
+            assert np.array_equal(Y[k, :, r], np.array(ref[k], dtype=np.float64))
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("n,j", [(50, 50), (50, 48), (200, 199), (201, 195)])
+def test_mpk_eigenpair_1d(n, j):
+    # tridiag(-1,2,-1): lambda_j = 2 - 2 cos(j pi/(n+1)), v_j(i) = sin(i j pi/(n+1)), i=1..n.
+    # Modes at the top of the spectrum: rounding error in other eigen-directions then grows
+    # no faster than the signal, so 1e-13 holds for every power.
+    A = gen.laplacian_1d(n)
+    th = j * np.pi / (n + 1)
+    v = np.sin(np.arange(1, n + 1) * th)
+    lam = 2 - 2 * np.cos(th)
+    Y = oracle.mpk(A, v, 8)
+    for k in range(9):
+        assert _rel(Y[k, :, 0], lam**k * v) < 1e-13, k
+
+
+def test_mpk_eigenpair_2d_3d():
+    nx, ny = 13, 9
+    A = gen.laplacian_2d(nx, ny)
+    a, b = (nx - 1) * np.pi / (nx + 1), ny * np.pi / (ny + 1)
+    X, Yc = np.meshgrid(np.arange(1, nx + 1), np.arange(1, ny + 1), indexing="xy")
+    v = (np.sin(X * a) * np.sin(Yc * b)).ravel()  # id = x + nx*y
+    lam = 4 - 2 * np.cos(a) - 2 * np.cos(b)
+    Y = oracle.mpk(A, v, 6)
+    for k in range(7):
+        assert _rel(Y[k, :, 0], lam**k * v) < 1e-13
+
+    nx, ny, nz = 6, 5, 4
+    A = gen.laplacian_3d(nx, ny, nz)
+    t = [nx * np.pi / (nx + 1), (ny - 1) * np.pi / (ny + 1), nz * np.pi / (nz + 1)]
+    z, y, x = np.meshgrid(np.arange(1, nz + 1), np.arange(1, ny + 1), np.arange(1, nx + 1), indexing="ij")
+    v = (np.sin(x * t[0]) * np.sin(y * t[1]) * np.sin(z * t[2])).ravel()
+    lam = 6 - 2 * sum(np.cos(tt) for tt in t)
+    Y = oracle.mpk(A, v, 8)
+    for k in range(9):
+        assert _rel(Y[k, :, 0], lam**k * v) < 1e-13
+
+
+def test_mpk_row_stochastic_exact():
+    A = gen.row_stochastic(300, 3, stream=31)
+    Y = oracle.mpk(A, np.ones(300), 12)
+    assert np.all(Y == 1.0)
+
+
+def test_mpk_permutation_powers_exact():
+    n = 257
+    P, pi = gen.permutation_matrix(n, stream=32)
+    x = gen.uniform(gen.derive_seed(33), n)
+    Y = oracle.mpk(P, x, 7)
+    idx = np.arange(n)
+    for k in range(8):
+        assert np.array_equal(Y[k, :, 0], x[idx])
+        idx = idx[pi]  # (P^{k+1} x)[i] = x[pi^{k+1}(i)]
+
+
+def test_mpk_rounding_bound_vs_longdouble():
+    A = gen.laplacian_2d(20, 17)
+    x = gen.uniform(gen.derive_seed(34), A.n)
+    Y = oracle.mpk(A, x, 8)[:, :, 0]
+    Z = oracle.mpk_longdouble(A, x, 8)
+    for k in range(9):
+        assert _rel(Y[k], Z[k]) < 1e-14
+
+
+def test_mpk_stored_order_single_rounding():
+    # y = 1e16*1 + 1*1 - 1e16*1 in stored order: the second term is lost to rounding;
+    # a different order (or exact arithmetic) would return 1.
+    A3 = gen.CSR([0, 3, 4, 5], [0, 1, 2, 1, 2], np.array([1e16, 1.0, -1e16, 1.0, 1.0]))
+    Y = oracle.mpk(A3, np.array([1.0, 1.0, 1.0]), 1)
+    assert Y[1, 0, 0] == 0.0
+
+
+# ----------------------------------------------------------------------------- levels
+def _fig1_matrix():
+    edges = read_golden("fig1_graph.txt")
+    n = 20
+    r = [i for i in range(n)] + [u for u, v in edges] + [v for u, v in edges]
+    c = [i for i in range(n)] + [v for u, v in edges] + [u for u, v in edges]
+    return gen.from_coo(n, r, c, np.ones(len(r)) * 2.0)
+
+
+def test_levels_fig1_exact():
+    A = _fig1_matrix()
+    level_of, perm, iperm, level_ptr = oracle.levels(A, 0)
+    assert np.diff(level_ptr).tolist() == [1, 1, 2, 3, 3, 3, 3, 2, 1, 1]
+    golden = dict((o, nl) for o, nl in read_golden("fig1_perm.txt"))
+    assert [int(iperm[o]) for o in range(20)] == [golden[o] for o in range(20)]
+    assert np.array_equal(perm[iperm], np.arange(20))
+
+
+@pytest.mark.parametrize("dims", [(5, 4, 3), (8, 8, 8), (1, 9, 2)])
+def test_levels_grid_closed_form(dims):
+    nx, ny, nz = dims
+    A = gen.laplacian_3d(nx, ny, nz)
+    level_of, perm, iperm, level_ptr = oracle.levels(A, 0)
+    i = np.arange(A.n)
+    assert np.array_equal(level_of, i % nx + (i // nx) % ny + i // (nx * ny))
+    # inside a level, ascending original index
+    for l in range(level_ptr.size - 1):
+        seg = perm[level_ptr[l]:level_ptr[l + 1]]
+        assert np.all(np.diff(seg) > 0)
+
+
+def test_levels_chain_is_index():
+    A = gen.laplacian_1d(33)
+    level_of, perm, _, level_ptr = oracle.levels(A, 0)
+    assert np.array_equal(level_of, np.arange(33))
+    level_of, _, _, _ = oracle.levels(A, 10)
+    assert np.array_equal(level_of, np.abs(np.arange(33) - 10))
+
+
+def test_levels_symmetrised_pattern():
+    # rows 1..n-1 reference column 0 only: edges exist in A's pattern one way only.
+    # On A + A^T every vertex neighbours 0, so there are two levels.
+    n = 9
+    r = list(range(n)) + list(range(1, n))
+    c = list(range(n)) + [0] * (n - 1)
+    A = gen.from_coo(n, r, c, np.ones(len(r)))
+    level_of, _, _, level_ptr = oracle.levels(A, 0)
+    assert np.diff(level_ptr).tolist() == [1, n - 1]
+    At = gen.from_coo(n, c, r, np.ones(len(r)))
+    assert np.array_equal(oracle.levels(At, 0)[0], level_of)
+
+
+def test_levels_disconnected_restart():
+    # components {0,1,2} (chain) and {3,4} (edge) and {5} (isolated)
+    n = 6
+    e = [(0, 1), (1, 2), (3, 4)]
+    r = list(range(n)) + [u for u, v in e] + [v for u, v in e]
+    c = list(range(n)) + [v for u, v in e] + [u for u, v in e]
+    A = gen.from_coo(n, r, c, np.ones(len(r)))
+    level_of, perm, _, level_ptr = oracle.levels(A, 0)
+    assert level_of.tolist() == [0, 1, 2, 3, 4, 5]
+    level_of, perm, _, level_ptr = oracle.levels(A, 4)
+    # from 4: L0={4}, L1={3}, restart at 0: L2={0}, L3={1}, L4={2}, restart at 5: L5={5}
+    assert level_of.tolist() == [2, 3, 4, 1, 0, 5]
+
+
+def test_levels_adjacency_invariant_random():
+    # Sec. 3: neighbours of L(i) lie in L(i-1), L(i), L(i+1)
+    for s, n in [(41, 500), (42, 3000)]:
+        A = gen.banded_random(n, stream=s)
+        level_of, perm, iperm, level_ptr = oracle.levels(A, 0)
+        rows = np.repeat(np.arange(n), np.diff(A.row_ptr))
+        assert np.max(np.abs(level_of[rows] - level_of[A.col])) <= 1
+        assert np.array_equal(np.sort(perm), np.arange(n))
+
+
+# ----------------------------------------------------------------------------- permutation
+def test_permute_is_pap_with_stored_order():
+    A = gen.random_int_matrix(25, 4, 51)
+    level_of, perm, iperm, _ = oracle.levels(A, 3)
+    prp, pci, pva = oracle.permute(A, perm, iperm)
+    D = A.to_dense()
+    Pd = gen.CSR(prp, pci, pva).to_dense()
+    assert np.array_equal(Pd, D[np.ix_(perm, perm)])
+    for r in range(25):
+        old = perm[r]
+        seg_old = slice(A.row_ptr[old], A.row_ptr[old + 1])
+        seg_new = slice(prp[r], prp[r + 1])
+        assert np.array_equal(pci[seg_new], iperm[A.col[seg_old]])
+        assert np.array_equal(pva[seg_new], A.val[seg_old])
+
+
+# ----------------------------------------------------------------------------- groups
+def test_groups_equal_levels():
+    # 12 levels of 10 rows with 3 entries each: bytes(level) = 12*30 + 4*10 + 16*10 = 560
+    L, rows, per = 12, 10, 3
+    level_ptr = np.arange(L + 1, dtype=np.int32) * rows
+    rp = np.arange(L * rows + 1, dtype=np.int32) * per
+    for k in (1, 2, 3, 5):
+        g = oracle.groups(level_ptr, rp, budget=560 * k)
+        assert np.array_equal(g, np.array(list(range(0, L, k)) + [L]))
+        g = oracle.groups(level_ptr, rp, budget=560 * k + 559)
+        assert np.array_equal(g, np.array(list(range(0, L, k)) + [L]))
+
+
+def test_groups_bulky_singleton_and_cover():
+    level_rows = [2, 2, 50, 2, 2, 2]
+    level_ptr = np.concatenate([[0], np.cumsum(level_rows)]).astype(np.int32)
+    rp = np.arange(level_ptr[-1] + 1, dtype=np.int32) * 2  # 2 entries per row
+    per_row = 12 * 2 + 4 + 16
+    g = oracle.groups(level_ptr, rp, budget=4 * per_row)
+    assert g.tolist() == [0, 2, 3, 5, 6]  # level 2 is bulky and alone
+    assert g[0] == 0 and g[-1] == len(level_rows) and np.all(np.diff(g) > 0)
+    # m right-hand sides and 4-byte values change the per-row cost
+    g2 = oracle.groups(level_ptr, rp, budget=4 * (8 * 2 + 4 + 32), val_bytes=4, m=2)
+    assert g2.tolist() == [0, 2, 3, 5, 6]
+
+
+# ----------------------------------------------------------------------------- schedule
+def test_lp_labels_fig2():
+    golden = np.array(read_golden("fig2_lp_labels.txt"))
+    assert np.array_equal(oracle.lp_labels(10, 5), golden)
+    # Sec. 3 text: L(5) at p=1 runs at step 15 and is reused at step 21 (p=2), p_m+1 steps later
+    lab = oracle.lp_labels(10, 5)
+    assert lab[0, 5] == 15 and lab[1, 5] == 21
+
+
+def test_lb_mpk_bitwise_equals_plain():
+    A = gen.laplacian_3d(9, 7, 5)
+    level_of, perm, iperm, level_ptr = oracle.levels(A, 0)
+    prp, pci, pva = oracle.permute(A, perm, iperm)
+    X = gen.vector(A.n, 2, stream=61)
+    Yplain = oracle.mpk(A, X, 6)
+    for budget in (1, 2000, 10**9):
+        gl = oracle.groups(level_ptr, prp, budget, m=2)
+        group_rows = level_ptr[gl]
+        Ylb = oracle.lb_mpk(prp, pci, pva, X[perm], 6, group_rows)
+        assert np.array_equal(Ylb[:, iperm, :], Yplain)
+
+
+# ----------------------------------------------------------------------------- Chebyshev
+def test_cheb_eigenvector_single_terms():
+    n = 60
+    A = gen.laplacian_1d(n)
+    lo, hi = gen.gershgorin_bounds(A)  # [0, 4]
+    assert (lo, hi) == (0.0, 4.0)
+    scale, shift = (hi - lo) / 2 * 1.01, (hi + lo) / 2
+    j = 7
+    th = j * np.pi / (n + 1)
+    v = np.sin(np.arange(1, n + 1) * th)
+    lamp = (2 - 2 * np.cos(th) - shift) / scale
+    for k in (0, 1, 2, 5, 16):
+        c = np.zeros(k + 1)
+        c[k] = 1.0
+        out = oracle.cheb(A, v, k, c, scale=scale, shift=shift)[:, 0]
+        assert _rel(out, np.cos(k * np.arccos(lamp)) * v) < 1e-12, k
+
+
+def test_bessel_against_published_and_scipy():
+    J = oracle.bessel_j(5, 1.0)
+    assert abs(J[0] - 0.7651976865579666) < 1e-15   # Abramowitz & Stegun Table 9.1
+    assert abs(J[1] - 0.4400505857449335) < 1e-15
+    J10 = oracle.bessel_j(30, 10.0)
+    assert abs(J10[0] - (-0.2459357644513483)) < 1e-14
+    assert abs(J10[1] - 0.04347274616886144) < 1e-14
+    assert abs(J10[0] ** 2 + 2 * np.sum(J10[1:] ** 2) - 1.0) < 1e-13
+    sp = pytest.importorskip("scipy.special")
+    for x in (0.5, 3.0, 25.0):
+        J = oracle.bessel_j(60, x)
+        assert np.max(np.abs(J - sp.jv(np.arange(61), x))) < 1e-14
+
+
+def test_cheb_time_step_matches_exponential():
+    # Sec. 7: exp(-i dt H) v = e^{-i dt c}[J0(a dt) v0 + 2 sum (-i)^k J_k(a dt) v_k] with H = a H' + c
+    n = 40
+    A = gen.laplacian_1d(n)
+    lo, hi = gen.gershgorin_bounds(A)
+    a, c = (hi - lo) / 2 * 1.01, (hi + lo) / 2
+    dt, M = 2.0, 40
+    J = oracle.bessel_j(M, a * dt)
+    coef = np.array([J[0]] + [2 * (-1j) ** k * J[k] for k in range(1, M + 1)]) * np.exp(-1j * dt * c)
+    j = 5
+    th = j * np.pi / (n + 1)
+    v = np.sin(np.arange(1, n + 1) * th)
+    lam = 2 - 2 * np.cos(th)
+    psi = np.stack([v, np.zeros(n)], axis=1)  # complex state as (re, im) columns
+    out = oracle.cheb(A, psi, M, coef.real.copy(), coef.imag.copy(), scale=a, shift=c)
+    got = out[:, 0] + 1j * out[:, 1]
+    want = np.exp(-1j * dt * lam) * v
+    assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-12
