@@ -1,0 +1,210 @@
+/*
+ * mpk.h -- C ABI of the GB300 level-blocked matrix power kernel library (libmpk.so).
+ *
+ * The library computes the matrix power kernel of "Cache Blocking of Distributed-Memory
+ * Parallel Matrix Power Kernels" (Lacey, Alappat, Lange, Hager, Fehske, Wellein):
+ *     Y[k] = A^k X,   k = 0..p          (Sec. 3, "MPK computes all vectors y_p = A^p x")
+ * for a square CSR matrix A, by level blocking: the rows are split into BFS levels of the
+ * graph of A (Sec. 3, level definition and Fig. 1), consecutive levels are grouped so that
+ * p+1 groups fit a cache budget (Sec. 3 reuse window, Sec. 6 parameter C), and the
+ * (group, power) cells of the Lp diagram are executed in its diagonal order (Fig. 2).
+ * On one GPU the paper's inter-process halo exchange (Alg. 2) is replaced by per-chunk
+ * completion flags in device memory.  A Chebyshev filter built on the same kernel
+ * implements the recurrence of Sec. 7.
+ *
+ * Conventions for every entry point
+ *  - All pointers named *_dev / documented as "device" are CUDA device pointers owned by
+ *    the caller unless stated otherwise; host pointers are marked "host".
+ *  - Dense blocks are row-major n x m ("nrhs" = m): the m values of one row are contiguous.
+ *    A power sequence Y is (p+1) x n x m doubles with Y[0] = X.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).  Work
+ *    is enqueued asynchronously on it; device-side failures (a bounded wait that expired)
+ *    are reported by mpk_sync_status().  Preprocessing calls (mpk_build_levels, mpk_plan)
+ *    synchronise the stream before returning.
+ *  - Every function returns an mpk_status and never throws; mpk_last_error() gives a
+ *    thread-local message for the last failure on the calling thread.
+ *  - Indices are int32: n, nnz < 2^31.  Floating point is IEEE binary64; each row sum is
+ *    evaluated in the row's stored order with one fused multiply-add per entry.
+ */
+#ifndef MPK_H
+#define MPK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    MPK_OK = 0,
+    MPK_ERR_INVALID = 1,     /* bad argument or malformed CSR (details in mpk_last_error) */
+    MPK_ERR_TOO_LARGE = 2,   /* a size exceeds int32 indexing or the library's limits */
+    MPK_ERR_OOM = 3,         /* a device allocation failed */
+    MPK_ERR_TIMEOUT = 4,     /* a bounded device wait expired; results of that call are void */
+    MPK_ERR_CUDA = 5,        /* a CUDA runtime call failed */
+    MPK_ERR_BUDGET = 6,      /* the plan would exceed mpk_plan_opts.mem_budget */
+    MPK_ERR_UNSUPPORTED = 7  /* valid request this build does not implement (e.g. nrhs) */
+} mpk_status;
+
+typedef enum { MPK_F64 = 0, MPK_F32 = 1, MPK_BF16 = 2 } mpk_dtype;
+
+typedef enum {
+    MPK_ORDER_ORIGINAL = 0,  /* X and Y use A's row numbering */
+    MPK_ORDER_PLAN = 1       /* X and Y use the plan's (BFS-permuted) row numbering */
+} mpk_order;
+
+typedef void *mpk_stream;
+
+/* A square CSR matrix in device memory, owned by the caller.  row_ptr has n+1 entries
+ * (row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz); col has nnz entries in [0, n); val
+ * has nnz entries of val_type.  Column order inside a row is free and duplicates are
+ * allowed: entries are summed in stored order.  is_symmetric = 1 declares that the
+ * sparsity pattern is symmetric, which skips the A + A^T step of the level builder. */
+typedef struct {
+    int32_t n;
+    int32_t nnz;
+    const int32_t *row_ptr;
+    const int32_t *col;
+    const void *val;
+    int32_t val_type;    /* mpk_dtype; this build accepts MPK_F64 */
+    int32_t is_symmetric;
+} mpk_csr;
+
+typedef struct mpk_levels_s mpk_levels;   /* opaque, library-owned */
+typedef struct mpk_plan_s mpk_plan_t;     /* opaque, library-owned */
+
+/* ---------------------------------------------------------------------------------------
+ * Levels.  Sec. 3: BFS from a root over the graph of A (pattern of A + A^T, self-loops
+ * ignored, the endnote on non-symmetric matrices); L(i+1) holds the untouched neighbours
+ * of L(i).  Inside a level vertices are ordered by ascending original index (the order of
+ * Fig. 1(c)).  When the search runs dry with vertices left (a disconnected graph) the
+ * smallest untouched vertex opens the next level.  perm maps new -> old, iperm old -> new.
+ * The result is unique for a given (A, root).  Synchronises `stream`.
+ * ------------------------------------------------------------------------------------- */
+mpk_status mpk_build_levels(const mpk_csr *A, int32_t root, mpk_stream stream, mpk_levels **out);
+
+/* Views into a levels object (device pointers valid until mpk_levels_destroy):
+ * level_ptr[num_levels+1] (row offsets of levels in the new order), perm[n], iperm[n],
+ * level_of[n].  Any output pointer may be NULL. */
+mpk_status mpk_levels_get(const mpk_levels *L, int32_t *n, int32_t *num_levels,
+                          const int32_t **level_ptr_dev, const int32_t **perm_dev,
+                          const int32_t **iperm_dev, const int32_t **level_of_dev);
+
+void mpk_levels_destroy(mpk_levels *L);
+
+/* ---------------------------------------------------------------------------------------
+ * Plans.  A plan owns a permuted copy of A (P A P^T, entries kept in stored order, in a
+ * sliced layout of 32-row slices), the level groups, the work-unit tables of the
+ * level-blocked schedule for every p <= p_max, per-chunk completion flags and a vector
+ * workspace.  Groups follow the greedy rule: walk the levels in order and add a level to
+ * the current group while the group's bytes stay <= floor(cache_bytes / (p_max + 1)),
+ * where a level costs (val_bytes + 4) * nnz + 4 * rows + 16 * nrhs * rows bytes; a level
+ * over the budget is a group of its own.  Passing L = NULL plans A in its own order with
+ * a single group (the unblocked reference configuration).
+ * ------------------------------------------------------------------------------------- */
+typedef struct {
+    int32_t p_max;          /* largest power mpk_apply may request (1..31)                 */
+    int32_t nrhs;           /* m: 1, 2, 4 or 8 right-hand sides per call                    */
+    int64_t cache_bytes;    /* C in bytes; 0 = half of the device L2                       */
+    int32_t order;          /* mpk_order of X, Y and the Chebyshev input/output             */
+    int32_t chunk_rows;     /* rows per work unit (multiple of 32); 0 = 512                 */
+    int64_t wait_limit_ns;  /* bound on every device-side wait; 0 = 2 s                     */
+    int64_t mem_budget;     /* bytes the plan may allocate on the device; 0 = no limit     */
+} mpk_plan_opts;
+
+/* Fills the defaults described above (p_max = 8, nrhs = 1, order = ORIGINAL). */
+void mpk_plan_opts_default(mpk_plan_opts *o);
+
+/* Builds a plan for A (the same matrix the levels were built from).  Synchronises. */
+mpk_status mpk_plan(const mpk_csr *A, const mpk_levels *L, const mpk_plan_opts *opts,
+                    mpk_stream stream, mpk_plan_t **out);
+
+typedef struct {
+    int32_t n, nnz, nrhs, p_max, order;
+    int32_t num_levels;           /* 0 for a plan without levels                         */
+    int32_t num_groups;
+    int32_t num_chunks;
+    int64_t group_budget_bytes;   /* floor(cache_bytes / (p_max + 1))                    */
+    int64_t cache_bytes;
+    int64_t device_bytes;         /* bytes allocated by the plan                         */
+    int64_t padded_entries;       /* entries of the sliced copy including padding        */
+    const int32_t *group_level_ptr_dev; /* num_groups+1 level indices (NULL without levels) */
+    const int32_t *group_row_ptr_dev;   /* num_groups+1 row offsets                        */
+    const int32_t *chunk_row_ptr_dev;   /* num_chunks+1 row offsets                        */
+    const int32_t *perm_dev;            /* new -> old (NULL: identity)                     */
+} mpk_plan_desc;
+
+mpk_status mpk_plan_describe(const mpk_plan_t *P, mpk_plan_desc *out);
+
+/* Writes the plan's permuted matrix P A P^T as CSR into caller buffers (device):
+ * row_ptr[n+1], col[nnz], val[nnz] (float64).  Asynchronous on `stream`. */
+mpk_status mpk_plan_export_csr(const mpk_plan_t *P, int32_t *row_ptr, int32_t *col, double *val,
+                               mpk_stream stream);
+
+void mpk_plan_destroy(mpk_plan_t *P);
+
+/* ---------------------------------------------------------------------------------------
+ * mpk_apply: Y[k] = A^k X for k = 0..p (Sec. 3; Alg. 2's local phase on one device).
+ * X: n x m device block; Y: (p+1) x n x m device block (Y[0] receives a copy of X), in the
+ * plan's order (opts.order).  1 <= p <= p_max (p = 0 only copies X).  X must not overlap
+ * Y[1..p].  One persistent kernel executes the Lp-diagram cells (group g, power k) in
+ * diagonal order, split into row chunks; each chunk waits on the completion flags of the
+ * chunks its rows read at power k-1.  With MPK_ORDER_ORIGINAL a gather kernel runs first
+ * and the kernel writes Y through the permutation.  Results equal back-to-back SpMV bit
+ * for bit.  Not safe to run concurrently with another call on the same plan.
+ * ------------------------------------------------------------------------------------- */
+mpk_status mpk_apply(const mpk_plan_t *P, const double *X, int32_t p, double *Y, mpk_stream stream);
+
+/* Plain comparator (Alg. 1 without halo exchange): p separate SpMV launches over the
+ * plan's matrix copy, same row arithmetic as mpk_apply.  Arguments as for mpk_apply. */
+mpk_status mpk_spmv_powers(const mpk_plan_t *P, const double *X, int32_t p, double *Y,
+                           mpk_stream stream);
+
+/* ---------------------------------------------------------------------------------------
+ * mpk_cheb_filter: out = sum_{k=0..degree} c_k T_k(A') X with A' = (A - shift I) / scale
+ * (Sec. 7: v_0 = x, v_1 = A' x, v_{k+1} = 2 A' v_k - v_{k-1}), run as ceil(degree/p_max)
+ * level-blocked launches of p_max steps (the paper's blocking of a long recurrence into
+ * MPK chunks of p_m).  Per row and step: w = A v_k (stored order), then
+ * v_1 = fma(1/scale, w, (-shift/scale) v_0) and v_{k+1} = fma(2/scale, w,
+ * fma(-2 shift/scale, v_k, -v_{k-1})); out accumulates c_0 v_0 then fma(c_k, v_k, out).
+ * coeff_re (host, degree+1 doubles) are real coefficients.  If coeff_im (host) is not
+ * NULL the coefficients are complex and act on pairs of right-hand sides (columns 2j,
+ * 2j+1 = real, imaginary part), as in the time step exp(-i dt H) of Sec. 7; nrhs must be
+ * even.  X and out: n x m device blocks in the plan's order; scale != 0.
+ * ------------------------------------------------------------------------------------- */
+mpk_status mpk_cheb_filter(const mpk_plan_t *P, const double *X, int32_t degree,
+                           const double *coeff_re, const double *coeff_im, double scale,
+                           double shift, double *out, mpk_stream stream);
+
+/* Synchronises `stream` and reports a device-side failure of the plan's calls since the
+ * last mpk_sync_status (MPK_ERR_TIMEOUT), else MPK_OK or a CUDA error. */
+mpk_status mpk_sync_status(const mpk_plan_t *P, mpk_stream stream);
+
+/* Fault injection for tests of the failure path (no counterpart in the paper): in the next
+ * level-blocked launch on this plan, work unit (chunk, k) computes its rows but does not
+ * publish its completion flag.  Units that read those rows wait until the plan's
+ * wait_limit_ns expires, record MPK_ERR_TIMEOUT and leave; every wait stays bounded and
+ * the device stays usable.  mpk_sync_status then reports MPK_ERR_TIMEOUT. */
+mpk_status mpk_debug_drop_release(mpk_plan_t *P, int32_t chunk, int32_t k);
+
+/* ---------------------------------------------------------------------------------------
+ * Measurement aids (the analogue of the paper's load-only bandwidth kernel, Sec. 6).
+ * mpk_probe_load: `reps` passes of 16-byte loads over buf[0..bytes) (bytes a multiple of
+ * 16) by ctas_per_sm * #SM blocks of 512 threads; sink is a device int that is written
+ * only if a checksum matches a constant.  mpk_probe_dfma: blocks * 256 threads each run
+ * `iters` x 8 independent FP64 FMAs; sink as above.
+ * ------------------------------------------------------------------------------------- */
+mpk_status mpk_probe_load(const void *buf, int64_t bytes, int32_t reps, int32_t ctas_per_sm,
+                          int32_t *sink, mpk_stream stream);
+mpk_status mpk_probe_dfma(int32_t blocks, int32_t iters, double *sink, mpk_stream stream);
+
+/* Number of SMs and L2 bytes of the current device. */
+mpk_status mpk_device_info(int32_t *num_sms, int64_t *l2_bytes);
+
+const char *mpk_status_string(mpk_status s);
+const char *mpk_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MPK_H */

@@ -1,0 +1,352 @@
+"""Python binding of libmpk.so, the GB300 level-blocked matrix power kernel library.
+
+Argument marshalling only: every step of the computation runs in the CUDA library behind
+the C ABI declared in include/mpk.h.  Tensors are torch CUDA tensors (torch provides
+device memory and streams); calls go to the current torch stream.  If the compiled
+library is missing, importing the binding's entry points raises instead of falling back.
+
+    import paper_2405_12525_gb300 as mpk
+    A = mpk.CsrMatrix(row_ptr, col, val)          # device tensors (int32, int32, float64)
+    L = mpk.build_levels(A, root=0)
+    P = mpk.plan(A, L, p_max=8, nrhs=1)
+    Y = P.apply(X, p=8)                            # (p+1, n, nrhs), Y[k] = A^k X
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+from ._build import LIB as _LIB_PATH
+from ._build import build as _build_lib
+
+__all__ = ["build", "load", "CsrMatrix", "Levels", "Plan", "build_levels", "plan", "MpkError",
+           "probe_load", "probe_dfma", "device_info", "EXPORTED_SYMBOLS"]
+
+MPK_OK, MPK_ERR_INVALID, MPK_ERR_TOO_LARGE, MPK_ERR_OOM, MPK_ERR_TIMEOUT = 0, 1, 2, 3, 4
+MPK_ERR_CUDA, MPK_ERR_BUDGET, MPK_ERR_UNSUPPORTED = 5, 6, 7
+MPK_F64, MPK_F32, MPK_BF16 = 0, 1, 2
+ORDER_ORIGINAL, ORDER_PLAN = 0, 1
+
+EXPORTED_SYMBOLS = [
+    "mpk_build_levels", "mpk_levels_get", "mpk_levels_destroy", "mpk_plan_opts_default", "mpk_plan",
+    "mpk_plan_describe", "mpk_plan_export_csr", "mpk_plan_destroy", "mpk_apply", "mpk_spmv_powers",
+    "mpk_cheb_filter", "mpk_sync_status", "mpk_probe_load", "mpk_probe_dfma", "mpk_device_info",
+    "mpk_status_string", "mpk_last_error", "mpk_debug_drop_release",
+]
+
+
+class MpkError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"mpk status {status}: {msg}")
+        self.status = status
+
+
+class _Csr(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int32), ("row_ptr", C.c_void_p), ("col", C.c_void_p),
+                ("val", C.c_void_p), ("val_type", C.c_int32), ("is_symmetric", C.c_int32)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("p_max", C.c_int32), ("nrhs", C.c_int32), ("cache_bytes", C.c_int64), ("order", C.c_int32),
+                ("chunk_rows", C.c_int32), ("wait_limit_ns", C.c_int64), ("mem_budget", C.c_int64)]
+
+
+class _Desc(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz", C.c_int32), ("nrhs", C.c_int32), ("p_max", C.c_int32),
+                ("order", C.c_int32), ("num_levels", C.c_int32), ("num_groups", C.c_int32),
+                ("num_chunks", C.c_int32), ("group_budget_bytes", C.c_int64), ("cache_bytes", C.c_int64),
+                ("device_bytes", C.c_int64), ("padded_entries", C.c_int64),
+                ("group_level_ptr_dev", C.c_void_p), ("group_row_ptr_dev", C.c_void_p),
+                ("chunk_row_ptr_dev", C.c_void_p), ("perm_dev", C.c_void_p)]
+
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile libmpk.so for sm_103a (nvcc) into paper_2405_12525_gb300/_lib/."""
+    return _build_lib(force=force)
+
+
+def load():
+    """Load libmpk.so; raises if it has not been built (there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_LIB_PATH):
+        raise RuntimeError(f"libmpk.so is missing at {_LIB_PATH}: run paper_2405_12525_gb300.build()")
+    lib = C.CDLL(_LIB_PATH)
+    vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "mpk_build_levels": [C.POINTER(_Csr), i32, vp, C.POINTER(vp)],
+        "mpk_levels_get": [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
+                           C.POINTER(vp)],
+        "mpk_plan": [C.POINTER(_Csr), vp, C.POINTER(_Opts), vp, C.POINTER(vp)],
+        "mpk_plan_describe": [vp, C.POINTER(_Desc)],
+        "mpk_plan_export_csr": [vp, vp, vp, vp, vp],
+        "mpk_apply": [vp, vp, i32, vp, vp],
+        "mpk_spmv_powers": [vp, vp, i32, vp, vp],
+        "mpk_cheb_filter": [vp, vp, i32, vp, vp, dbl, dbl, vp, vp],
+        "mpk_sync_status": [vp, vp],
+        "mpk_probe_load": [vp, i64, i32, i32, vp, vp],
+        "mpk_probe_dfma": [i32, i32, vp, vp],
+        "mpk_device_info": [C.POINTER(i32), C.POINTER(i64)],
+        "mpk_debug_drop_release": [vp, i32, i32],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.mpk_plan_opts_default.argtypes = [C.POINTER(_Opts)]
+    lib.mpk_plan_opts_default.restype = None
+    lib.mpk_levels_destroy.argtypes = [vp]
+    lib.mpk_levels_destroy.restype = None
+    lib.mpk_plan_destroy.argtypes = [vp]
+    lib.mpk_plan_destroy.restype = None
+    lib.mpk_status_string.argtypes = [C.c_int]
+    lib.mpk_status_string.restype = C.c_char_p
+    lib.mpk_last_error.argtypes = []
+    lib.mpk_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != MPK_OK:
+        lib = load()
+        raise MpkError(status, (lib.mpk_last_error() or b"").decode() or lib.mpk_status_string(status).decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def _ptr(t) -> int:
+    return int(t.data_ptr()) if t is not None and t.numel() > 0 else 0
+
+
+@dataclass
+class CsrMatrix:
+    """Device CSR matrix: row_ptr (n+1) and col (nnz) int32, val (nnz) float64 CUDA tensors."""
+    row_ptr: object
+    col: object
+    val: object
+    is_symmetric: bool = False
+
+    @property
+    def n(self) -> int:
+        return int(self.row_ptr.numel()) - 1
+
+    @property
+    def nnz(self) -> int:
+        return int(self.col.numel())
+
+    def _c(self) -> _Csr:
+        torch = _torch()
+        for t, dt in ((self.row_ptr, torch.int32), (self.col, torch.int32), (self.val, torch.float64)):
+            if t.dtype != dt or not t.is_cuda or not t.is_contiguous():
+                raise TypeError("CsrMatrix wants contiguous CUDA tensors: int32 row_ptr/col, float64 val")
+        return _Csr(self.n, self.nnz, _ptr(self.row_ptr), _ptr(self.col), _ptr(self.val), MPK_F64,
+                    1 if self.is_symmetric else 0)
+
+    @staticmethod
+    def from_host(A, device="cuda", is_symmetric=False) -> "CsrMatrix":
+        """From any object with row_ptr/col/val numpy arrays (e.g. gen.CSR)."""
+        torch = _torch()
+        return CsrMatrix(torch.as_tensor(A.row_ptr, dtype=torch.int32).to(device),
+                         torch.as_tensor(A.col, dtype=torch.int32).to(device),
+                         torch.as_tensor(A.val, dtype=torch.float64).to(device), is_symmetric)
+
+
+class Levels:
+    """BFS levels and permutation of a matrix (owns the library handle)."""
+
+    def __init__(self, handle, lib):
+        self._h = handle
+        self._lib = lib
+        n, nl = C.c_int32(), C.c_int32()
+        lp, pe, ip, lo = C.c_void_p(), C.c_void_p(), C.c_void_p(), C.c_void_p()
+        _check(lib.mpk_levels_get(handle, C.byref(n), C.byref(nl), C.byref(lp), C.byref(pe), C.byref(ip),
+                                  C.byref(lo)))
+        self.n, self.num_levels = n.value, nl.value
+        self._ptrs = (lp.value, pe.value, ip.value, lo.value)
+
+    def _view(self, ptr, count):
+        return _device_i32_copy(ptr, count)
+
+    @property
+    def level_ptr(self):
+        return self._view(self._ptrs[0], self.num_levels + 1)
+
+    @property
+    def perm(self):
+        return self._view(self._ptrs[1], self.n)
+
+    @property
+    def iperm(self):
+        return self._view(self._ptrs[2], self.n)
+
+    @property
+    def level_of(self):
+        return self._view(self._ptrs[3], self.n)
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            self._lib.mpk_levels_destroy(self._h)
+            self._h = None
+
+
+class _DeviceArray:
+    """Zero-copy view of library-owned device memory (CUDA array interface v3)."""
+
+    def __init__(self, ptr: int, count: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (count,), "typestr": typestr, "data": (ptr, False),
+                                         "version": 3, "strides": None}
+
+
+def _device_i32_copy(ptr: int, count: int):
+    """Copy `count` int32 values of library-owned device memory into a new torch tensor."""
+    torch = _torch()
+    if not ptr or count == 0:
+        return torch.empty(count, dtype=torch.int32, device="cuda")
+    return torch.as_tensor(_DeviceArray(ptr, count, "<i4"), device="cuda").clone()
+
+
+def build_levels(A: CsrMatrix, root: int = 0, stream=None) -> Levels:
+    lib = load()
+    h = C.c_void_p()
+    csr = A._c()
+    _check(lib.mpk_build_levels(C.byref(csr), int(root), _stream(stream), C.byref(h)))
+    return Levels(h, lib)
+
+
+class Plan:
+    """A level-blocked plan (owns the library handle)."""
+
+    def __init__(self, handle, lib):
+        self._h = handle
+        self._lib = lib
+        d = _Desc()
+        _check(lib.mpk_plan_describe(handle, C.byref(d)))
+        self.desc = d
+        self.n, self.nrhs, self.p_max, self.order = d.n, d.nrhs, d.p_max, d.order
+
+    def describe(self) -> dict:
+        d = _Desc()
+        _check(self._lib.mpk_plan_describe(self._h, C.byref(d)))
+        return {f: getattr(d, f) for f, _ in _Desc._fields_ if not f.endswith("_dev")}
+
+    def _device_i32(self, field: str, count: int):
+        return _device_i32_copy(getattr(self.desc, field), count)
+
+    @property
+    def group_level_ptr(self):
+        return self._device_i32("group_level_ptr_dev", self.desc.num_groups + 1) if self.desc.group_level_ptr_dev else None
+
+    @property
+    def group_row_ptr(self):
+        return self._device_i32("group_row_ptr_dev", self.desc.num_groups + 1)
+
+    @property
+    def chunk_row_ptr(self):
+        return self._device_i32("chunk_row_ptr_dev", self.desc.num_chunks + 1)
+
+    def export_csr(self, stream=None):
+        torch = _torch()
+        rp = torch.empty(self.n + 1, dtype=torch.int32, device="cuda")
+        ci = torch.empty(self.desc.nnz, dtype=torch.int32, device="cuda")
+        va = torch.empty(self.desc.nnz, dtype=torch.float64, device="cuda")
+        _check(self._lib.mpk_plan_export_csr(self._h, _ptr(rp), _ptr(ci), _ptr(va), _stream(stream)))
+        return rp, ci, va
+
+    def _block(self, X):
+        torch = _torch()
+        if X.dtype != torch.float64 or not X.is_cuda or not X.is_contiguous():
+            raise TypeError("X must be a contiguous float64 CUDA tensor")
+        if X.numel() != self.n * self.nrhs:
+            raise ValueError(f"X has {X.numel()} elements, plan wants n*nrhs = {self.n * self.nrhs}")
+
+    def apply(self, X, p: int, Y=None, stream=None):
+        """Y[k] = A^k X, k = 0..p (level-blocked).  Returns Y of shape (p+1, n, nrhs)."""
+        torch = _torch()
+        self._block(X)
+        if Y is None:
+            Y = torch.empty((p + 1, self.n, self.nrhs), dtype=torch.float64, device=X.device)
+        _check(self._lib.mpk_apply(self._h, _ptr(X), int(p), _ptr(Y), _stream(stream)))
+        return Y
+
+    def spmv_powers(self, X, p: int, Y=None, stream=None):
+        """Comparator: p separate SpMV launches over the same matrix copy."""
+        torch = _torch()
+        self._block(X)
+        if Y is None:
+            Y = torch.empty((p + 1, self.n, self.nrhs), dtype=torch.float64, device=X.device)
+        _check(self._lib.mpk_spmv_powers(self._h, _ptr(X), int(p), _ptr(Y), _stream(stream)))
+        return Y
+
+    def cheb_filter(self, X, degree: int, coeff_re, coeff_im=None, scale: float = 1.0, shift: float = 0.0,
+                    out=None, stream=None):
+        """sum_k c_k T_k((A - shift)/scale) X; complex coefficients act on (re, im) column pairs."""
+        torch = _torch()
+        import numpy as np
+        self._block(X)
+        cr = np.ascontiguousarray(coeff_re, dtype=np.float64)
+        ci = None if coeff_im is None else np.ascontiguousarray(coeff_im, dtype=np.float64)
+        if cr.size < degree + 1 or (ci is not None and ci.size < degree + 1):
+            raise ValueError("need degree+1 coefficients")
+        if out is None:
+            out = torch.empty((self.n, self.nrhs), dtype=torch.float64, device=X.device)
+        _check(self._lib.mpk_cheb_filter(self._h, _ptr(X), int(degree), cr.ctypes.data,
+                                         ci.ctypes.data if ci is not None else None, float(scale), float(shift),
+                                         _ptr(out), _stream(stream)))
+        return out
+
+    def debug_drop_release(self, chunk: int, k: int):
+        """Test hook: unit (chunk, k) of the next launch skips its completion flag."""
+        _check(self._lib.mpk_debug_drop_release(self._h, int(chunk), int(k)))
+
+    def sync_status(self, stream=None):
+        _check(self._lib.mpk_sync_status(self._h, _stream(stream)))
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            self._lib.mpk_plan_destroy(self._h)
+            self._h = None
+
+
+def plan(A: CsrMatrix, levels: Levels | None = None, p_max: int = 8, nrhs: int = 1, cache_bytes: int = 0,
+         order: int = ORDER_ORIGINAL, chunk_rows: int = 0, wait_limit_ns: int = 0, mem_budget: int = 0,
+         stream=None) -> Plan:
+    lib = load()
+    o = _Opts()
+    lib.mpk_plan_opts_default(C.byref(o))
+    o.p_max, o.nrhs, o.cache_bytes, o.order = p_max, nrhs, cache_bytes, order
+    o.chunk_rows, o.wait_limit_ns, o.mem_budget = chunk_rows, wait_limit_ns, mem_budget
+    h = C.c_void_p()
+    csr = A._c()
+    _check(lib.mpk_plan(C.byref(csr), levels._h if levels is not None else None, C.byref(o), _stream(stream),
+                        C.byref(h)))
+    return Plan(h, lib)
+
+
+def probe_load(buf, reps: int, ctas_per_sm: int, sink, stream=None):
+    _check(load().mpk_probe_load(_ptr(buf), buf.numel() * buf.element_size(), reps, ctas_per_sm, _ptr(sink),
+                                 _stream(stream)))
+
+
+def probe_dfma(blocks: int, iters: int, sink, stream=None):
+    _check(load().mpk_probe_dfma(blocks, iters, _ptr(sink), _stream(stream)))
+
+
+def device_info():
+    sms, l2 = C.c_int32(), C.c_int64()
+    _check(load().mpk_device_info(C.byref(sms), C.byref(l2)))
+    return sms.value, l2.value

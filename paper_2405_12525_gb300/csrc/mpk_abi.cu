@@ -1,0 +1,357 @@
+// extern "C" entry points of libmpk.so (declared in include/mpk.h).  Argument checks
+// happen here; every entry point converts internal failures into an mpk_status.
+#include "mpk_internal.h"
+
+#include <algorithm>
+#include <climits>
+#include <cstring>
+#include <new>
+
+namespace mpk {
+const char *last_error_text();
+}
+
+using namespace mpk;
+
+#define MPK_GUARD_BEGIN try {
+#define MPK_GUARD_END                                                  \
+    }                                                                  \
+    catch (const Fail &f) {                                            \
+        return f.status;                                               \
+    }                                                                  \
+    catch (const std::bad_alloc &) {                                   \
+        set_error("host allocation failed");                           \
+        return MPK_ERR_OOM;                                            \
+    }                                                                  \
+    catch (...) {                                                      \
+        set_error("unexpected internal error");                        \
+        return MPK_ERR_CUDA;                                           \
+    }
+
+struct mpk_levels_s {
+    Levels *impl;
+};
+struct mpk_plan_s {
+    Plan *impl;
+};
+
+static cudaStream_t as_stream(mpk_stream s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// ---------------------------------------------------------------------------------------- levels
+extern "C" mpk_status mpk_build_levels(const mpk_csr *A, int32_t root, mpk_stream stream, mpk_levels **out) {
+    MPK_GUARD_BEGIN
+    if (!out) fail(MPK_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    Levels *L = build_levels(A, root, as_stream(stream));
+    *out = new mpk_levels_s{L};
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
+extern "C" mpk_status mpk_levels_get(const mpk_levels *L, int32_t *n, int32_t *num_levels, const int32_t **level_ptr,
+                                     const int32_t **perm, const int32_t **iperm, const int32_t **level_of) {
+    if (!L || !L->impl) {
+        set_error("levels handle is NULL");
+        return MPK_ERR_INVALID;
+    }
+    if (n) *n = L->impl->n;
+    if (num_levels) *num_levels = L->impl->num_levels;
+    if (level_ptr) *level_ptr = L->impl->level_ptr;
+    if (perm) *perm = L->impl->perm;
+    if (iperm) *iperm = L->impl->iperm;
+    if (level_of) *level_of = L->impl->level_of;
+    return MPK_OK;
+}
+
+extern "C" void mpk_levels_destroy(mpk_levels *L) {
+    if (!L) return;
+    if (L->impl) {
+        L->impl->arena.release();
+        delete L->impl;
+    }
+    delete L;
+}
+
+// ---------------------------------------------------------------------------------------- plans
+extern "C" void mpk_plan_opts_default(mpk_plan_opts *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->p_max = 8;
+    o->nrhs = 1;
+    o->order = MPK_ORDER_ORIGINAL;
+}
+
+extern "C" mpk_status mpk_plan(const mpk_csr *A, const mpk_levels *L, const mpk_plan_opts *opts, mpk_stream stream,
+                               mpk_plan_t **out) {
+    MPK_GUARD_BEGIN
+    if (!out) fail(MPK_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (L && !L->impl) fail(MPK_ERR_INVALID, "levels handle is empty");
+    Plan *P = build_plan(A, L ? L->impl : nullptr, opts, as_stream(stream));
+    *out = new mpk_plan_s{P};
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
+extern "C" mpk_status mpk_plan_describe(const mpk_plan_t *P, mpk_plan_desc *d) {
+    if (!P || !P->impl || !d) {
+        set_error("NULL plan or descriptor");
+        return MPK_ERR_INVALID;
+    }
+    const Plan &p = *P->impl;
+    std::memset(d, 0, sizeof(*d));
+    d->n = p.n;
+    d->nnz = p.nnz;
+    d->nrhs = p.m;
+    d->p_max = p.p_max;
+    d->order = p.order;
+    d->num_levels = p.num_levels;
+    d->num_groups = p.num_groups;
+    d->num_chunks = p.num_chunks;
+    d->group_budget_bytes = p.group_budget;
+    d->cache_bytes = p.cache_bytes;
+    d->device_bytes = p.arena.bytes;
+    d->padded_entries = p.padded;
+    d->group_level_ptr_dev = p.group_level_ptr;
+    d->group_row_ptr_dev = p.group_row_ptr;
+    d->chunk_row_ptr_dev = p.chunk_row;
+    d->perm_dev = p.perm;
+    return MPK_OK;
+}
+
+extern "C" mpk_status mpk_plan_export_csr(const mpk_plan_t *P, int32_t *row_ptr, int32_t *col, double *val,
+                                          mpk_stream stream) {
+    MPK_GUARD_BEGIN
+    if (!P || !P->impl) fail(MPK_ERR_INVALID, "plan is NULL");
+    export_csr(*P->impl, row_ptr, col, val, as_stream(stream));
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
+extern "C" void mpk_plan_destroy(mpk_plan_t *P) {
+    if (!P) return;
+    if (P->impl) {
+        P->impl->arena.release();
+        delete P->impl;
+    }
+    delete P;
+}
+
+// ---------------------------------------------------------------------------------------- apply
+static void next_epoch(Plan &P, cudaStream_t s) {
+    if (P.epoch == INT_MAX) {  // flags hold old epochs: clear them before reuse
+        MPK_CUDA(cudaMemsetAsync(P.flags, 0, sizeof(int32_t) * (size_t)(P.p_max + 1) * std::max(1, P.num_chunks), s));
+        MPK_CUDA(cudaMemsetAsync(P.ctl + 2, 0, 2 * sizeof(unsigned int), s));
+        P.epoch = 0;
+        P.last_checked_epoch = 0;
+    }
+    ++P.epoch;
+}
+
+static KArgs base_args(Plan &P, int32_t p) {
+    KArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.val = P.val;
+    a.col = P.col;
+    a.slice_ptr = P.slice_ptr;
+    a.rowlen = P.rowlen;
+    a.chunk_row = P.chunk_row;
+    a.chunk_slice = P.chunk_slice;
+    a.dep = P.dep;
+    a.n = P.n;
+    a.nchunks = P.num_chunks;
+    a.units = P.units + P.unit_off[p];
+    a.nunits = P.unit_off[p + 1] - P.unit_off[p];
+    a.flags = P.flags;
+    a.epoch = P.epoch;
+    a.ticket = P.ctl;
+    a.exit_count = P.ctl + 1;
+    a.err = reinterpret_cast<int32_t *>(P.ctl + 2);
+    a.wait_ns = P.wait_ns;
+    a.drop_unit = P.drop_unit;
+    P.drop_unit = -1;
+    a.ystride = (int64_t)P.n * P.m;
+    a.ostride = (int64_t)P.n * P.m;
+    a.perm = P.perm;
+    return a;
+}
+
+static void check_apply_args(const mpk_plan_t *Ph, const double *X, int32_t p, const double *Y) {
+    if (!Ph || !Ph->impl) fail(MPK_ERR_INVALID, "plan is NULL");
+    const Plan &P = *Ph->impl;
+    if (p < 0 || p > P.p_max) fail(MPK_ERR_INVALID, "p = %d outside [0, p_max = %d]", p, P.p_max);
+    if (P.n > 0 && (!X || !Y)) fail(MPK_ERR_INVALID, "NULL X or Y");
+}
+
+extern "C" mpk_status mpk_apply(const mpk_plan_t *Ph, const double *X, int32_t p, double *Y, mpk_stream stream) {
+    MPK_GUARD_BEGIN
+    check_apply_args(Ph, X, p, Y);
+    Plan &P = *const_cast<Plan *>(Ph->impl);
+    cudaStream_t s = as_stream(stream);
+    const int64_t nm = (int64_t)P.n * P.m;
+    if (P.n == 0) return MPK_OK;
+    if (p == 0) {
+        if (Y != X) MPK_CUDA(cudaMemcpyAsync(Y, X, sizeof(double) * nm, cudaMemcpyDeviceToDevice, s));
+        return MPK_OK;
+    }
+    next_epoch(P, s);
+    KArgs a = base_args(P, p);
+    int mode;
+    if (P.identity || P.order == MPK_ORDER_PLAN) {
+        a.x0 = X;
+        a.ybase = Y;
+        a.ring = p + 1;
+        a.y0copy = (Y != X) ? Y : nullptr;
+        mode = 0;
+    } else {
+        launch_gather_rows(X, P.perm, P.work, P.n, P.m, s);
+        if (Y != X) MPK_CUDA(cudaMemcpyAsync(Y, X, sizeof(double) * nm, cudaMemcpyDeviceToDevice, s));
+        a.x0 = P.work;
+        a.ybase = P.work;
+        a.ring = 3;
+        a.yorig = Y;
+        mode = 1;
+    }
+    launch_mpk(P, a, mode, s);
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
+extern "C" mpk_status mpk_spmv_powers(const mpk_plan_t *Ph, const double *X, int32_t p, double *Y,
+                                      mpk_stream stream) {
+    MPK_GUARD_BEGIN
+    check_apply_args(Ph, X, p, Y);
+    Plan &P = *const_cast<Plan *>(Ph->impl);
+    cudaStream_t s = as_stream(stream);
+    const int64_t nm = (int64_t)P.n * P.m;
+    if (P.n == 0) return MPK_OK;
+    if (Y != X) MPK_CUDA(cudaMemcpyAsync(Y, X, sizeof(double) * nm, cudaMemcpyDeviceToDevice, s));
+    if (P.identity || P.order == MPK_ORDER_PLAN) {
+        for (int k = 1; k <= p; ++k) launch_spmv(P, Y + (k - 1) * nm, Y + k * nm, nullptr, 0, s);
+    } else {
+        launch_gather_rows(X, P.perm, P.work, P.n, P.m, s);
+        for (int k = 1; k <= p; ++k)
+            launch_spmv(P, P.work + ((k - 1) % 2) * nm, P.work + (k % 2) * nm, Y, k * nm, s);
+    }
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
+extern "C" mpk_status mpk_cheb_filter(const mpk_plan_t *Ph, const double *X, int32_t degree, const double *coeff_re,
+                                      const double *coeff_im, double scale, double shift, double *out,
+                                      mpk_stream stream) {
+    MPK_GUARD_BEGIN
+    if (!Ph || !Ph->impl) fail(MPK_ERR_INVALID, "plan is NULL");
+    Plan &P = *const_cast<Plan *>(Ph->impl);
+    if (degree < 0) fail(MPK_ERR_INVALID, "degree must be >= 0");
+    if (!coeff_re) fail(MPK_ERR_INVALID, "coeff_re is NULL");
+    if (!(scale != 0.0)) fail(MPK_ERR_INVALID, "scale must be non-zero");
+    if (coeff_im && (P.m % 2)) fail(MPK_ERR_INVALID, "complex coefficients need an even nrhs");
+    if (P.n > 0 && (!X || !out)) fail(MPK_ERR_INVALID, "NULL X or out");
+    if (P.n == 0) return MPK_OK;
+    cudaStream_t s = as_stream(stream);
+    const int64_t nm = (int64_t)P.n * P.m;
+    const bool plan_order = P.identity || P.order == MPK_ORDER_PLAN;
+    // same expressions as the recurrence's definition: 2A'v = alpha Av + beta v
+    const double alpha = 2.0 / scale, beta = -2.0 * shift / scale;
+    const double halpha = 1.0 / scale, hbeta = -shift / scale;
+    double *v0 = P.work;
+    double *acc = plan_order ? out : P.work + 3 * nm;
+    if (plan_order) {
+        MPK_CUDA(cudaMemcpyAsync(v0, X, sizeof(double) * nm, cudaMemcpyDeviceToDevice, s));
+    } else {
+        launch_gather_rows(X, P.perm, v0, P.n, P.m, s);
+    }
+    launch_cheb_init(v0, acc, P.n, P.m, coeff_re[0], coeff_im ? coeff_im[0] : 0.0, coeff_im ? 1 : 0, s);
+    for (int32_t j0 = 0; j0 < degree; j0 += P.p_max) {
+        const int32_t pb = std::min(P.p_max, degree - j0);
+        next_epoch(P, s);
+        KArgs a = base_args(P, pb);
+        a.x0 = v0;
+        a.ybase = P.work;
+        a.ring = 3;
+        a.k_offset = j0;
+        a.alpha = alpha;
+        a.beta = beta;
+        a.halpha = halpha;
+        a.hbeta = hbeta;
+        a.acc = acc;
+        a.complex_coeff = coeff_im ? 1 : 0;
+        for (int k = 1; k <= pb; ++k) {
+            a.cre[k] = coeff_re[j0 + k];
+            a.cim[k] = coeff_im ? coeff_im[j0 + k] : 0.0;
+        }
+        launch_mpk(P, a, 2, s);
+    }
+    if (!plan_order) launch_scatter_rows(acc, P.iperm, out, P.n, P.m, s);
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
+extern "C" mpk_status mpk_sync_status(const mpk_plan_t *Ph, mpk_stream stream) {
+    MPK_GUARD_BEGIN
+    if (!Ph || !Ph->impl) fail(MPK_ERR_INVALID, "plan is NULL");
+    Plan &P = *const_cast<Plan *>(Ph->impl);
+    MPK_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    unsigned int h[2] = {0, 0};
+    MPK_CUDA(cudaMemcpy(h, P.ctl + 2, sizeof(h), cudaMemcpyDeviceToHost));
+    const int32_t err_epoch = (int32_t)h[0];
+    const int32_t checked = P.last_checked_epoch;
+    P.last_checked_epoch = P.epoch;
+    if (err_epoch > checked && err_epoch <= P.epoch) {
+        set_error("a bounded device wait expired in launch %d", err_epoch);
+        return h[1] ? (mpk_status)h[1] : MPK_ERR_TIMEOUT;
+    }
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
+extern "C" mpk_status mpk_debug_drop_release(mpk_plan_t *Ph, int32_t chunk, int32_t k) {
+    MPK_GUARD_BEGIN
+    if (!Ph || !Ph->impl) fail(MPK_ERR_INVALID, "plan is NULL");
+    Plan &P = *Ph->impl;
+    if (chunk < 0 || chunk >= P.num_chunks || k < 1 || k > P.p_max) fail(MPK_ERR_INVALID, "no such unit");
+    P.drop_unit = (chunk << 5) | k;
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
+// ---------------------------------------------------------------------------------------- probes
+extern "C" mpk_status mpk_probe_load(const void *buf, int64_t bytes, int32_t reps, int32_t ctas_per_sm, int32_t *sink,
+                                     mpk_stream stream) {
+    MPK_GUARD_BEGIN
+    probe_load(buf, bytes, reps, ctas_per_sm, sink, as_stream(stream));
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
+extern "C" mpk_status mpk_probe_dfma(int32_t blocks, int32_t iters, double *sink, mpk_stream stream) {
+    MPK_GUARD_BEGIN
+    probe_dfma(blocks, iters, sink, as_stream(stream));
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
+extern "C" mpk_status mpk_device_info(int32_t *num_sms, int64_t *l2_bytes) {
+    MPK_GUARD_BEGIN
+    if (num_sms) *num_sms = device_sms();
+    if (l2_bytes) *l2_bytes = device_l2_bytes();
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
+extern "C" const char *mpk_status_string(mpk_status s) {
+    switch (s) {
+        case MPK_OK: return "ok";
+        case MPK_ERR_INVALID: return "invalid argument";
+        case MPK_ERR_TOO_LARGE: return "too large";
+        case MPK_ERR_OOM: return "out of device memory";
+        case MPK_ERR_TIMEOUT: return "device wait timed out";
+        case MPK_ERR_CUDA: return "CUDA error";
+        case MPK_ERR_BUDGET: return "memory budget exceeded";
+        case MPK_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+extern "C" const char *mpk_last_error(void) { return last_error_text(); }

@@ -1,0 +1,184 @@
+// Internal declarations shared by the CUDA translation units of libmpk.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/mpk.h"
+
+namespace mpk {
+
+// ----------------------------------------------------------------------------- errors
+// Library code throws Fail; every extern "C" entry point catches it and returns .status.
+struct Fail {
+    mpk_status status;
+};
+
+void set_error(const char *fmt, ...);
+[[noreturn]] void fail(mpk_status s, const char *fmt, ...);
+
+#define MPK_CUDA(call)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (call);                                                                \
+        if (e_ != cudaSuccess)                                                                  \
+            ::mpk::fail(e_ == cudaErrorMemoryAllocation ? MPK_ERR_OOM : MPK_ERR_CUDA,           \
+                        "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__,       \
+                        __LINE__);                                                              \
+    } while (0)
+
+#define MPK_LAUNCHED() MPK_CUDA(cudaGetLastError())
+
+// ----------------------------------------------------------------------------- memory
+// Device allocation with byte accounting against an optional budget.
+struct Arena {
+    int64_t bytes = 0;
+    int64_t budget = 0;  // 0 = unlimited
+    std::vector<void *> ptrs;
+    void *alloc(int64_t nbytes);
+    template <class T> T *alloc_n(int64_t n) { return static_cast<T *>(alloc(n * (int64_t)sizeof(T))); }
+    void release();
+};
+
+// Temporary device buffer freed on scope exit (not counted in a plan).
+template <class T> struct Tmp {
+    T *p = nullptr;
+    explicit Tmp(int64_t n) {
+        if (n > 0) MPK_CUDA(cudaMalloc(&p, (size_t)n * sizeof(T)));
+    }
+    ~Tmp() {
+        if (p) cudaFree(p);
+    }
+    Tmp(const Tmp &) = delete;
+    Tmp &operator=(const Tmp &) = delete;
+};
+
+// ----------------------------------------------------------------------------- primitives
+// out[0..n] = exclusive prefix sum of in[0..n) (out[n] = total).  out may alias in.
+void exclusive_scan(const int32_t *in, int32_t *out, int64_t n, cudaStream_t s);
+void exclusive_scan(const int64_t *in, int64_t *out, int64_t n, cudaStream_t s);
+
+// Stable LSD radix sort of (key, value) pairs by the low `key_bits` bits of key.
+// Inputs are consumed (used as ping-pong buffers); the sorted result is returned through
+// *keys_out / *vals_out, which point into either the input or the scratch buffers.
+void radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_tmp, uint32_t *vals_tmp,
+                      int64_t n, int key_bits, cudaStream_t s, uint32_t **keys_out,
+                      uint32_t **vals_out);
+
+void fill_i32(int32_t *p, int32_t v, int64_t n, cudaStream_t s);
+void iota_i32(int32_t *p, int64_t n, cudaStream_t s);
+
+int device_sms();
+int64_t device_l2_bytes();
+
+// ----------------------------------------------------------------------------- objects
+struct Levels {
+    int32_t n = 0;
+    int32_t num_levels = 0;
+    int32_t *level_ptr = nullptr;  // num_levels + 1
+    int32_t *perm = nullptr;       // new -> old
+    int32_t *iperm = nullptr;      // old -> new
+    int32_t *level_of = nullptr;   // per original vertex
+    std::vector<int32_t> h_level_ptr;
+    Arena arena;
+};
+
+// Arguments of the level-blocked kernel, passed by value.
+constexpr int kMaxP = 31;
+struct KArgs {
+    // sliced matrix copy (plan order)
+    const double *val;
+    const int32_t *col;
+    const int64_t *slice_ptr;
+    const int32_t *rowlen;
+    const int32_t *chunk_row;
+    const int32_t *chunk_slice;
+    const int2 *dep;
+    int32_t n;
+    int32_t nchunks;
+    // schedule for this launch
+    const int32_t *units;
+    int64_t nunits;
+    int32_t *flags;  // (p+1) x nchunks, epoch-valued
+    int32_t epoch;
+    unsigned int *ticket;
+    unsigned int *exit_count;
+    int32_t *err;    // err[0] = epoch of a failed launch, err[1] = status code
+    int64_t wait_ns;
+    int32_t drop_unit;  // test hook: this unit (chunk << 5 | k) skips its release, -1 = none
+    // vectors
+    const double *x0;  // power-0 block (plan order)
+    double *ybase;     // slot(k) = ybase + (k % ring) * ystride
+    int64_t ystride;
+    int32_t ring;
+    double *y0copy;    // if set, units of power 1 copy their rows of x0 here
+    double *yorig;     // if set, power k of row r is also written to yorig[k*ostride + perm[r]*M]
+    const int32_t *perm;
+    int64_t ostride;
+    int32_t k_offset;  // absolute index of local power 0 (Chebyshev blocks)
+    // Chebyshev recurrence
+    double alpha, beta, halpha, hbeta;
+    double *acc;
+    int32_t complex_coeff;
+    double cre[kMaxP + 1];
+    double cim[kMaxP + 1];
+};
+
+struct Plan {
+    int32_t n = 0, nnz = 0, m = 1, p_max = 8, order = MPK_ORDER_ORIGINAL;
+    int32_t num_levels = 0, num_groups = 0, num_chunks = 0, num_slices = 0;
+    int32_t chunk_rows = 512;
+    int64_t cache_bytes = 0, group_budget = 0, padded = 0, wait_ns = 0;
+    bool identity = false;
+    // device data (owned by arena)
+    double *val = nullptr;
+    int32_t *col = nullptr;
+    int64_t *slice_ptr = nullptr;
+    int32_t *rowlen = nullptr;
+    int32_t *chunk_row = nullptr;
+    int32_t *chunk_slice = nullptr;
+    int2 *dep = nullptr;
+    int32_t *group_level_ptr = nullptr;
+    int32_t *group_row_ptr = nullptr;
+    int32_t *perm = nullptr;   // owned copy (NULL for identity)
+    int32_t *iperm = nullptr;
+    int32_t *units = nullptr;  // concatenated unit tables for p = 1..p_max
+    std::vector<int64_t> unit_off;  // unit_off[p] .. unit_off[p] + nunits(p)
+    int32_t *flags = nullptr;
+    unsigned int *ctl = nullptr;  // [0] ticket, [1] exit count, [2] err epoch, [3] err code
+    double *work = nullptr;       // 3 ring slots + accumulator, each n*m
+    int32_t epoch = 0;
+    int32_t last_checked_epoch = 0;
+    int32_t drop_unit = -1;  // armed by mpk_debug_drop_release for the next launch
+    int grid_mpk[4] = {0, 0, 0, 0};  // persistent grid size per mode
+    Arena arena;
+};
+
+// kernels (mpk_kernel.cu)
+void launch_mpk(const Plan &P, KArgs &a, int mode, cudaStream_t s);
+void launch_spmv(const Plan &P, const double *x, double *y, double *yorig, int64_t orig_off,
+                 cudaStream_t s);
+void launch_gather_rows(const double *src, const int32_t *perm, double *dst, int32_t n, int32_t m,
+                        cudaStream_t s);
+void launch_scatter_rows(const double *src, const int32_t *iperm, double *dst, int32_t n, int32_t m,
+                         cudaStream_t s);
+void launch_cheb_init(const double *v0, double *acc, int32_t n, int32_t m, double c0re, double c0im,
+                      int complex_coeff, cudaStream_t s);
+int occupancy_grid(int mode, int m);
+
+// level builder (mpk_levels.cu)
+Levels *build_levels(const mpk_csr *A, int32_t root, cudaStream_t s);
+void validate_csr(const mpk_csr *A, cudaStream_t s);
+
+// planner (mpk_plan.cu)
+Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cudaStream_t s);
+void export_csr(const Plan &P, int32_t *rp, int32_t *ci, double *va, cudaStream_t s);
+
+// probes (mpk_kernel.cu)
+void probe_load(const void *buf, int64_t bytes, int reps, int ctas_per_sm, int32_t *sink, cudaStream_t s);
+void probe_dfma(int blocks, int iters, double *sink, cudaStream_t s);
+
+}  // namespace mpk

@@ -1,0 +1,337 @@
+"""CUDA path (through the C ABI) against the CPU oracle.
+
+Bit-exact everywhere: levels, permutation and groups are integers; every floating-point
+result is a row sum evaluated in stored order with one fma per entry on both sides, so
+the CUDA results must equal the oracle's bit for bit (the 1e-13 relative tolerance of the
+FP64 contract is therefore met with margin; it is asserted as well).
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from conftest import read_golden
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL_TOL = 1e-13
+
+
+@pytest.fixture(scope="module")
+def mpk():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2405_12525_gb300 as m
+    m.build()
+    m.load()
+    return m
+
+
+def _dev(A, mpk, sym=False):
+    return mpk.CsrMatrix.from_host(A, is_symmetric=sym)
+
+
+def _fig1():
+    edges = read_golden("fig1_graph.txt")
+    n = 20
+    r = list(range(n)) + [u for u, v in edges] + [v for u, v in edges]
+    c = list(range(n)) + [v for u, v in edges] + [u for u, v in edges]
+    return gen.from_coo(n, r, c, np.arange(len(r), dtype=np.float64) * 0.25 - 3.0)
+
+
+def _disconnected():
+    n = 9
+    e = [(0, 1), (1, 2), (3, 4), (6, 7)]
+    r = list(range(n)) + [u for u, v in e] + [v for u, v in e]
+    c = list(range(n)) + [v for u, v in e] + [u for u, v in e]
+    return gen.from_coo(n, r, c, np.linspace(-1, 1, len(r)))
+
+
+def _star_one_way(n=40):
+    r = list(range(n)) + list(range(1, n))
+    c = list(range(n)) + [0] * (n - 1)
+    return gen.from_coo(n, r, c, np.linspace(0.5, 1.5, len(r)))
+
+
+def _empty_rows():
+    # rows 3 and 7 store nothing; row 5 stores only a zero
+    rows = [0, 0, 1, 2, 4, 4, 5, 6, 8, 8, 9]
+    cols = [0, 4, 1, 2, 4, 8, 5, 6, 8, 0, 9]
+    vals = [1.5, -2.0, 1.0, 3.0, 0.5, 1.0, 0.0, -1.0, 2.0, 0.25, 1.0]
+    return gen.from_coo(10, rows, cols, vals)
+
+
+MATRICES = {
+    "fig1": (_fig1, False),
+    "lap3d_5x4x3": (lambda: gen.laplacian_3d(5, 4, 3), True),
+    "lap3d_17x9x6": (lambda: gen.laplacian_3d(17, 9, 6), True),
+    "lap2d_64": (lambda: gen.laplacian_2d(64, 64), True),
+    "band_3000": (lambda: gen.banded_random(3000, stream=71), True),
+    "int_nonsym_500": (lambda: gen.random_int_matrix(500, 5, stream=72), False),
+    "disconnected": (_disconnected, False),
+    "star_one_way": (_star_one_way, False),
+    "empty_rows": (_empty_rows, False),
+    "xxz_10": (lambda: gen.xxz_chain(10, stream=73), True),
+    "single": (lambda: gen.CSR([0, 1], [0], np.array([2.0])), True),
+}
+
+
+def _poisoned(shape):
+    return torch.full(shape, float("nan"), dtype=torch.float64, device="cuda")
+
+
+# ----------------------------------------------------------------------------- levels (a1-a3)
+@pytest.mark.parametrize("name", sorted(MATRICES))
+@pytest.mark.parametrize("declare_symmetric", [False, True])
+def test_levels_bit_exact(mpk, name, declare_symmetric):
+    make, sym = MATRICES[name]
+    if declare_symmetric and not sym:
+        pytest.skip("pattern not symmetric")
+    A = make()
+    roots = [0] if A.n < 3 else [0, A.n // 2, A.n - 1]
+    for root in roots:
+        L = mpk.build_levels(_dev(A, mpk, declare_symmetric), root=root)
+        lo, pe, ip, lp = oracle.levels(A, root)
+        assert L.num_levels == lp.size - 1
+        assert np.array_equal(L.level_of.cpu().numpy(), lo)
+        assert np.array_equal(L.perm.cpu().numpy(), pe)
+        assert np.array_equal(L.iperm.cpu().numpy(), ip)
+        assert np.array_equal(L.level_ptr.cpu().numpy(), lp)
+
+
+def test_levels_fig1_against_paper(mpk):
+    L = mpk.build_levels(_dev(_fig1(), mpk), 0)
+    golden = dict((o, nl) for o, nl in read_golden("fig1_perm.txt"))
+    assert L.iperm.cpu().numpy().tolist() == [golden[o] for o in range(20)]
+    assert np.diff(L.level_ptr.cpu().numpy()).tolist() == [1, 1, 2, 3, 3, 3, 3, 2, 1, 1]
+
+
+def test_levels_grid_many_levels(mpk):
+    A = gen.laplacian_3d(48, 40, 33)   # 118 levels, widths vary
+    L = mpk.build_levels(_dev(A, mpk, True), 0)
+    i = np.arange(A.n)
+    assert np.array_equal(L.level_of.cpu().numpy(), i % 48 + (i // 48) % 40 + i // (48 * 40))
+    _, pe, _, lp = oracle.levels(A, 0)
+    assert np.array_equal(L.perm.cpu().numpy(), pe)
+    assert np.array_equal(L.level_ptr.cpu().numpy(), lp)
+
+
+def test_invalid_csr_rejected(mpk):
+    A = gen.laplacian_2d(5, 5)
+    bad = gen.CSR(A.row_ptr, A.col.copy(), A.val)
+    bad.col[3] = 25
+    with pytest.raises(mpk.MpkError) as e:
+        mpk.build_levels(_dev(bad, mpk), 0)
+    assert e.value.status == 1
+    rp = A.row_ptr.copy()
+    rp[4], rp[5] = rp[5], rp[4]
+    with pytest.raises(mpk.MpkError):
+        mpk.build_levels(_dev(gen.CSR(rp, A.col, A.val), mpk), 0)
+    with pytest.raises(mpk.MpkError):
+        mpk.build_levels(_dev(A, mpk), root=25)
+
+
+# ----------------------------------------------------------------------------- plan (a3-a4)
+@pytest.mark.parametrize("name", ["lap3d_17x9x6", "band_3000", "int_nonsym_500", "xxz_10", "fig1"])
+@pytest.mark.parametrize("cache_bytes,p_max,m", [(4000, 4, 1), (60000, 8, 2), (10**9, 3, 1), (1, 2, 4)])
+def test_plan_groups_and_permuted_matrix(mpk, name, cache_bytes, p_max, m):
+    make, sym = MATRICES[name]
+    A = make()
+    dA = _dev(A, mpk, sym)
+    L = mpk.build_levels(dA, 0)
+    P = mpk.plan(dA, L, p_max=p_max, nrhs=m, cache_bytes=cache_bytes, chunk_rows=64)
+    lo, pe, ip, lp = oracle.levels(A, 0)
+    prp, pci, pva = oracle.permute(A, pe, ip)
+    budget = cache_bytes // (p_max + 1)
+    g = oracle.groups(lp, prp, budget, val_bytes=8, m=m)
+    assert np.array_equal(P.group_level_ptr.cpu().numpy(), g)
+    assert np.array_equal(P.group_row_ptr.cpu().numpy(), lp[g])
+    rp, ci, va = P.export_csr()
+    assert np.array_equal(rp.cpu().numpy(), prp)
+    assert np.array_equal(ci.cpu().numpy(), pci)
+    assert np.array_equal(va.cpu().numpy().view(np.uint64), pva.view(np.uint64))
+    # chunks never cross a group boundary and hold at most chunk_rows rows
+    cr = P.chunk_row_ptr.cpu().numpy()
+    assert cr[0] == 0 and cr[-1] == A.n and np.all(np.diff(cr) <= 64) and np.all(np.diff(cr) > 0)
+    assert set(lp[g].tolist()) <= set(cr.tolist())
+
+
+# ----------------------------------------------------------------------------- apply (a5-a7)
+def _check_powers(Yg, Yo):
+    Yg = Yg.cpu().numpy()
+    assert Yg.shape == Yo.shape
+    assert np.array_equal(Yg.view(np.uint64), Yo.view(np.uint64)), "not bit-identical to the oracle"
+    for k in range(Yo.shape[0]):
+        nrm = np.linalg.norm(Yo[k])
+        if nrm > 0:
+            assert np.linalg.norm(Yg[k] - Yo[k]) / nrm <= REL_TOL
+
+
+@pytest.mark.parametrize("name", sorted(MATRICES))
+@pytest.mark.parametrize("order", [0, 1])
+def test_apply_bit_exact(mpk, name, order):
+    make, sym = MATRICES[name]
+    A = make()
+    dA = _dev(A, mpk, sym)
+    L = mpk.build_levels(dA, 0)
+    p_max, m = 6, 2
+    P = mpk.plan(dA, L, p_max=p_max, nrhs=m, cache_bytes=20000, order=order, chunk_rows=32)
+    X = gen.vector(A.n, m, stream=81)
+    _, pe, ip, _ = oracle.levels(A, 0)
+    Xin = X if order == 0 else X[pe]
+    Yo = oracle.mpk(A, X, p_max)
+    if order == 1:
+        Yo = Yo[:, pe, :]
+    for p in (1, 3, p_max):
+        Y = _poisoned((p + 1, A.n, m))
+        P.apply(torch.from_numpy(np.ascontiguousarray(Xin)).cuda(), p, Y=Y)
+        P.sync_status()
+        _check_powers(Y, Yo[: p + 1])
+
+
+@pytest.mark.parametrize("m", [1, 2, 4, 8])
+@pytest.mark.parametrize("chunk_rows", [32, 96, 512])
+def test_apply_nrhs_and_chunks(mpk, m, chunk_rows):
+    A = gen.laplacian_3d(21, 13, 11)
+    dA = _dev(A, mpk, True)
+    L = mpk.build_levels(dA, 0)
+    P = mpk.plan(dA, L, p_max=8, nrhs=m, cache_bytes=300000, chunk_rows=chunk_rows)
+    X = gen.vector(A.n, m, stream=82)
+    Y = P.apply(torch.from_numpy(X).cuda(), 8, Y=_poisoned((9, A.n, m)))
+    P.sync_status()
+    _check_powers(Y, oracle.mpk(A, X, 8))
+
+
+def test_apply_small_config_many_groups(mpk):
+    # 64x64 5-point Laplacian, p = 4 (the small configuration), groups of single levels
+    A, p = gen.config_small()
+    dA = _dev(A, mpk, True)
+    L = mpk.build_levels(dA, 0)
+    X = gen.vector(A.n, 1, stream=1)
+    for cache in (1, 5000, 0):
+        P = mpk.plan(dA, L, p_max=p, cache_bytes=cache)
+        Y = P.apply(torch.from_numpy(X).cuda(), p, Y=_poisoned((p + 1, A.n, 1)))
+        P.sync_status()
+        _check_powers(Y, oracle.mpk(A, X, p))
+
+
+def test_apply_p31_and_p0(mpk):
+    A = gen.row_stochastic(700, 2, stream=83)
+    dA = _dev(A, mpk)
+    L = mpk.build_levels(dA, 5)
+    P = mpk.plan(dA, L, p_max=31, cache_bytes=4000, chunk_rows=32)
+    X = np.ones((A.n, 1))
+    Y = P.apply(torch.from_numpy(X).cuda(), 31)
+    P.sync_status()
+    assert torch.all(Y == 1.0)
+    Y0 = P.apply(torch.from_numpy(X).cuda(), 0)
+    assert torch.all(Y0 == 1.0) and Y0.shape == (1, A.n, 1)
+
+
+def test_identity_plan_and_comparator(mpk):
+    A = gen.laplacian_3d(19, 11, 7)
+    dA = _dev(A, mpk, True)
+    X = gen.vector(A.n, 1, stream=84)
+    Yo = oracle.mpk(A, X, 7)
+    P0 = mpk.plan(dA, None, p_max=7, chunk_rows=64)         # natural order, one group
+    assert P0.describe()["num_groups"] == 1
+    _check_powers(P0.apply(torch.from_numpy(X).cuda(), 7), Yo)
+    _check_powers(P0.spmv_powers(torch.from_numpy(X).cuda(), 7), Yo)
+    L = mpk.build_levels(dA, 0)
+    for order in (0, 1):
+        P = mpk.plan(dA, L, p_max=7, order=order, cache_bytes=50000)
+        _, pe, _, _ = oracle.levels(A, 0)
+        Xin = X if order == 0 else X[pe]
+        want = Yo if order == 0 else Yo[:, pe, :]
+        Ya = P.apply(torch.from_numpy(np.ascontiguousarray(Xin)).cuda(), 7)
+        Ys = P.spmv_powers(torch.from_numpy(np.ascontiguousarray(Xin)).cuda(), 7)
+        P.sync_status()
+        _check_powers(Ya, want)
+        _check_powers(Ys, want)
+        assert torch.equal(Ya, Ys)  # level-blocked == back-to-back, bit for bit
+
+
+def test_repeated_applies_reuse_plan(mpk):
+    A = gen.banded_random(4000, stream=85)
+    dA = _dev(A, mpk, True)
+    P = mpk.plan(dA, mpk.build_levels(dA, 0), p_max=5, cache_bytes=100000, chunk_rows=64)
+    for s in range(6):
+        X = gen.vector(A.n, 1, stream=200 + s)
+        Y = P.apply(torch.from_numpy(X).cuda(), 1 + s % 5)
+        P.sync_status()
+        _check_powers(Y, oracle.mpk(A, X, 1 + s % 5))
+
+
+def test_timeout_is_reported_and_plan_recovers(mpk):
+    A = gen.laplacian_3d(16, 16, 16)
+    dA = _dev(A, mpk, True)
+    P = mpk.plan(dA, mpk.build_levels(dA, 0), p_max=4, chunk_rows=32, cache_bytes=20000,
+                 wait_limit_ns=20_000_000)
+    X = torch.from_numpy(gen.vector(A.n, 1, stream=86)).cuda()
+    P.debug_drop_release(chunk=3, k=1)     # nothing will ever set this flag
+    P.apply(X, 4)
+    with pytest.raises(mpk.MpkError) as e:
+        P.sync_status()
+    assert e.value.status == 4
+    Y = P.apply(X, 4)                      # the next launch is unaffected
+    P.sync_status()
+    _check_powers(Y, oracle.mpk(A, X.cpu().numpy(), 4))
+
+
+def test_bad_arguments(mpk):
+    A = gen.laplacian_2d(8, 8)
+    dA = _dev(A, mpk, True)
+    L = mpk.build_levels(dA, 0)
+    with pytest.raises(mpk.MpkError):
+        mpk.plan(dA, L, p_max=0)
+    with pytest.raises(mpk.MpkError):
+        mpk.plan(dA, L, nrhs=3)
+    with pytest.raises(mpk.MpkError) as e:
+        mpk.plan(dA, L, mem_budget=1000)
+    assert e.value.status == 6
+    P = mpk.plan(dA, L, p_max=3)
+    with pytest.raises(mpk.MpkError):
+        P.apply(torch.zeros(64, dtype=torch.float64, device="cuda"), 4)
+
+
+# ----------------------------------------------------------------------------- Chebyshev (a6')
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("degree,p_max", [(0, 4), (1, 4), (13, 4), (16, 8), (7, 31)])
+def test_cheb_real_bit_exact(mpk, order, degree, p_max):
+    A = gen.xxz_chain(12, stream=87)
+    dA = _dev(A, mpk, True)
+    lo, hi = gen.gershgorin_bounds(A)
+    scale, shift = (hi - lo) / 2 * 1.01, (hi + lo) / 2
+    P = mpk.plan(dA, mpk.build_levels(dA, 0), p_max=p_max, nrhs=2, order=order, cache_bytes=30000, chunk_rows=64)
+    X = gen.vector(A.n, 2, stream=88)
+    c = gen.uniform(gen.derive_seed(89), degree + 1)
+    want = oracle.cheb(A, X, degree, c, scale=scale, shift=shift)
+    _, pe, ip, _ = oracle.levels(A, 0)
+    Xin = X if order == 0 else X[pe]
+    got = P.cheb_filter(torch.from_numpy(np.ascontiguousarray(Xin)).cuda(), degree, c, scale=scale, shift=shift)
+    P.sync_status()
+    got = got.cpu().numpy()
+    if order == 1:
+        got = got[ip]
+    assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+
+
+def test_cheb_complex_time_step(mpk):
+    A = gen.laplacian_3d(12, 10, 9)
+    dA = _dev(A, mpk, True)
+    lo, hi = gen.gershgorin_bounds(A)
+    a, c = (hi - lo) / 2 * 1.01, (hi + lo) / 2
+    dt, M = 0.5, 24
+    J = oracle.bessel_j(M, a * dt)
+    coef = np.array([J[0]] + [2 * (-1j) ** k * J[k] for k in range(1, M + 1)]) * np.exp(-1j * dt * c)
+    P = mpk.plan(dA, mpk.build_levels(dA, 0), p_max=8, nrhs=2, cache_bytes=40000)
+    psi = gen.vector(A.n, 2, stream=90)
+    want = oracle.cheb(A, psi, M, coef.real.copy(), coef.imag.copy(), scale=a, shift=c)
+    got = P.cheb_filter(torch.from_numpy(psi).cuda(), M, coef.real.copy(), coef.imag.copy(), scale=a, shift=c)
+    P.sync_status()
+    assert np.array_equal(got.cpu().numpy().view(np.uint64), want.view(np.uint64))
+    # and the step is unitary to within the expansion's truncation
+    z0 = psi[:, 0] + 1j * psi[:, 1]
+    g = got.cpu().numpy()
+    assert abs(np.linalg.norm(g[:, 0] + 1j * g[:, 1]) / np.linalg.norm(z0) - 1) < 1e-12
