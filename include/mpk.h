@@ -96,18 +96,24 @@ void mpk_levels_destroy(mpk_levels *L);
  * Plans.  A plan owns a permuted copy of A (P A P^T, entries kept in stored order, in a
  * sliced layout of 32-row slices), the level groups, the work-unit tables of the
  * level-blocked schedule for every p <= p_max, per-chunk completion flags and a vector
- * workspace.  Groups follow the greedy rule: walk the levels in order and add a level to
- * the current group while the group's bytes stay <= floor(cache_bytes / (p_max + 1)),
- * where a level costs (val_bytes + 4) * nnz + 4 * rows + 16 * nrhs * rows bytes; a level
- * over the budget is a group of its own.  Passing L = NULL plans A in its own order with
- * a single group (the unblocked reference configuration).
+ * workspace.
+ *
+ * Groups follow the greedy rule of the paper's cache blocking (Sec. 3 reuse window, Sec. 6
+ * parameter C): walk the levels in order and add a level to the current group while the
+ * group's bytes stay <= floor(cache_bytes / window); a level costs
+ * (val_bytes + 4) * nnz + 4 * rows + 16 * nrhs * rows bytes; a level over the budget is a
+ * group of its own.  The GPU executes the Lp-diagram cells (group g, power k) along lines
+ * g + 3k = const (the paper walks the diagonals g + k = const, whose cells depend on one
+ * another in turn); a group is then reused 3p lines later, so window = 3 * p_max + 1
+ * groups share the budget (the paper's window is p_m + 1).  Passing L = NULL plans A in
+ * its own order with a single group (the unblocked reference configuration).
  * ------------------------------------------------------------------------------------- */
 typedef struct {
     int32_t p_max;          /* largest power mpk_apply may request (1..31)                 */
     int32_t nrhs;           /* m: 1, 2, 4 or 8 right-hand sides per call                    */
     int64_t cache_bytes;    /* C in bytes; 0 = half of the device L2                       */
     int32_t order;          /* mpk_order of X, Y and the Chebyshev input/output             */
-    int32_t chunk_rows;     /* rows per work unit (multiple of 32); 0 = 512                 */
+    int32_t chunk_rows;     /* rows per work unit (multiple of 32); 0 = 480                 */
     int64_t wait_limit_ns;  /* bound on every device-side wait; 0 = 2 s                     */
     int64_t mem_budget;     /* bytes the plan may allocate on the device; 0 = no limit     */
 } mpk_plan_opts;
@@ -124,7 +130,8 @@ typedef struct {
     int32_t num_levels;           /* 0 for a plan without levels                         */
     int32_t num_groups;
     int32_t num_chunks;
-    int64_t group_budget_bytes;   /* floor(cache_bytes / (p_max + 1))                    */
+    int64_t group_budget_bytes;   /* floor(cache_bytes / window)                         */
+    int32_t window;               /* groups sharing the cache budget: 3 * p_max + 1      */
     int64_t cache_bytes;
     int64_t device_bytes;         /* bytes allocated by the plan                         */
     int64_t padded_entries;       /* entries of the sliced copy including padding        */

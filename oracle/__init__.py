@@ -50,8 +50,8 @@ def _L():
             lib.orc_levels.argtypes = [i32, _i32p, _i32p, i32, _i32p, _i32p, _i32p, _i32p, C.POINTER(i32)]
             lib.orc_permute.argtypes = [i32, _i32p, _i32p, _f64p, _i32p, _i32p, _i32p, _i32p, _f64p]
             lib.orc_groups.argtypes = [i32, _i32p, _i32p, i32, i32, i64, _i32p, C.POINTER(i32)]
-            lib.orc_lp_labels.argtypes = [i32, i32, _i32p]
-            lib.orc_lb_mpk.argtypes = [i32, _i32p, _i32p, _f64p, i32, _f64p, i32, i32, _i32p, _f64p]
+            lib.orc_lp_labels.argtypes = [i32, i32, i32, _i32p]
+            lib.orc_lb_mpk.argtypes = [i32, _i32p, _i32p, _f64p, i32, _f64p, i32, i32, _i32p, i32, _f64p]
             lib.orc_cheb.argtypes = [i32, _i32p, _i32p, _f64p, i32, _f64p, i32, _f64p, C.c_void_p,
                                      f64, f64, _f64p]
             lib.orc_bessel_j.argtypes = [i32, f64, _f64p]
@@ -133,23 +133,24 @@ def groups(level_ptr, perm_row_ptr, budget: int, val_bytes: int = 8, m: int = 1)
     return gp[: G.value + 1].copy()
 
 
-def lp_labels(L: int, pm: int) -> np.ndarray:
-    """Execution step of each Lp-diagram cell, shape (pm, L): row p-1, column i."""
+def lp_labels(L: int, pm: int, skew: int = 1) -> np.ndarray:
+    """Execution step of each Lp-diagram cell, shape (pm, L): row p-1, column i.
+    skew = 1 is the paper's diagonal order (Fig. 2); skew s walks lines i + s*p."""
     lab = np.empty(L * pm, np.int32)
-    _check(_L().orc_lp_labels(L, pm, lab), "lp_labels")
+    _check(_L().orc_lp_labels(L, pm, skew, lab), "lp_labels")
     return lab.reshape(pm, L)
 
 
-def lb_mpk(prp, pci, pva, X, p: int, group_rows) -> np.ndarray:
-    """Serial level-blocked MPK on a permuted matrix, Lp-diagram order (Sec. 3)."""
+def lb_mpk(prp, pci, pva, X, p: int, group_rows, skew: int = 1) -> np.ndarray:
+    """Serial level-blocked MPK on a permuted matrix, Lp-diagram order (Sec. 3), lines g + skew*k."""
     prp = np.ascontiguousarray(prp, np.int32)
     n = prp.size - 1
     X = _block(X, n)
     m = X.shape[1]
     gr = np.ascontiguousarray(group_rows, np.int32)
-    Y = np.empty((p + 1, n, m), np.float64)
+    Y = np.full((p + 1, n, m), np.nan)  # a cell computed too early reads NaN
     _check(_L().orc_lb_mpk(n, prp, np.ascontiguousarray(pci, np.int32), np.ascontiguousarray(pva, np.float64),
-                           m, X, p, gr.size - 1, gr, Y), "lb_mpk")
+                           m, X, p, gr.size - 1, gr, int(skew), Y), "lb_mpk")
     return Y
 
 

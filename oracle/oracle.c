@@ -215,17 +215,21 @@ int orc_groups(int32_t nlevels, const int32_t *level_ptr, const int32_t *rp, int
 
 /*
  * Execution order of the Lp diagram (Sec. 3, Fig. 2): cells (i, p) with level i in
- * 0..L-1 and power p in 1..pm are visited diagonal by diagonal, i + p increasing, and
- * inside one diagonal from bottom-right to top-left, i.e. p ascending.
- * labels[(p-1)*L + i] receives the 0-based step at which cell (i, p) runs.
+ * 0..L-1 and power p in 1..pm are visited line by line, i + skew*p increasing, and inside
+ * one line from bottom-right to top-left, i.e. p ascending.  skew = 1 gives the paper's
+ * diagonals i + p = const.  Every line with skew >= 1 visits (i-1, p-1), (i, p-1) and
+ * (i+1, p-1) before (i, p), since those lie on earlier lines (or, for skew = 1, earlier on
+ * the same line).  skew = 0 visits all powers of level 0, then of level 1, ...: that order
+ * breaks the rule ((i, 2) runs before (i+1, 1)) and exists so that tests can show a wrong
+ * order being caught.  labels[(p-1)*L + i] receives the 0-based step of cell (i, p).
  */
-int orc_lp_labels(int32_t L, int32_t pm, int32_t *labels)
+int orc_lp_labels(int32_t L, int32_t pm, int32_t skew, int32_t *labels)
 {
-    if (L < 0 || pm < 0) return ORC_EINVAL;
+    if (L < 0 || pm < 0 || skew < 0) return ORC_EINVAL;
     int32_t step = 0;
-    for (int32_t d = 1; d <= L - 1 + pm; ++d)     /* d = i + p */
+    for (int32_t d = skew; d <= L - 1 + skew * pm; ++d)     /* d = i + skew * p */
         for (int32_t p = 1; p <= pm; ++p) {
-            const int32_t i = d - p;
+            const int32_t i = d - skew * p;
             if (i >= 0 && i < L) labels[(p - 1) * L + i] = step++;
         }
     return ORC_OK;
@@ -233,22 +237,23 @@ int orc_lp_labels(int32_t L, int32_t pm, int32_t *labels)
 
 /*
  * Serial level-blocked MPK (Sec. 3): the groups of the permuted matrix are promoted
- * power by power in the Lp-diagram order of orc_lp_labels, computing every row of a
- * cell with the same row body as orc_mpk.  Because no row changes its summation
- * order, the result equals back-to-back SpMV on the permuted matrix bit for bit; a
- * cell that ran before its dependencies (groups g-1, g, g+1 at power p-1) would read
- * unset values.  Y (p+1)*n*m in permuted order, Y[0] = X (permuted order).
- * group_rows[G+1] are row offsets of the groups.
+ * power by power in the Lp-diagram order of orc_lp_labels (with the given skew),
+ * computing every row of a cell with the same row body as orc_mpk.  Because no row
+ * changes its summation order, the result equals back-to-back SpMV on the permuted matrix
+ * bit for bit; a cell that ran before its dependencies (groups g-1, g, g+1 at power p-1)
+ * would read values that are not yet set.  Y (p+1)*n*m in permuted order, Y[0] = X
+ * (permuted order).  group_rows[G+1] are row offsets of the groups.  Y[1..p] are only
+ * written, never cleared, so a caller that fills them with NaN sees every early read.
  */
 int orc_lb_mpk(int32_t n, const int32_t *rp, const int32_t *ci, const double *va, int32_t m,
-               const double *X, int32_t p, int32_t G, const int32_t *group_rows, double *Y)
+               const double *X, int32_t p, int32_t G, const int32_t *group_rows, int32_t skew, double *Y)
 {
-    if (n < 0 || m < 1 || p < 0 || G < 0) return ORC_EINVAL;
+    if (n < 0 || m < 1 || p < 0 || G < 0 || skew < 0) return ORC_EINVAL;
     const int64_t nm = (int64_t)n * m;
     memcpy(Y, X, sizeof(double) * (size_t)nm);
-    for (int32_t d = 1; d <= G - 1 + p; ++d)
+    for (int32_t d = skew; d <= G - 1 + skew * p; ++d)
         for (int32_t k = 1; k <= p; ++k) {
-            const int32_t g = d - k;
+            const int32_t g = d - skew * k;
             if (g < 0 || g >= G) continue;
             const double *xin = Y + (int64_t)(k - 1) * nm;
             double *yout = Y + (int64_t)k * nm;

@@ -55,7 +55,8 @@ class _Opts(C.Structure):
 class _Desc(C.Structure):
     _fields_ = [("n", C.c_int32), ("nnz", C.c_int32), ("nrhs", C.c_int32), ("p_max", C.c_int32),
                 ("order", C.c_int32), ("num_levels", C.c_int32), ("num_groups", C.c_int32),
-                ("num_chunks", C.c_int32), ("group_budget_bytes", C.c_int64), ("cache_bytes", C.c_int64),
+                ("num_chunks", C.c_int32), ("group_budget_bytes", C.c_int64), ("window", C.c_int32),
+                ("cache_bytes", C.c_int64),
                 ("device_bytes", C.c_int64), ("padded_entries", C.c_int64),
                 ("group_level_ptr_dev", C.c_void_p), ("group_row_ptr_dev", C.c_void_p),
                 ("chunk_row_ptr_dev", C.c_void_p), ("perm_dev", C.c_void_p)]

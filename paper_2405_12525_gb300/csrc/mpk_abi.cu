@@ -109,6 +109,7 @@ extern "C" mpk_status mpk_plan_describe(const mpk_plan_t *P, mpk_plan_desc *d) {
     d->num_groups = p.num_groups;
     d->num_chunks = p.num_chunks;
     d->group_budget_bytes = p.group_budget;
+    d->window = p.window;
     d->cache_bytes = p.cache_bytes;
     d->device_bytes = p.arena.bytes;
     d->padded_entries = p.padded;
@@ -158,6 +159,8 @@ static KArgs base_args(Plan &P, int32_t p) {
     a.chunk_row = P.chunk_row;
     a.chunk_slice = P.chunk_slice;
     a.dep = P.dep;
+    a.dep_ranges = P.dep_ranges;
+    a.chunk_rec = P.chunk_rec;
     a.n = P.n;
     a.nchunks = P.num_chunks;
     a.units = P.units + P.unit_off[p];

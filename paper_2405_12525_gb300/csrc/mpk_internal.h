@@ -88,6 +88,19 @@ struct Levels {
 
 // Arguments of the level-blocked kernel, passed by value.
 constexpr int kMaxP = 31;
+// padded entries of one chunk that the kernel stages in shared memory (per buffer)
+constexpr int kStageEntries = 4096;
+// dependency ranges kept per chunk (exact sets compressed to this many index ranges)
+constexpr int kDepRanges = 4;
+// compute warps of the level-blocked kernel; the default chunk is one 32-row slice per warp
+constexpr int kCompWarps = 15;
+constexpr int kDefaultChunkRows = 32 * kCompWarps;
+// The level-blocked kernel walks the Lp diagram along lines g + kSlotSkew * k = const.  With
+// skew 1 (the paper's diagonals) the cells of one line form a dependency chain; with skew 3
+// every dependency of a cell lies at least two lines back, so the cells in flight on the
+// GPU do not wait on each other.  A group is then reused kSlotSkew * p lines later, so the
+// cache budget is shared by kSlotSkew * p_max + 1 groups.
+constexpr int kSlotSkew = 3;
 struct KArgs {
     // sliced matrix copy (plan order)
     const double *val;
@@ -97,6 +110,8 @@ struct KArgs {
     const int32_t *chunk_row;
     const int32_t *chunk_slice;
     const int2 *dep;
+    const int4 *dep_ranges;  // 2 x int4 per chunk: kDepRanges (lo, hi) pairs
+    const int4 *chunk_rec;   // 4 x int4 per chunk: rows, slices, entries, ranges
     int32_t n;
     int32_t nchunks;
     // schedule for this launch
@@ -132,6 +147,7 @@ struct Plan {
     int32_t num_levels = 0, num_groups = 0, num_chunks = 0, num_slices = 0;
     int32_t chunk_rows = 512;
     int64_t cache_bytes = 0, group_budget = 0, padded = 0, wait_ns = 0;
+    int32_t window = 0;  // groups sharing the cache budget: kSlotSkew * p_max + 1
     bool identity = false;
     // device data (owned by arena)
     double *val = nullptr;
@@ -140,7 +156,9 @@ struct Plan {
     int32_t *rowlen = nullptr;
     int32_t *chunk_row = nullptr;
     int32_t *chunk_slice = nullptr;
-    int2 *dep = nullptr;
+    int2 *dep = nullptr;         // hull of each chunk's dependencies
+    int4 *dep_ranges = nullptr;  // exact dependencies as kDepRanges index ranges
+    int4 *chunk_rec = nullptr;   // per-chunk records read by the kernel's control warp
     int32_t *group_level_ptr = nullptr;
     int32_t *group_row_ptr = nullptr;
     int32_t *perm = nullptr;   // owned copy (NULL for identity)

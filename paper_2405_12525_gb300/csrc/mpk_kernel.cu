@@ -6,14 +6,19 @@
 // row body therefore spends exactly one DFMA per stored entry and right-hand side: one
 // thread owns one row and accumulates its entries sequentially in stored order (no
 // shuffle-tree reduction, which would add FP64 additions).  The matrix copy is sliced by
-// 32 rows (entry j of lane l at slice_ptr + 32 j + l) so that a warp's loads of entry j
-// are contiguous.  The result equals the oracle's fma-per-term row sums bit for bit.
+// 32 rows (entry j of lane l at slice_ptr + 32 j + l), so a warp's entries j are
+// contiguous and a chunk's entries form one contiguous, 128-byte aligned range that the
+// kernel stages into shared memory with one bulk (TMA) copy per array.  All x gathers of
+// a row are issued before its FMAs.  The result equals the oracle's fma-per-term row sums
+// bit for bit.
 #include "mpk_internal.h"
 
 namespace mpk {
 
-constexpr int kBS = 256;            // threads per block (8 warps)
-constexpr int kWarps = kBS / 32;
+constexpr int kBS = 32 * (1 + kCompWarps);  // level-blocked kernel: 1 control warp + compute warps
+constexpr int kSpmvBS = 256;        // threads per block of the plain SpMV kernel
+constexpr int kStageBytes = kStageEntries * 12;          // one buffer: values + columns
+constexpr int kSmemBytes = 2 * kStageBytes;             // double buffered
 
 enum Mode { MODE_PLAN = 0, MODE_SCATTER = 1, MODE_CHEB = 2 };
 
@@ -31,36 +36,91 @@ __device__ __forceinline__ uint64_t globaltimer() {
     return t;
 }
 
-// acc[i] = sum_j val[j] * x[col[j]*M + i] over row r's entries, in stored order
-template <int M>
-__device__ __forceinline__ void row_sum(const double *__restrict__ val, const int32_t *__restrict__ col,
-                                        int64_t base, int len, const double *x, double (&acc)[M]) {
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx_only(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// global -> shared bulk copy (TMA, untiled); addresses 16-byte aligned, bytes % 16 == 0
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Entries whose x loads are issued together before their FMAs.
+template <int M> struct Batch {
+    static constexpr int B = M == 1 ? 8 : (M == 2 ? 4 : (M == 4 ? 2 : 1));
+};
+
+// acc[i] = sum_j val[j] * x[col[j]*M + i] over a row's entries, in stored order.  Entry j
+// of the row is at val[off + 32 j] / col[off + 32 j] (global or shared memory).
+template <int M, int B, class VP, class CP>
+__device__ __forceinline__ void row_sum(VP val, CP col, int64_t off, int len, const double *x, double (&acc)[M]) {
 #pragma unroll
     for (int i = 0; i < M; ++i) acc[i] = 0.0;
-    int j = 0;
-    for (; j + 1 < len; j += 2) {   // two entries per trip: loads of j+1 overlap the FMAs of j
-        const double v0 = __ldg(val + base + 32 * (int64_t)j);
-        const double v1 = __ldg(val + base + 32 * (int64_t)(j + 1));
-        const int32_t c0 = __ldg(col + base + 32 * (int64_t)j);
-        const int32_t c1 = __ldg(col + base + 32 * (int64_t)(j + 1));
-        double x0[M], x1[M];
+    for (int j0 = 0; j0 < len; j0 += B) {
+        double v[B];
+        int32_t c[B];
 #pragma unroll
-        for (int i = 0; i < M; ++i) {
-            x0[i] = x[(int64_t)c0 * M + i];
-            x1[i] = x[(int64_t)c1 * M + i];
+        for (int b = 0; b < B; ++b) {
+            if (j0 + b < len) {
+                v[b] = val[off + 32 * (int64_t)(j0 + b)];
+                c[b] = col[off + 32 * (int64_t)(j0 + b)];
+            } else {
+                v[b] = 0.0;
+                c[b] = 0;
+            }
         }
+        double xv[B][M];
 #pragma unroll
-        for (int i = 0; i < M; ++i) acc[i] = fma(v0, x0[i], acc[i]);
+        for (int b = 0; b < B; ++b)
 #pragma unroll
-        for (int i = 0; i < M; ++i) acc[i] = fma(v1, x1[i], acc[i]);
-    }
-    if (j < len) {
-        const double v0 = __ldg(val + base + 32 * (int64_t)j);
-        const int32_t c0 = __ldg(col + base + 32 * (int64_t)j);
+            for (int i = 0; i < M; ++i) xv[b][i] = (j0 + b < len) ? x[(int64_t)c[b] * M + i] : 0.0;
 #pragma unroll
-        for (int i = 0; i < M; ++i) acc[i] = fma(v0, x[(int64_t)c0 * M + i], acc[i]);
+        for (int b = 0; b < B; ++b)
+            if (j0 + b < len) {
+#pragma unroll
+                for (int i = 0; i < M; ++i) acc[i] = fma(v[b], xv[b][i], acc[i]);
+            }
     }
 }
+
+// read-only global views (immutable matrix copy)
+struct GVal {
+    const double *p;
+    __device__ __forceinline__ double operator[](int64_t i) const { return __ldg(p + i); }
+};
+struct GCol {
+    const int32_t *p;
+    __device__ __forceinline__ int32_t operator[](int64_t i) const { return __ldg(p + i); }
+};
 
 // Epilogue of one row at local power k: store into the plan-order slot, optionally into
 // the original-order output, or advance the Chebyshev recurrence.
@@ -117,111 +177,273 @@ __device__ __forceinline__ void row_epilogue(const KArgs &a, int k, int64_t r, c
 // dependency of a unit (chunks holding the rows it reads, at power k-1) lies on an earlier
 // diagonal or earlier in the same one, so it has a smaller ticket: the unit holding the
 // smallest unfinished ticket can always run, whichever blocks are resident, and the
-// schedule cannot deadlock.  A finished unit publishes flags[k][c] = epoch (release);
-// a unit waits until flags[k-1][lo..hi] all equal the epoch (acquire).  Each block claims
-// its next ticket while it waits for the current one.  Waits are bounded by
-// a.wait_ns (globaltimer); on expiry the block records the epoch and MPK_ERR_TIMEOUT in
-// a.err and all blocks drain out.  The last block to exit resets the ticket.
-template <int M, int MODE>
-__global__ void __launch_bounds__(kBS) k_mpk(const KArgs a) {
-    __shared__ int s_unit[2];
-    __shared__ int2 s_dep[2];
-    __shared__ int s_row[2][2];
-    __shared__ int s_slice[2];
-    __shared__ int s_abort;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// schedule cannot deadlock.  A finished unit publishes flags[k][c] = epoch (release); a
+// unit waits until the flags of its dependency ranges at power k-1 equal the epoch
+// (acquire).
+//
+// Warp roles.  Warp 0 (control) claims units, stages each unit's matrix entries into one
+// of two shared-memory slots with bulk (TMA) copies and polls the unit's dependencies;
+// warps 1..kCompWarps (compute) compute rows, and the last of them to finish a unit
+// publishes its completion flag.  Slot b has two mbarriers: full[b] completes when the
+// entries have landed and the dependencies are met, empty[b] when every compute warp is
+// done with the slot.  The control warp prepares unit i+1 while unit i is computed; its
+// claims run two units ahead (the ticket of unit i+2 and the chunk record of unit i+1 are
+// fetched while unit i is handled), so only the dependency poll is on its critical path.
+// A block processes its tickets in claim order and claims are increasing, so the block
+// holding the smallest unfinished ticket is working on it: the schedule stays deadlock
+// free with tickets claimed ahead.
+// When no ticket is left, or a wait fails, the control warp stores the number of units it
+// handed over in s_final; compute warps stop at that unit.  Every wait is bounded by
+// a.wait_ns (globaltimer); on expiry the control warp records the epoch and
+// MPK_ERR_TIMEOUT in a.err and all blocks drain out; no block exits with a bulk copy of
+// its own still in flight.  The last block to exit resets the ticket.
+struct UnitInfo {
+    int unit;         // chunk << 5 | k
+    int row0, row1, slice0;
+    int ecount;       // padded entries of the chunk
+    int staged;       // entries were copied to the slot's shared buffer
+    long long ebase;  // first entry of the chunk in the sliced copy
+};
 
-    auto claim = [&](int slot) {
-        const unsigned int t = atomicAdd(a.ticket, 1u);
-        if ((int64_t)t >= a.nunits) {
-            s_unit[slot] = -1;
-            return;
+__device__ __forceinline__ bool timed_out(uint64_t t0, int64_t limit) { return globaltimer() - t0 > (uint64_t)limit; }
+
+template <int M, int MODE>
+__device__ __forceinline__ void compute_unit(const KArgs &a, const UnitInfo &u, const double *sval,
+                                             const int32_t *scol, int cwarp, int lane) {
+    const int k = u.unit & 31;
+    const int nsl = (u.row1 - u.row0 + 31) >> 5;
+    const double *xin = (k == 1 && a.k_offset == 0)
+                            ? a.x0
+                            : a.ybase + (int64_t)((a.k_offset + k - 1) % a.ring) * a.ystride;
+    for (int sl = cwarp; sl < nsl; sl += kCompWarps) {
+        const int64_t r = (int64_t)u.row0 + 32 * sl + lane;
+        if (r < u.row1) {
+            const int64_t off = __ldg(a.slice_ptr + u.slice0 + sl) - u.ebase + lane;
+            const int len = __ldg(a.rowlen + r);
+            double w[M];
+            if (u.staged)
+                row_sum<M, Batch<M>::B>(sval, scol, off, len, xin, w);
+            else
+                row_sum<M, 1>(GVal{a.val + u.ebase}, GCol{a.col + u.ebase}, off, len, xin, w);
+            row_epilogue<M, MODE>(a, k, r, w, xin);
+            if (k == 1 && a.y0copy) {
+#pragma unroll
+                for (int i = 0; i < M; ++i) a.y0copy[r * M + i] = a.x0[r * M + i];
+            }
         }
-        const int u = __ldg(a.units + t);
-        const int c = u >> 5;
-        s_unit[slot] = u;
-        s_dep[slot] = __ldg(a.dep + c);
-        s_row[slot][0] = __ldg(a.chunk_row + c);
-        s_row[slot][1] = __ldg(a.chunk_row + c + 1);
-        s_slice[slot] = __ldg(a.chunk_slice + c);
-    };
+    }
+}
+
+// all lanes of the control warp: true when every flag of the unit's ranges equals epoch
+__device__ __forceinline__ bool deps_ready(const KArgs &a, int k, const int (&lo)[kDepRanges],
+                                           const int (&len)[kDepRanges], int total, int lane) {
+    const int32_t *f = a.flags + (int64_t)(k - 1) * a.nchunks;
+    bool ok = true;
+    for (int v0 = 0; v0 < total; v0 += 128) {
+        int got[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int v = v0 + 32 * q + lane;
+            int idx = -1;
+            if (v < total) {
+#pragma unroll
+                for (int r = 0; r < kDepRanges; ++r) {
+                    if (idx < 0 && v < len[r]) idx = lo[r] + v;
+                    if (idx < 0) v -= len[r];
+                }
+            }
+            got[q] = idx >= 0 ? ld_relaxed(f + idx) : a.epoch;
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ok = ok && got[q] == a.epoch;
+    }
+    return __all_sync(0xffffffffu, ok);
+}
+
+template <int M, int MODE>
+__global__ void __launch_bounds__(kBS, 2) k_mpk(const KArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t s_full[2];
+    __shared__ __align__(8) uint64_t s_empty[2];
+    __shared__ UnitInfo s_u[2];
+    __shared__ volatile int s_final;  // units handed over in total; -1 while the control warp runs
+    __shared__ int s_done[2];         // compute warps finished with the slot's unit
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double *const sval0 = reinterpret_cast<double *>(smem);
+    int32_t *const scol0 = reinterpret_cast<int32_t *>(smem + 2 * kStageEntries * 8);
 
     if (tid == 0) {
-        s_abort = 0;
-        claim(0);
+        s_final = -1;
+        s_done[0] = 0;
+        s_done[1] = 0;
+        mbar_init(&s_full[0], 1);
+        mbar_init(&s_full[1], 1);
+        mbar_init(&s_empty[0], kCompWarps);
+        mbar_init(&s_empty[1], kCompWarps);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    int cur = 0;
-    while (true) {
-        const int u = s_unit[cur];
-        if (u < 0) break;
-        const int k = u & 31, c = u >> 5;
-        if (tid == 32) claim(cur ^ 1);
-        if (k > 1 && warp == 0) {
-            // wait until the chunks [lo, hi] have finished power k-1
-            const int32_t *f = a.flags + (int64_t)(k - 1) * a.nchunks;
-            int lo = s_dep[cur].x;
-            const int hi = s_dep[cur].y;
-            const uint64_t t0 = globaltimer();
-            bool failed = false;
-            while (true) {
-                int first_bad = hi + 1;
-                for (int i = lo + lane; i <= hi; i += 32)
-                    if (ld_relaxed(f + i) != a.epoch) {
-                        first_bad = i;
-                        break;
-                    }
+
+    if (warp == 0) {
+        // ------------------------------------------------------------------ control warp
+        const int32_t *rec = reinterpret_cast<const int32_t *>(a.chunk_rec);
+        bool slot_busy[2] = {false, false};  // a handed-over unit may still be computed
+        int slot_use[2] = {0, 0};            // phase index (i >> 1) of that hand-over
+        bool aborted = false;
+        auto record_timeout = [&]() {
+            if (lane == 0 && atomicExch(a.err, a.epoch) != a.epoch) st_relaxed(a.err + 1, (int)MPK_ERR_TIMEOUT);
+        };
+        auto unit_at = [&](unsigned int t) -> int { return (int64_t)t < a.nunits ? __ldg(a.units + t) : -1; };
+        // claims run ahead: u_cur (record in lanes), u_nxt, ticket t_nn of the unit after
+        int u_cur = -1, u_nxt = -1;
+        unsigned int t_nn = 0;
+        if (lane == 0) {
+            const unsigned int t0 = atomicAdd(a.ticket, 1u);
+            const unsigned int t1 = atomicAdd(a.ticket, 1u);
+            t_nn = atomicAdd(a.ticket, 1u);
+            u_cur = unit_at(t0);
+            u_nxt = unit_at(t1);
+        }
+        u_cur = __shfl_sync(0xffffffffu, u_cur, 0);
+        int r_cur = (u_cur >= 0 && lane < 16) ? __ldg(rec + 16 * (int64_t)(u_cur >> 5) + lane) : 0;
+        int i = 0;
+        for (;; ++i) {
+            if (u_cur < 0) break;  // no more work
+            const int b = i & 1;
+            // prefetch: record of the next unit, unit after next, next ticket
+            const int un = __shfl_sync(0xffffffffu, u_nxt, 0);
+            const int r_nxt = (un >= 0 && lane < 16) ? __ldg(rec + 16 * (int64_t)(un >> 5) + lane) : 0;
+            int u_nn = -1;
+            unsigned int t_nnn = t_nn;
+            if (lane == 0) {
+                u_nn = unit_at(t_nn);
+                if (u_nn >= 0) t_nnn = atomicAdd(a.ticket, 1u);
+            }
+            // current unit
+            UnitInfo u;
+            u.unit = u_cur;
+            u.row0 = __shfl_sync(0xffffffffu, r_cur, 0);
+            u.row1 = __shfl_sync(0xffffffffu, r_cur, 1);
+            u.slice0 = __shfl_sync(0xffffffffu, r_cur, 2);
+            u.ecount = __shfl_sync(0xffffffffu, r_cur, 3);
+            u.ebase = (long long)(unsigned int)__shfl_sync(0xffffffffu, r_cur, 4) |
+                      ((long long)__shfl_sync(0xffffffffu, r_cur, 5) << 32);
+            u.staged = __shfl_sync(0xffffffffu, r_cur, 6);
+            int dlo[kDepRanges], dlen[kDepRanges];
+            int total = 0;
 #pragma unroll
-                for (int d = 16; d > 0; d >>= 1) first_bad = min(first_bad, __shfl_xor_sync(0xffffffffu, first_bad, d));
-                if (first_bad > hi) break;
-                lo = first_bad;
-                const bool stop = ld_relaxed(a.err) == a.epoch || globaltimer() - t0 > (uint64_t)a.wait_ns;
-                if (__any_sync(0xffffffffu, stop)) {
-                    failed = true;
+            for (int r = 0; r < kDepRanges; ++r) {
+                dlo[r] = __shfl_sync(0xffffffffu, r_cur, 8 + 2 * r);
+                dlen[r] = max(0, __shfl_sync(0xffffffffu, r_cur, 9 + 2 * r) - dlo[r] + 1);
+                total += dlen[r];
+            }
+            // slot b held unit i-2: wait until it is computed before reusing the slot
+            if (slot_busy[b]) {
+                const uint64_t t0 = globaltimer();
+                bool ok;
+                while (!(ok = mbar_try_wait(&s_empty[b], slot_use[b] & 1)))
+                    if (timed_out(t0, a.wait_ns)) break;
+                if (!ok) {
+                    record_timeout();
+                    aborted = true;
                     break;
                 }
-                __nanosleep(128);
+                slot_busy[b] = false;
             }
-            if (failed) {
+            // stage the entries
+            if (lane == 0) {
+                s_u[b] = u;
+                if (u.staged) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_expect_tx_only(&s_full[b], (uint32_t)u.ecount * 12u);
+                    bulk_g2s(sval0 + b * kStageEntries, a.val + u.ebase, (uint32_t)u.ecount * 8u, &s_full[b]);
+                    bulk_g2s(scol0 + b * kStageEntries, a.col + u.ebase, (uint32_t)u.ecount * 4u, &s_full[b]);
+                }
+            }
+            // dependencies of unit i
+            const int k = u.unit & 31;
+            if (k > 1) {
+                const uint64_t t0 = globaltimer();
+                while (!deps_ready(a, k, dlo, dlen, total, lane)) {
+                    const bool stop = ld_relaxed(a.err) == a.epoch || timed_out(t0, a.wait_ns);
+                    if (__any_sync(0xffffffffu, stop)) {
+                        aborted = true;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+            }
+            if (aborted) {
+                // unit i is not handed over: the compute warps stop before it.  Complete the
+                // slot's phase so that its bulk copy can be waited for, then wait for it.
+                record_timeout();
                 if (lane == 0) {
-                    // first block to give up in this launch records the timeout
-                    if (atomicExch(a.err, a.epoch) != a.epoch) st_relaxed(a.err + 1, (int)MPK_ERR_TIMEOUT);
-                    s_abort = 1;
+                    s_final = i;
+                    mbar_arrive(&s_full[b]);
                 }
-            } else {
-                __threadfence();  // acquire: order the flag reads before the block's data reads
+                if (u.staged) {
+                    const uint64_t t1 = globaltimer();
+                    while (!mbar_try_wait(&s_full[b], (i >> 1) & 1))
+                        if (timed_out(t1, a.wait_ns)) break;
+                }
+                break;
+            }
+            fence_acq_rel_gpu();  // acquire: flags before the compute warps' reads (via full[b])
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s_full[b]);
+            slot_busy[b] = true;
+            slot_use[b] = i >> 1;
+            // rotate the claim pipeline
+            u_cur = un;
+            r_cur = r_nxt;
+            u_nxt = u_nn;
+            t_nn = t_nnn;
+        }
+        if (lane == 0 && s_final < 0) s_final = i;  // units 0..i-1 were handed over
+    } else {
+        // ------------------------------------------------------------------ compute warps
+        const int cw = warp - 1;
+        for (int i = 0;; ++i) {
+            const int b = i & 1;
+            const uint64_t t0 = globaltimer();
+            bool got = false, stop = false;
+            while (true) {
+                if (mbar_try_wait(&s_full[b], (i >> 1) & 1)) {
+                    got = true;
+                    break;
+                }
+                const int fin = s_final;
+                if (fin >= 0 && i >= fin) {
+                    stop = true;
+                    break;
+                }
+                if (timed_out(t0, 2 * a.wait_ns + 100000000LL)) break;
+            }
+            if (got) {
+                const int fin = s_final;  // set before the hand-over of an aborted unit
+                if (fin >= 0 && i >= fin) stop = true;
+            }
+            if (stop) break;
+            if (!got) {  // the control warp gave no sign of life: give up
+                if (lane == 0 && atomicExch(a.err, a.epoch) != a.epoch) st_relaxed(a.err + 1, (int)MPK_ERR_TIMEOUT);
+                break;
+            }
+            const UnitInfo u = s_u[b];
+            compute_unit<M, MODE>(a, u, sval0 + b * kStageEntries, scol0 + b * kStageEntries, cw, lane);
+            __syncwarp();
+            if (lane == 0) {
+                // the last compute warp to finish the unit publishes it (release at gpu scope
+                // after the other warps' stores were ordered at block scope)
+                __threadfence_block();
+                if (atomicAdd(&s_done[b], 1) == kCompWarps - 1) {
+                    s_done[b] = 0;
+                    fence_acq_rel_gpu();
+                    if (u.unit != a.drop_unit)
+                        st_relaxed(a.flags + (int64_t)(u.unit & 31) * a.nchunks + (u.unit >> 5), a.epoch);
+                }
+                mbar_arrive(&s_empty[b]);
             }
         }
-        __syncthreads();
-        if (s_abort) break;
-
-        // ---- rows of chunk c at power k
-        const int r0 = s_row[cur][0], r1 = s_row[cur][1], sl0 = s_slice[cur];
-        const int nsl = (r1 - r0 + 31) >> 5;
-        // input block: power (k_offset + k - 1); the very first power reads x0
-        const double *xin = (k == 1 && a.k_offset == 0)
-                                ? a.x0
-                                : a.ybase + (int64_t)((a.k_offset + k - 1) % a.ring) * a.ystride;
-        for (int sl = warp; sl < nsl; sl += kWarps) {
-            const int64_t r = (int64_t)r0 + 32 * sl + lane;
-            if (r < r1) {
-                const int64_t base = __ldg(a.slice_ptr + sl0 + sl) + lane;
-                const int len = __ldg(a.rowlen + r);
-                double w[M];
-                row_sum<M>(a.val, a.col, base, len, xin, w);
-                row_epilogue<M, MODE>(a, k, r, w, xin);
-                if (k == 1 && a.y0copy) {
-#pragma unroll
-                    for (int i = 0; i < M; ++i) a.y0copy[r * M + i] = a.x0[r * M + i];
-                }
-            }
-        }
-        __syncthreads();
-        if (tid == 0 && u != a.drop_unit) {
-            __threadfence();  // release: the block's stores before the flag
-            st_relaxed(a.flags + (int64_t)k * a.nchunks + c, a.epoch);
-        }
-        cur ^= 1;
     }
     // ---- exit: the last block resets the ticket for the next launch on the stream
     __syncthreads();
@@ -237,26 +459,27 @@ __global__ void __launch_bounds__(kBS) k_mpk(const KArgs a) {
 }
 
 // ----------------------------------------------------------------------------- K-SpMV
-// One plain SpMV over the plan's sliced copy: y = A x (plan order), same row body.
-// One warp per slice.  Optionally also writes yorig[perm[r]].
+// One plain SpMV over the plan's sliced copy: y = A x (plan order), same row body with
+// direct (read-only cached) loads of the entries.  Blocks walk chunks, warps walk the
+// chunk's slices.  Optionally also writes yorig[perm[r]].
 template <int M>
-__global__ void __launch_bounds__(kBS) k_spmv(const double *__restrict__ val, const int32_t *__restrict__ col,
-                                              const int64_t *__restrict__ slice_ptr,
-                                              const int32_t *__restrict__ rowlen, const int32_t *__restrict__ chunk_row,
-                                              const int32_t *__restrict__ chunk_slice, int32_t nchunks,
-                                              const double *x, double *y, double *yorig,
-                                              const int32_t *__restrict__ perm) {
+__global__ void __launch_bounds__(kSpmvBS) k_spmv(const double *__restrict__ val, const int32_t *__restrict__ col,
+                                                  const int64_t *__restrict__ slice_ptr,
+                                                  const int32_t *__restrict__ rowlen,
+                                                  const int32_t *__restrict__ chunk_row,
+                                                  const int32_t *__restrict__ chunk_slice, int32_t nchunks,
+                                                  const double *x, double *y, double *yorig,
+                                                  const int32_t *__restrict__ perm) {
     const int lane = threadIdx.x & 31;
-    // blocks walk chunks; warps walk the chunk's slices
     for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const int r0 = chunk_row[c], r1 = chunk_row[c + 1], sl0 = chunk_slice[c];
         const int nsl = (r1 - r0 + 31) >> 5;
-        for (int sl = threadIdx.x >> 5; sl < nsl; sl += kWarps) {
+        for (int sl = threadIdx.x >> 5; sl < nsl; sl += kSpmvBS / 32) {
             const int64_t r = (int64_t)r0 + 32 * sl + lane;
             if (r < r1) {
-                const int64_t base = slice_ptr[sl0 + sl] + lane;
+                const int64_t off = slice_ptr[sl0 + sl] + lane;
                 double w[M];
-                row_sum<M>(val, col, base, rowlen[r], x, w);
+                row_sum<M, Batch<M>::B>(GVal{val}, GCol{col}, off, rowlen[r], x, w);
 #pragma unroll
                 for (int i = 0; i < M; ++i) y[r * M + i] = w[i];
                 if (yorig) {
@@ -342,13 +565,14 @@ static void *select_mpk(int mode, int m) {
 
 int occupancy_grid(int mode, int m) {
     static int cache[3][9] = {};
-    const int mi = m;
-    if (cache[mode][mi]) return cache[mode][mi];
+    if (cache[mode][m]) return cache[mode][m];
+    void *fn = select_mpk(mode, m);
+    MPK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
     int per_sm = 0;
-    MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_mpk(mode, m), kBS, 0));
-    if (per_sm < 1) per_sm = 1;
-    cache[mode][mi] = per_sm * device_sms();
-    return cache[mode][mi];
+    MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBS, kSmemBytes));
+    if (per_sm < 1) fail(MPK_ERR_CUDA, "level-blocked kernel cannot be resident (occupancy 0)");
+    cache[mode][m] = per_sm * device_sms();
+    return cache[mode][m];
 }
 
 void launch_mpk(const Plan &P, KArgs &a, int mode, cudaStream_t s) {
@@ -357,7 +581,7 @@ void launch_mpk(const Plan &P, KArgs &a, int mode, cudaStream_t s) {
     if ((int64_t)grid > a.nunits) grid = (int)a.nunits;
     void *fn = select_mpk(mode, P.m);
     void *args[] = {&a};
-    MPK_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(kBS), args, 0, s));
+    MPK_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(kBS), args, kSmemBytes, s));
 }
 
 void launch_spmv(const Plan &P, const double *x, double *y, double *yorig, int64_t orig_off, cudaStream_t s) {
@@ -366,7 +590,7 @@ void launch_spmv(const Plan &P, const double *x, double *y, double *yorig, int64
     double *yo = yorig ? yorig + orig_off : nullptr;
 #define L(MM)                                                                                                 \
     case MM:                                                                                                  \
-        k_spmv<MM><<<grid, kBS, 0, s>>>(P.val, P.col, P.slice_ptr, P.rowlen, P.chunk_row, P.chunk_slice,     \
+        k_spmv<MM><<<grid, kSpmvBS, 0, s>>>(P.val, P.col, P.slice_ptr, P.rowlen, P.chunk_row, P.chunk_slice,     \
                                         P.num_chunks, x, y, yo, P.perm);                                      \
         break;
     switch (P.m) {

@@ -32,16 +32,13 @@ __global__ void k_chunk_of_row(const int32_t *chunk_row, int32_t nchunks, int32_
         for (int32_t r = chunk_row[c] + threadIdx.x; r < chunk_row[c + 1]; r += blockDim.x) chunk_of_row[r] = c;
 }
 
-// 32 x (longest row) entries per slice; one thread per slice
-__global__ void k_slice_size(const int32_t *chunk_row, const int32_t *chunk_slice, int32_t nchunks,
-                             const int32_t *rowlen, int64_t *size) {
-    for (int32_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        const int32_t r0 = chunk_row[c], r1 = chunk_row[c + 1], s0 = chunk_slice[c];
-        for (int32_t sl = threadIdx.x; s0 + sl < chunk_slice[c + 1]; sl += blockDim.x) {
-            int32_t w = 0;
-            for (int32_t r = r0 + 32 * sl; r < r0 + 32 * sl + 32 && r < r1; ++r) w = max(w, rowlen[r]);
-            size[s0 + sl] = 32 * (int64_t)w;
-        }
+// longest row of each 32-row slice; one thread per slice
+__global__ void k_slice_width(const int32_t *slice_row, int32_t nslices, const int32_t *rowlen, int32_t *width) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t sl = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sl < nslices; sl += stride) {
+        int32_t w = 0;
+        for (int32_t r = slice_row[sl]; r < slice_row[sl + 1]; ++r) w = max(w, rowlen[r]);
+        width[sl] = w;
     }
 }
 
@@ -84,6 +81,102 @@ __global__ void k_dep_init(int2 *dep, int32_t nchunks) {
         dep[c] = make_int2(c, c);
 }
 
+// Exact dependency sets: bit (cc - hull_lo[c]) of chunk c's bitmap is set when a row of c
+// reads a row of chunk cc (and, for patterns not known to be symmetric, when a row of cc
+// reads a row of c).  Every chunk depends on itself.
+__global__ void k_dep_bits(int32_t n, const int32_t *rowlen, const int32_t *chunk_row, const int32_t *chunk_slice,
+                           const int32_t *cor, const int64_t *slice_ptr, const int32_t *scol, const int2 *hull,
+                           const int64_t *word_off, uint32_t *bits, int symmetric) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
+        const int32_t c = cor[r];
+        const int32_t local = (int32_t)r - chunk_row[c];
+        const int64_t base = slice_ptr[chunk_slice[c] + (local >> 5)] + (local & 31);
+        const int32_t lo_c = hull[c].x;
+        auto set = [&](int32_t owner, int32_t owner_lo, int32_t target) {
+            const int32_t off = target - owner_lo;
+            atomicOr(&bits[word_off[owner] + (off >> 5)], 1u << (off & 31));
+        };
+        set(c, lo_c, c);
+        int32_t last = -1;
+        for (int32_t j = 0; j < rowlen[r]; ++j) {
+            const int32_t cc = cor[scol[base + 32 * (int64_t)j]];
+            if (cc == last) continue;
+            last = cc;
+            set(c, lo_c, cc);
+            if (!symmetric) set(cc, hull[cc].x, c);
+        }
+    }
+}
+
+// Compresses each chunk's bitmap into at most kDepRanges ranges of chunk indices: maximal
+// runs of set bits, then the runs separated by the smallest gaps are merged.  Chunks with
+// more than 64 runs fall back to their hull.  Empty ranges are (0, -1).
+__global__ void k_dep_ranges(int32_t nchunks, const int2 *hull, const int64_t *word_off, const uint32_t *bits,
+                             int4 *ranges) {
+    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nchunks; c += gridDim.x * blockDim.x) {
+        const int32_t lo = hull[c].x, hi = hull[c].y;
+        const int64_t w0 = word_off[c];
+        const int32_t nb = hi - lo + 1;
+        int32_t rs[64], re[64];
+        int nr = 0;
+        bool overflow = false;
+        int32_t run_start = -1;
+        for (int32_t b = 0; b < nb && !overflow; ++b) {
+            const bool on = (bits[w0 + (b >> 5)] >> (b & 31)) & 1u;
+            if (on && run_start < 0) run_start = b;
+            if (!on && run_start >= 0) {
+                if (nr == 64) overflow = true;
+                else { rs[nr] = lo + run_start; re[nr] = lo + b - 1; ++nr; }
+                run_start = -1;
+            }
+        }
+        if (!overflow && run_start >= 0) {
+            if (nr == 64) overflow = true;
+            else { rs[nr] = lo + run_start; re[nr] = hi; ++nr; }
+        }
+        if (overflow || nr == 0) {
+            nr = 1;
+            rs[0] = lo;
+            re[0] = hi;
+        }
+        while (nr > kDepRanges) {  // merge the pair of neighbouring runs with the smallest gap
+            int best = 0;
+            for (int q = 1; q + 1 < nr; ++q)
+                if (rs[q + 1] - re[q] < rs[best + 1] - re[best]) best = q;
+            re[best] = re[best + 1];
+            for (int q = best + 1; q + 1 < nr; ++q) {
+                rs[q] = rs[q + 1];
+                re[q] = re[q + 1];
+            }
+            --nr;
+        }
+        int32_t out[2 * kDepRanges];
+        for (int q = 0; q < kDepRanges; ++q) {
+            out[2 * q] = q < nr ? rs[q] : 0;
+            out[2 * q + 1] = q < nr ? re[q] : -1;
+        }
+        ranges[2 * c] = make_int4(out[0], out[1], out[2], out[3]);
+        ranges[2 * c + 1] = make_int4(out[4], out[5], out[6], out[7]);
+    }
+}
+
+// One 64-byte record per chunk with everything the kernel's control warp needs:
+// [row0, row1, slice0, padded entries, first entry (lo, hi 32 bits), staged, 0,
+//  kDepRanges (lo, hi) dependency ranges].
+__global__ void k_chunk_records(int32_t nchunks, const int32_t *chunk_row, const int32_t *chunk_slice,
+                                const int64_t *slice_ptr, const int4 *ranges, int4 *rec) {
+    for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nchunks; c += gridDim.x * blockDim.x) {
+        const int64_t e0 = slice_ptr[chunk_slice[c]], e1 = slice_ptr[chunk_slice[c + 1]];
+        const int32_t cnt = (int32_t)(e1 - e0);
+        rec[4 * c + 0] = make_int4(chunk_row[c], chunk_row[c + 1], chunk_slice[c], cnt);
+        rec[4 * c + 1] = make_int4((int32_t)(e0 & 0xffffffffLL), (int32_t)(e0 >> 32),
+                                   (cnt > 0 && cnt <= kStageEntries) ? 1 : 0, 0);
+        rec[4 * c + 2] = ranges[2 * c];
+        rec[4 * c + 3] = ranges[2 * c + 1];
+    }
+}
+
 // sliced copy -> CSR (for inspection and tests)
 __global__ void k_export(int32_t n, const int32_t *rowlen, const int32_t *chunk_row, const int32_t *chunk_slice,
                          const int32_t *chunk_of_row, const int64_t *slice_ptr, const double *sval,
@@ -120,7 +213,7 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
     if (!(o->nrhs == 1 || o->nrhs == 2 || o->nrhs == 4 || o->nrhs == 8))
         fail(MPK_ERR_UNSUPPORTED, "nrhs must be 1, 2, 4 or 8 (got %d)", o->nrhs);
     if (o->order != MPK_ORDER_ORIGINAL && o->order != MPK_ORDER_PLAN) fail(MPK_ERR_INVALID, "bad order");
-    const int32_t chunk_rows = o->chunk_rows ? o->chunk_rows : 512;
+    const int32_t chunk_rows = o->chunk_rows ? o->chunk_rows : kDefaultChunkRows;
     if (chunk_rows < 32 || chunk_rows > 8192 || chunk_rows % 32)
         fail(MPK_ERR_INVALID, "chunk_rows must be a multiple of 32 in [32, 8192]");
     if (o->cache_bytes < 0 || o->mem_budget < 0 || o->wait_limit_ns < 0) fail(MPK_ERR_INVALID, "negative option");
@@ -138,7 +231,8 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         P->identity = (L == nullptr);
         P->chunk_rows = chunk_rows;
         P->cache_bytes = o->cache_bytes ? o->cache_bytes : device_l2_bytes() / 2;
-        P->group_budget = P->cache_bytes / (pmax + 1);
+        P->window = kSlotSkew * pmax + 1;
+        P->group_budget = P->cache_bytes / P->window;
         P->wait_ns = o->wait_limit_ns ? o->wait_limit_ns : 2000000000LL;
         P->num_levels = L ? L->num_levels : 0;
 
@@ -194,24 +288,54 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         const int32_t G = (int32_t)g_row.size() - 1;
         P->num_groups = G;
 
-        // ---- chunks and slices (host)
+        // ---- slices: 32-row blocks counted from each group's first row (host)
+        std::vector<int32_t> s_row;
+        s_row.push_back(0);
+        std::vector<int32_t> g_slice;
+        for (int32_t g = 0; g < G; ++g) {
+            g_slice.push_back((int32_t)s_row.size() - 1);
+            for (int32_t r = g_row[g]; r < g_row[g + 1]; r += 32) s_row.push_back(std::min(r + 32, g_row[g + 1]));
+        }
+        g_slice.push_back((int32_t)s_row.size() - 1);
+        const int32_t NS = (int32_t)s_row.size() - 1;
+        P->num_slices = NS;
+        Tmp<int32_t> d_srow((int64_t)NS + 1);
+        Tmp<int32_t> d_width(NS);
+        MPK_CUDA(cudaMemcpyAsync(d_srow.p, s_row.data(), sizeof(int32_t) * ((size_t)NS + 1), cudaMemcpyHostToDevice, s));
+        if (NS > 0) {
+            k_slice_width<<<grid_n(NS), 256, 0, s>>>(d_srow.p, NS, P->rowlen, d_width.p);
+            MPK_LAUNCHED();
+        }
+        std::vector<int32_t> width((size_t)NS);
+        if (NS > 0)
+            MPK_CUDA(cudaMemcpyAsync(width.data(), d_width.p, sizeof(int32_t) * (size_t)NS, cudaMemcpyDeviceToHost, s));
+        MPK_CUDA(cudaStreamSynchronize(s));
+        std::vector<int64_t> sptr((size_t)NS + 1, 0);
+        for (int32_t i = 0; i < NS; ++i) sptr[i + 1] = sptr[i] + 32 * (int64_t)width[i];
+        P->padded = sptr[NS];
+
+        // ---- chunks: consecutive slices of one group, at most chunk_rows rows and at most
+        //      kStageEntries padded entries (a single wider slice forms its own chunk)
         std::vector<int32_t> c_row, c_slice, g_chunk;
         c_row.push_back(0);
         c_slice.push_back(0);
         for (int32_t g = 0; g < G; ++g) {
             g_chunk.push_back((int32_t)c_row.size() - 1);
-            for (int32_t r = g_row[g]; r < g_row[g + 1]; r += chunk_rows) {
-                const int32_t e = std::min(r + chunk_rows, g_row[g + 1]);
-                c_row.push_back(e);
-                c_slice.push_back(c_slice.back() + (e - r + 31) / 32);
+            int32_t s0 = g_slice[g];
+            while (s0 < g_slice[g + 1]) {
+                int32_t s1 = s0 + 1;
+                while (s1 < g_slice[g + 1] && s_row[s1 + 1] - s_row[s0] <= chunk_rows &&
+                       sptr[s1 + 1] - sptr[s0] <= kStageEntries)
+                    ++s1;
+                c_row.push_back(s_row[s1]);
+                c_slice.push_back(s1);
+                s0 = s1;
             }
         }
         g_chunk.push_back((int32_t)c_row.size() - 1);
         const int32_t NC = (int32_t)c_row.size() - 1;
         if (NC >= (1 << 26)) fail(MPK_ERR_TOO_LARGE, "too many chunks (%d)", NC);
-        const int32_t NS = c_slice.back();
         P->num_chunks = NC;
-        P->num_slices = NS;
         P->chunk_row = P->arena.alloc_n<int32_t>(NC + 1);
         P->chunk_slice = P->arena.alloc_n<int32_t>(NC + 1);
         P->group_row_ptr = P->arena.alloc_n<int32_t>(G + 1);
@@ -226,15 +350,8 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
 
         // ---- sliced copy
         P->slice_ptr = P->arena.alloc_n<int64_t>((int64_t)NS + 1);
+        MPK_CUDA(cudaMemcpyAsync(P->slice_ptr, sptr.data(), sizeof(int64_t) * ((size_t)NS + 1), cudaMemcpyHostToDevice, s));
         Tmp<int32_t> cor(n);
-        if (NC > 0) {
-            k_slice_size<<<grid_n((int64_t)NC * 256), 256, 0, s>>>(P->chunk_row, P->chunk_slice, NC, P->rowlen,
-                                                                   P->slice_ptr);
-            MPK_LAUNCHED();
-        }
-        exclusive_scan(P->slice_ptr, P->slice_ptr, NS, s);
-        MPK_CUDA(cudaMemcpyAsync(&P->padded, P->slice_ptr + NS, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-        MPK_CUDA(cudaStreamSynchronize(s));
         P->val = P->arena.alloc_n<double>(P->padded + 32);
         P->col = P->arena.alloc_n<int32_t>(P->padded + 32);
         MPK_CUDA(cudaMemsetAsync(P->val, 0, sizeof(double) * (size_t)(P->padded + 32), s));
@@ -250,16 +367,55 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
                                              P->col, P->dep, A->is_symmetric ? 1 : 0);
             MPK_LAUNCHED();
         }
+        // ---- dependency ranges: exact chunk sets as bitmaps over each hull, compressed
+        P->dep_ranges = P->arena.alloc_n<int4>(2 * (int64_t)(NC > 0 ? NC : 1));
+        if (NC > 0) {
+            std::vector<int2> hull((size_t)NC);
+            MPK_CUDA(cudaMemcpyAsync(hull.data(), P->dep, sizeof(int2) * (size_t)NC, cudaMemcpyDeviceToHost, s));
+            MPK_CUDA(cudaStreamSynchronize(s));
+            std::vector<int64_t> woff((size_t)NC + 1, 0);
+            for (int32_t c = 0; c < NC; ++c) woff[c + 1] = woff[c] + (hull[c].y - hull[c].x + 32) / 32;
+            const int64_t words = woff[NC];
+            if (words <= ((int64_t)1 << 27)) {
+                Tmp<int64_t> d_woff((int64_t)NC + 1);
+                Tmp<uint32_t> d_bits(words);
+                MPK_CUDA(cudaMemcpyAsync(d_woff.p, woff.data(), sizeof(int64_t) * ((size_t)NC + 1),
+                                         cudaMemcpyHostToDevice, s));
+                MPK_CUDA(cudaMemsetAsync(d_bits.p, 0, sizeof(uint32_t) * (size_t)words, s));
+                k_dep_bits<<<grid_n(n), 256, 0, s>>>(n, P->rowlen, P->chunk_row, P->chunk_slice, cor.p, P->slice_ptr,
+                                                     P->col, P->dep, d_woff.p, d_bits.p, A->is_symmetric ? 1 : 0);
+                MPK_LAUNCHED();
+                k_dep_ranges<<<grid_n(NC), 256, 0, s>>>(NC, P->dep, d_woff.p, d_bits.p, P->dep_ranges);
+                MPK_LAUNCHED();
+                MPK_CUDA(cudaStreamSynchronize(s));
+            } else {  // bitmaps too large: one range per chunk, the hull
+                std::vector<int4> rr((size_t)2 * NC);
+                for (int32_t c = 0; c < NC; ++c) {
+                    rr[2 * c] = make_int4(hull[c].x, hull[c].y, 0, -1);
+                    rr[2 * c + 1] = make_int4(0, -1, 0, -1);
+                }
+                MPK_CUDA(cudaMemcpyAsync(P->dep_ranges, rr.data(), sizeof(int4) * rr.size(), cudaMemcpyHostToDevice, s));
+                MPK_CUDA(cudaStreamSynchronize(s));
+            }
+        }
 
-        // ---- unit tables: Lp-diagram order (diagonal d = g + k ascending, then k ascending,
-        //      then chunks in row order) for every p = 1..p_max; unit = chunk << 5 | k
+        P->chunk_rec = P->arena.alloc_n<int4>(4 * (int64_t)(NC > 0 ? NC : 1));
+        if (NC > 0) {
+            k_chunk_records<<<grid_n(NC), 256, 0, s>>>(NC, P->chunk_row, P->chunk_slice, P->slice_ptr, P->dep_ranges,
+                                                      P->chunk_rec);
+            MPK_LAUNCHED();
+        }
+
+        // ---- unit tables: Lp-diagram cells (group g, power k) along lines g + kSlotSkew*k
+        //      ascending, k ascending inside a line, chunks in row order; unit = chunk << 5 | k
         P->unit_off.assign((size_t)pmax + 2, 0);
         std::vector<int32_t> units;
         for (int32_t p = 1; p <= pmax; ++p) {
             P->unit_off[p] = (int64_t)units.size();
-            for (int32_t d = 1; d <= G - 1 + p; ++d)
-                for (int32_t k = std::max(1, d - G + 1); k <= std::min(p, d); ++k) {
-                    const int32_t g = d - k;
+            for (int32_t d = kSlotSkew; d <= G - 1 + kSlotSkew * p; ++d)
+                for (int32_t k = 1; k <= p; ++k) {
+                    const int32_t g = d - kSlotSkew * k;
+                    if (g < 0 || g >= G) continue;
                     for (int32_t c = g_chunk[g]; c < g_chunk[g + 1]; ++c) units.push_back((c << 5) | k);
                 }
         }

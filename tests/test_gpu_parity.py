@@ -143,7 +143,8 @@ def test_plan_groups_and_permuted_matrix(mpk, name, cache_bytes, p_max, m):
     P = mpk.plan(dA, L, p_max=p_max, nrhs=m, cache_bytes=cache_bytes, chunk_rows=64)
     lo, pe, ip, lp = oracle.levels(A, 0)
     prp, pci, pva = oracle.permute(A, pe, ip)
-    budget = cache_bytes // (p_max + 1)
+    budget = cache_bytes // (3 * p_max + 1)
+    assert P.describe()["window"] == 3 * p_max + 1
     g = oracle.groups(lp, prp, budget, val_bytes=8, m=m)
     assert np.array_equal(P.group_level_ptr.cpu().numpy(), g)
     assert np.array_equal(P.group_row_ptr.cpu().numpy(), lp[g])

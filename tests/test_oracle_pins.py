@@ -247,12 +247,38 @@ def test_groups_bulky_singleton_and_cover():
 def test_lp_labels_fig2():
     golden = np.array(read_golden("fig2_lp_labels.txt"))
     assert np.array_equal(oracle.lp_labels(10, 5), golden)
+    assert np.array_equal(oracle.lp_labels(10, 5, skew=1), golden)
     # Sec. 3 text: L(5) at p=1 runs at step 15 and is reused at step 21 (p=2), p_m+1 steps later
     lab = oracle.lp_labels(10, 5)
     assert lab[0, 5] == 15 and lab[1, 5] == 21
 
 
-def test_lb_mpk_bitwise_equals_plain():
+@pytest.mark.parametrize("skew", [1, 2, 3, 4])
+def test_lp_order_respects_dependencies(skew):
+    # every cell runs after (i-1, p-1), (i, p-1) and (i+1, p-1), the Sec. 3 dependency rule
+    L, pm = 13, 6
+    lab = oracle.lp_labels(L, pm, skew)
+    assert sorted(lab.ravel().tolist()) == list(range(L * pm))
+    for p in range(1, pm):
+        for i in range(L):
+            for j in (i - 1, i, i + 1):
+                if 0 <= j < L:
+                    assert lab[p, i] > lab[p - 1, j]
+
+
+def test_lp_order_skew_lines_are_independent():
+    # with skew >= 2 no cell depends on another cell of its own line g + skew*k
+    L, pm = 11, 5
+    for skew in (2, 3):
+        for p in range(2, pm + 1):
+            for i in range(L):
+                for j in (i - 1, i, i + 1):
+                    if 0 <= j < L:
+                        assert (i + skew * p) - (j + skew * (p - 1)) >= skew - 1 >= 1
+
+
+@pytest.mark.parametrize("skew", [1, 2, 3])
+def test_lb_mpk_bitwise_equals_plain(skew):
     A = gen.laplacian_3d(9, 7, 5)
     level_of, perm, iperm, level_ptr = oracle.levels(A, 0)
     prp, pci, pva = oracle.permute(A, perm, iperm)
@@ -261,8 +287,22 @@ def test_lb_mpk_bitwise_equals_plain():
     for budget in (1, 2000, 10**9):
         gl = oracle.groups(level_ptr, prp, budget, m=2)
         group_rows = level_ptr[gl]
-        Ylb = oracle.lb_mpk(prp, pci, pva, X[perm], 6, group_rows)
+        Ylb = oracle.lb_mpk(prp, pci, pva, X[perm], 6, group_rows, skew=skew)
         assert np.array_equal(Ylb[:, iperm, :], Yplain)
+
+
+def test_lb_mpk_detects_a_wrong_order():
+    # planted mistake: skew 0 runs all powers of a group before the next group, so (g, 2)
+    # reads group g+1 at power 1 before it exists; the run must not match back-to-back SpMV
+    A = gen.laplacian_3d(9, 7, 5)
+    level_of, perm, iperm, level_ptr = oracle.levels(A, 0)
+    prp, pci, pva = oracle.permute(A, perm, iperm)
+    X = gen.vector(A.n, 1, stream=62)
+    gl = oracle.groups(level_ptr, prp, 1)
+    Ybad = oracle.lb_mpk(prp, pci, pva, X[perm], 3, level_ptr[gl], skew=0)
+    assert np.isnan(Ybad[2:]).any()
+    lab = oracle.lp_labels(10, 3, skew=0)
+    assert lab[1, 4] < lab[0, 5]  # (i=4, p=2) before (i=5, p=1): the rule is broken
 
 
 # ----------------------------------------------------------------------------- Chebyshev
