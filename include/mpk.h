@@ -116,6 +116,7 @@ typedef struct {
     int32_t chunk_rows;     /* rows per work unit (multiple of 32); 0 = 480                 */
     int64_t wait_limit_ns;  /* bound on every device-side wait; 0 = 2 s                     */
     int64_t mem_budget;     /* bytes the plan may allocate on the device; 0 = no limit     */
+    int32_t trace;          /* 1: the level-blocked kernel accumulates timing counters      */
 } mpk_plan_opts;
 
 /* Fills the defaults described above (p_max = 8, nrhs = 1, order = ORIGINAL). */
@@ -182,6 +183,15 @@ mpk_status mpk_spmv_powers(const mpk_plan_t *P, const double *X, int32_t p, doub
 mpk_status mpk_cheb_filter(const mpk_plan_t *P, const double *X, int32_t degree,
                            const double *coeff_re, const double *coeff_im, double scale,
                            double shift, double *out, mpk_stream stream);
+
+/* Timing counters of a plan built with opts.trace = 1, accumulated over all launches since
+ * the plan was created (host array of MPK_TRACE_COUNTERS int64): 0 units, 1 ns the control
+ * warps spent polling dependencies, 2 failed dependency checks, 3 ns control warps waited for
+ * a free slot, 4 ns compute warps waited for a unit, 5 ns compute warps spent computing,
+ * 6 ns summed over blocks from start to exit, 7 launches.  Synchronises `stream`.
+ * MPK_ERR_UNSUPPORTED if the plan has no trace. */
+#define MPK_TRACE_COUNTERS 8
+mpk_status mpk_read_trace(const mpk_plan_t *P, int64_t *counters, mpk_stream stream);
 
 /* Synchronises `stream` and reports a device-side failure of the plan's calls since the
  * last mpk_sync_status (MPK_ERR_TIMEOUT), else MPK_OK or a CUDA error. */

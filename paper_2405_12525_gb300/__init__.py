@@ -32,7 +32,7 @@ EXPORTED_SYMBOLS = [
     "mpk_build_levels", "mpk_levels_get", "mpk_levels_destroy", "mpk_plan_opts_default", "mpk_plan",
     "mpk_plan_describe", "mpk_plan_export_csr", "mpk_plan_destroy", "mpk_apply", "mpk_spmv_powers",
     "mpk_cheb_filter", "mpk_sync_status", "mpk_probe_load", "mpk_probe_dfma", "mpk_device_info",
-    "mpk_status_string", "mpk_last_error", "mpk_debug_drop_release",
+    "mpk_status_string", "mpk_last_error", "mpk_debug_drop_release", "mpk_read_trace",
 ]
 
 
@@ -49,7 +49,8 @@ class _Csr(C.Structure):
 
 class _Opts(C.Structure):
     _fields_ = [("p_max", C.c_int32), ("nrhs", C.c_int32), ("cache_bytes", C.c_int64), ("order", C.c_int32),
-                ("chunk_rows", C.c_int32), ("wait_limit_ns", C.c_int64), ("mem_budget", C.c_int64)]
+                ("chunk_rows", C.c_int32), ("wait_limit_ns", C.c_int64), ("mem_budget", C.c_int64),
+                ("trace", C.c_int32)]
 
 
 class _Desc(C.Structure):
@@ -75,9 +76,10 @@ def load():
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(_LIB_PATH):
-        raise RuntimeError(f"libmpk.so is missing at {_LIB_PATH}: run paper_2405_12525_gb300.build()")
-    lib = C.CDLL(_LIB_PATH)
+    path = os.environ.get("MPK_LIBRARY", _LIB_PATH)  # an alternative build of the same sources
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmpk.so is missing at {path}: run paper_2405_12525_gb300.build()")
+    lib = C.CDLL(path)
     vp, i32, i64, dbl = C.c_void_p, C.c_int32, C.c_int64, C.c_double
     sig = {
         "mpk_build_levels": [C.POINTER(_Csr), i32, vp, C.POINTER(vp)],
@@ -94,6 +96,7 @@ def load():
         "mpk_probe_dfma": [i32, i32, vp, vp],
         "mpk_device_info": [C.POINTER(i32), C.POINTER(i64)],
         "mpk_debug_drop_release": [vp, i32, i32],
+        "mpk_read_trace": [vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -314,6 +317,16 @@ class Plan:
         """Test hook: unit (chunk, k) of the next launch skips its completion flag."""
         _check(self._lib.mpk_debug_drop_release(self._h, int(chunk), int(k)))
 
+    TRACE_FIELDS = ("units", "ctrl_poll_ns", "ctrl_poll_retries", "ctrl_slot_wait_ns", "comp_wait_ns",
+                    "comp_busy_ns", "block_ns", "launches")
+
+    def read_trace(self, stream=None) -> dict:
+        """Timing counters of a plan built with trace=1 (accumulated over its launches)."""
+        import numpy as np
+        out = np.zeros(8, dtype=np.int64)
+        _check(self._lib.mpk_read_trace(self._h, out.ctypes.data, _stream(stream)))
+        return dict(zip(self.TRACE_FIELDS, out.tolist()))
+
     def sync_status(self, stream=None):
         _check(self._lib.mpk_sync_status(self._h, _stream(stream)))
 
@@ -325,12 +338,13 @@ class Plan:
 
 def plan(A: CsrMatrix, levels: Levels | None = None, p_max: int = 8, nrhs: int = 1, cache_bytes: int = 0,
          order: int = ORDER_ORIGINAL, chunk_rows: int = 0, wait_limit_ns: int = 0, mem_budget: int = 0,
-         stream=None) -> Plan:
+         trace: bool = False, stream=None) -> Plan:
     lib = load()
     o = _Opts()
     lib.mpk_plan_opts_default(C.byref(o))
     o.p_max, o.nrhs, o.cache_bytes, o.order = p_max, nrhs, cache_bytes, order
     o.chunk_rows, o.wait_limit_ns, o.mem_budget = chunk_rows, wait_limit_ns, mem_budget
+    o.trace = 1 if trace else 0
     h = C.c_void_p()
     csr = A._c()
     _check(lib.mpk_plan(C.byref(csr), levels._h if levels is not None else None, C.byref(o), _stream(stream),

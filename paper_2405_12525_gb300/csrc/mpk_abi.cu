@@ -172,10 +172,9 @@ static KArgs base_args(Plan &P, int32_t p) {
     a.err = reinterpret_cast<int32_t *>(P.ctl + 2);
     a.wait_ns = P.wait_ns;
     a.drop_unit = P.drop_unit;
+    a.trace = P.trace;
     P.drop_unit = -1;
     a.ystride = (int64_t)P.n * P.m;
-    a.ostride = (int64_t)P.n * P.m;
-    a.perm = P.perm;
     return a;
 }
 
@@ -199,23 +198,22 @@ extern "C" mpk_status mpk_apply(const mpk_plan_t *Ph, const double *X, int32_t p
     }
     next_epoch(P, s);
     KArgs a = base_args(P, p);
-    int mode;
+    a.ring = p + 1;
     if (P.identity || P.order == MPK_ORDER_PLAN) {
         a.x0 = X;
         a.ybase = Y;
-        a.ring = p + 1;
         a.y0copy = (Y != X) ? Y : nullptr;
-        mode = 0;
+        launch_mpk(P, a, 0, s);
     } else {
+        // gather X into plan order, compute every power in plan order in the workspace,
+        // then write the powers through the permutation (gather by output row)
         launch_gather_rows(X, P.perm, P.work, P.n, P.m, s);
         if (Y != X) MPK_CUDA(cudaMemcpyAsync(Y, X, sizeof(double) * nm, cudaMemcpyDeviceToDevice, s));
         a.x0 = P.work;
         a.ybase = P.work;
-        a.ring = 3;
-        a.yorig = Y;
-        mode = 1;
+        launch_mpk(P, a, 0, s);
+        launch_scatter_powers(P.work, P.iperm, Y, P.n, P.m, p, s);
     }
-    launch_mpk(P, a, mode, s);
     return MPK_OK;
     MPK_GUARD_END
 }
@@ -230,11 +228,11 @@ extern "C" mpk_status mpk_spmv_powers(const mpk_plan_t *Ph, const double *X, int
     if (P.n == 0) return MPK_OK;
     if (Y != X) MPK_CUDA(cudaMemcpyAsync(Y, X, sizeof(double) * nm, cudaMemcpyDeviceToDevice, s));
     if (P.identity || P.order == MPK_ORDER_PLAN) {
-        for (int k = 1; k <= p; ++k) launch_spmv(P, Y + (k - 1) * nm, Y + k * nm, nullptr, 0, s);
+        for (int k = 1; k <= p; ++k) launch_spmv(P, Y + (k - 1) * nm, Y + k * nm, s);
     } else {
         launch_gather_rows(X, P.perm, P.work, P.n, P.m, s);
-        for (int k = 1; k <= p; ++k)
-            launch_spmv(P, P.work + ((k - 1) % 2) * nm, P.work + (k % 2) * nm, Y, k * nm, s);
+        for (int k = 1; k <= p; ++k) launch_spmv(P, P.work + (k - 1) * nm, P.work + k * nm, s);
+        launch_scatter_powers(P.work, P.iperm, Y, P.n, P.m, p, s);
     }
     return MPK_OK;
     MPK_GUARD_END
@@ -284,9 +282,20 @@ extern "C" mpk_status mpk_cheb_filter(const mpk_plan_t *Ph, const double *X, int
             a.cre[k] = coeff_re[j0 + k];
             a.cim[k] = coeff_im ? coeff_im[j0 + k] : 0.0;
         }
-        launch_mpk(P, a, 2, s);
+        launch_mpk(P, a, 1, s);
     }
     if (!plan_order) launch_scatter_rows(acc, P.iperm, out, P.n, P.m, s);
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
+extern "C" mpk_status mpk_read_trace(const mpk_plan_t *Ph, int64_t *counters, mpk_stream stream) {
+    MPK_GUARD_BEGIN
+    if (!Ph || !Ph->impl || !counters) fail(MPK_ERR_INVALID, "NULL plan or output");
+    const Plan &P = *Ph->impl;
+    if (!P.trace) fail(MPK_ERR_UNSUPPORTED, "plan was built without opts.trace");
+    MPK_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    MPK_CUDA(cudaMemcpy(counters, P.trace, sizeof(int64_t) * MPK_TRACE_COUNTERS, cudaMemcpyDeviceToHost));
     return MPK_OK;
     MPK_GUARD_END
 }

@@ -89,11 +89,17 @@ struct Levels {
 // Arguments of the level-blocked kernel, passed by value.
 constexpr int kMaxP = 31;
 // padded entries of one chunk that the kernel stages in shared memory (per buffer)
-constexpr int kStageEntries = 4096;
+#ifndef MPK_STAGE_ENTRIES
+#define MPK_STAGE_ENTRIES 4096
+#endif
+constexpr int kStageEntries = MPK_STAGE_ENTRIES;
 // dependency ranges kept per chunk (exact sets compressed to this many index ranges)
 constexpr int kDepRanges = 4;
 // compute warps of the level-blocked kernel; the default chunk is one 32-row slice per warp
-constexpr int kCompWarps = 15;
+#ifndef MPK_COMP_WARPS
+#define MPK_COMP_WARPS 15
+#endif
+constexpr int kCompWarps = MPK_COMP_WARPS;
 constexpr int kDefaultChunkRows = 32 * kCompWarps;
 // The level-blocked kernel walks the Lp diagram along lines g + kSlotSkew * k = const.  With
 // skew 1 (the paper's diagonals) the cells of one line form a dependency chain; with skew 3
@@ -101,6 +107,10 @@ constexpr int kDefaultChunkRows = 32 * kCompWarps;
 // GPU do not wait on each other.  A group is then reused kSlotSkew * p lines later, so the
 // cache budget is shared by kSlotSkew * p_max + 1 groups.
 constexpr int kSlotSkew = 3;
+// chunk record: 8 ints of chunk data, 2 * kDepRanges ints of dependency ranges and the
+// widths of up to kRecSlices slices as bytes (only staged chunks use them)
+constexpr int kRecSlices = 16;
+constexpr int kRecInts = 8 + 2 * kDepRanges + kRecSlices / 4;
 struct KArgs {
     // sliced matrix copy (plan order)
     const double *val;
@@ -111,7 +121,7 @@ struct KArgs {
     const int32_t *chunk_slice;
     const int2 *dep;
     const int4 *dep_ranges;  // 2 x int4 per chunk: kDepRanges (lo, hi) pairs
-    const int4 *chunk_rec;   // 4 x int4 per chunk: rows, slices, entries, ranges
+    const int4 *chunk_rec;   // kRecInts ints per chunk: rows, slices, entries, ranges, widths
     int32_t n;
     int32_t nchunks;
     // schedule for this launch
@@ -124,15 +134,13 @@ struct KArgs {
     int32_t *err;    // err[0] = epoch of a failed launch, err[1] = status code
     int64_t wait_ns;
     int32_t drop_unit;  // test hook: this unit (chunk << 5 | k) skips its release, -1 = none
+    unsigned long long *trace;  // timing counters (MPK_TRACE_COUNTERS) or null
     // vectors
     const double *x0;  // power-0 block (plan order)
     double *ybase;     // slot(k) = ybase + (k % ring) * ystride
     int64_t ystride;
     int32_t ring;
     double *y0copy;    // if set, units of power 1 copy their rows of x0 here
-    double *yorig;     // if set, power k of row r is also written to yorig[k*ostride + perm[r]*M]
-    const int32_t *perm;
-    int64_t ostride;
     int32_t k_offset;  // absolute index of local power 0 (Chebyshev blocks)
     // Chebyshev recurrence
     double alpha, beta, halpha, hbeta;
@@ -167,18 +175,21 @@ struct Plan {
     std::vector<int64_t> unit_off;  // unit_off[p] .. unit_off[p] + nunits(p)
     int32_t *flags = nullptr;
     unsigned int *ctl = nullptr;  // [0] ticket, [1] exit count, [2] err epoch, [3] err code
-    double *work = nullptr;       // 3 ring slots + accumulator, each n*m
+    double *work = nullptr;       // work_slots blocks of n*m: powers in plan order, or Chebyshev ring + accumulator
+    int32_t work_slots = 0;
     int32_t epoch = 0;
     int32_t last_checked_epoch = 0;
     int32_t drop_unit = -1;  // armed by mpk_debug_drop_release for the next launch
+    unsigned long long *trace = nullptr;  // counters when built with opts.trace
     int grid_mpk[4] = {0, 0, 0, 0};  // persistent grid size per mode
     Arena arena;
 };
 
 // kernels (mpk_kernel.cu)
 void launch_mpk(const Plan &P, KArgs &a, int mode, cudaStream_t s);
-void launch_spmv(const Plan &P, const double *x, double *y, double *yorig, int64_t orig_off,
-                 cudaStream_t s);
+void launch_spmv(const Plan &P, const double *x, double *y, cudaStream_t s);
+void launch_scatter_powers(const double *W, const int32_t *iperm, double *Y, int32_t n, int32_t m, int32_t p,
+                           cudaStream_t s);
 void launch_gather_rows(const double *src, const int32_t *perm, double *dst, int32_t n, int32_t m,
                         cudaStream_t s);
 void launch_scatter_rows(const double *src, const int32_t *iperm, double *dst, int32_t n, int32_t m,

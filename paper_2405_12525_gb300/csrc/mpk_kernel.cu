@@ -16,11 +16,18 @@
 namespace mpk {
 
 constexpr int kBS = 32 * (1 + kCompWarps);  // level-blocked kernel: 1 control warp + compute warps
+constexpr int kBlocksPerSM = 1024 / kBS;     // register budget: 64 per thread at 2048 threads per SM
 constexpr int kSpmvBS = 256;        // threads per block of the plain SpMV kernel
-constexpr int kStageBytes = kStageEntries * 12;          // one buffer: values + columns
-constexpr int kSmemBytes = 2 * kStageBytes;             // double buffered
+#ifndef MPK_COMPUTE_PIPELINE
+#define MPK_COMPUTE_PIPELINE 0
+#endif
+// Staging slots: the control warp fills one while the compute warps hold the others (two
+// when compute warps software-pipeline consecutive units, one otherwise).
+constexpr int kSlots = MPK_COMPUTE_PIPELINE ? 3 : 2;
+constexpr int kStageBytes = kStageEntries * 12;          // one slot: values + columns
+constexpr int kSmemBytes = kSlots * kStageBytes;
 
-enum Mode { MODE_PLAN = 0, MODE_SCATTER = 1, MODE_CHEB = 2 };
+enum Mode { MODE_POWERS = 0, MODE_CHEB = 1 };
 
 __device__ __forceinline__ int ld_relaxed(const int32_t *p) {
     int v;
@@ -80,32 +87,64 @@ template <int M> struct Batch {
 };
 
 // acc[i] = sum_j val[j] * x[col[j]*M + i] over a row's entries, in stored order.  Entry j
-// of the row is at val[off + 32 j] / col[off + 32 j] (global or shared memory).
+// of the row is at val[off + 32 j] / col[off + 32 j] (global or shared memory), j < width
+// of the row's slice; entries past the row's end are padding with col < 0 and are skipped.
 template <int M, int B, class VP, class CP>
-__device__ __forceinline__ void row_sum(VP val, CP col, int64_t off, int len, const double *x, double (&acc)[M]) {
+__device__ __forceinline__ void row_sum(VP val, CP col, int64_t off, int width, const double *x, double (&acc)[M]) {
 #pragma unroll
     for (int i = 0; i < M; ++i) acc[i] = 0.0;
-    for (int j0 = 0; j0 < len; j0 += B) {
+    for (int j0 = 0; j0 < width; j0 += B) {
         double v[B];
         int32_t c[B];
 #pragma unroll
         for (int b = 0; b < B; ++b) {
-            if (j0 + b < len) {
+            if (j0 + b < width) {
                 v[b] = val[off + 32 * (int64_t)(j0 + b)];
                 c[b] = col[off + 32 * (int64_t)(j0 + b)];
             } else {
                 v[b] = 0.0;
-                c[b] = 0;
+                c[b] = -1;
             }
         }
         double xv[B][M];
 #pragma unroll
         for (int b = 0; b < B; ++b)
 #pragma unroll
-            for (int i = 0; i < M; ++i) xv[b][i] = (j0 + b < len) ? x[(int64_t)c[b] * M + i] : 0.0;
+            for (int i = 0; i < M; ++i) xv[b][i] = (c[b] >= 0) ? x[(int64_t)c[b] * M + i] : 0.0;
 #pragma unroll
         for (int b = 0; b < B; ++b)
-            if (j0 + b < len) {
+            if (c[b] >= 0) {
+#pragma unroll
+                for (int i = 0; i < M; ++i) acc[i] = fma(v[b], xv[b][i], acc[i]);
+            }
+    }
+}
+
+// Continues a row sum from entry j0 (acc already holds entries 0..j0-1).
+template <int M, int B, class VP, class CP>
+__device__ __forceinline__ void row_sum_from(VP val, CP col, int64_t off, int j_start, int width, const double *x,
+                                             double (&acc)[M]) {
+    for (int j0 = j_start; j0 < width; j0 += B) {
+        double v[B];
+        int32_t c[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            if (j0 + b < width) {
+                v[b] = val[off + 32 * (int64_t)(j0 + b)];
+                c[b] = col[off + 32 * (int64_t)(j0 + b)];
+            } else {
+                v[b] = 0.0;
+                c[b] = -1;
+            }
+        }
+        double xv[B][M];
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+#pragma unroll
+            for (int i = 0; i < M; ++i) xv[b][i] = (c[b] >= 0) ? x[(int64_t)c[b] * M + i] : 0.0;
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+            if (c[b] >= 0) {
 #pragma unroll
                 for (int i = 0; i < M; ++i) acc[i] = fma(v[b], xv[b][i], acc[i]);
             }
@@ -122,8 +161,8 @@ struct GCol {
     __device__ __forceinline__ int32_t operator[](int64_t i) const { return __ldg(p + i); }
 };
 
-// Epilogue of one row at local power k: store into the plan-order slot, optionally into
-// the original-order output, or advance the Chebyshev recurrence.
+// Epilogue of one row at local power k: store into the plan-order slot, or advance the
+// Chebyshev recurrence.
 template <int M, int MODE>
 __device__ __forceinline__ void row_epilogue(const KArgs &a, int k, int64_t r, const double (&w)[M],
                                              const double *xin) {
@@ -162,11 +201,6 @@ __device__ __forceinline__ void row_epilogue(const KArgs &a, int k, int64_t r, c
     } else {
 #pragma unroll
         for (int i = 0; i < M; ++i) y[i] = w[i];
-        if constexpr (MODE == MODE_SCATTER) {
-            double *yo = a.yorig + (int64_t)j * a.ostride + (int64_t)a.perm[r] * M;
-#pragma unroll
-            for (int i = 0; i < M; ++i) yo[i] = w[i];
-        }
     }
 }
 
@@ -182,13 +216,14 @@ __device__ __forceinline__ void row_epilogue(const KArgs &a, int k, int64_t r, c
 // (acquire).
 //
 // Warp roles.  Warp 0 (control) claims units, stages each unit's matrix entries into one
-// of two shared-memory slots with bulk (TMA) copies and polls the unit's dependencies;
+// of kSlots shared-memory slots with bulk (TMA) copies and polls the unit's dependencies;
 // warps 1..kCompWarps (compute) compute rows, and the last of them to finish a unit
 // publishes its completion flag.  Slot b has two mbarriers: full[b] completes when the
 // entries have landed and the dependencies are met, empty[b] when every compute warp is
-// done with the slot.  The control warp prepares unit i+1 while unit i is computed; its
-// claims run two units ahead (the ticket of unit i+2 and the chunk record of unit i+1 are
-// fetched while unit i is handled), so only the dependency poll is on its critical path.
+// done with the slot.  The control warp prepares unit i+1 while compute warps finish unit
+// i-1 and start unit i (their software pipeline holds two slots); its
+// claims run three units ahead (tickets, unit ids and chunk records are fetched an
+// iteration before they are needed), so only the dependency poll is on its critical path.
 // A block processes its tickets in claim order and claims are increasing, so the block
 // holding the smallest unfinished ticket is working on it: the schedule stays deadlock
 // free with tickets claimed ahead.
@@ -202,35 +237,142 @@ struct UnitInfo {
     int row0, row1, slice0;
     int ecount;       // padded entries of the chunk
     int staged;       // entries were copied to the slot's shared buffer
+    int nsl;          // slices of the chunk
+    int widths[4];    // staged chunks: width of slice q in byte q of the 16 bytes
     long long ebase;  // first entry of the chunk in the sliced copy
 };
 
 __device__ __forceinline__ bool timed_out(uint64_t t0, int64_t limit) { return globaltimer() - t0 > (uint64_t)limit; }
 
+__device__ __forceinline__ int slice_width(const int (&w)[4], int q) {
+    const int word = (q < 8) ? ((q < 4) ? w[0] : w[1]) : ((q < 12) ? w[2] : w[3]);  // no dynamic indexing
+    return (word >> (8 * (q & 3))) & 0xff;
+}
+
+// A compute warp handles a unit in two phases.  Phase A reads the column indices of the
+// warp's first row batch from shared memory and issues the x gathers; phase B runs the
+// FMAs on those x values, finishes any further batches or slices, stores the results and
+// publishes the unit.  By default phase B follows phase A of the same unit.  Built with
+// MPK_COMPUTE_PIPELINE=1, phase B of unit i-1 runs after phase A of unit i, so the gather
+// latency of one unit hides behind the FMA chains of the previous one (three slots); when
+// the next unit is not ready yet, the pending unit is finished before waiting (a unit can
+// depend on the previous unit of the same block), so the pipeline never holds back a flag
+// that the control warp waits for.
+template <int M> struct Prefetch {
+    static constexpr int B = Batch<M>::B;
+    int unit;             // -1: nothing pending
+    int slot;
+    int r;                // this lane's row in the warp's first slice, -1 if none
+    int off;              // offset of that row's entries in the slot (staged units)
+    int width;            // width of the warp's first slice (staged units)
+    double x[B][M];       // x values of the first batch (entries j < min(B, width))
+};
+
+template <int M>
+__device__ __forceinline__ const double *input_block(const KArgs &a, int k) {
+    return (k == 1 && a.k_offset == 0) ? a.x0 : a.ybase + (int64_t)((a.k_offset + k - 1) % a.ring) * a.ystride;
+}
+
+// phase A: request the x values of the warp's first batch of unit u (slot b)
+template <int M>
+__device__ __forceinline__ void phase_a(const KArgs &a, const UnitInfo &u, int b, const int32_t *scol, int cwarp,
+                                        int lane, Prefetch<M> &pf) {
+    constexpr int B = Batch<M>::B;
+    pf.unit = u.unit;
+    pf.slot = b;
+    const double *xin = input_block<M>(a, u.unit & 31);
+    pf.r = -1;
+    pf.width = 0;
+    pf.off = 0;
+    if (u.staged && cwarp < u.nsl) {
+        int pre = 0;
+#pragma unroll
+        for (int q = 0; q < kRecSlices; ++q) pre += (q < cwarp) ? slice_width(u.widths, q) : 0;
+        pf.width = slice_width(u.widths, cwarp);
+        pf.off = 32 * pre + lane;
+        const int r = u.row0 + 32 * cwarp + lane;
+        if (r < u.row1) pf.r = r;
+    }
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        const int c = (pf.r >= 0 && q < pf.width) ? scol[pf.off + 32 * q] : -1;
+#pragma unroll
+        for (int i = 0; i < M; ++i) pf.x[q][i] = (c >= 0) ? xin[(int64_t)c * M + i] : 0.0;
+    }
+}
+
+// phase B: finish unit pf (all of the warp's rows), then publish and release its slot
 template <int M, int MODE>
-__device__ __forceinline__ void compute_unit(const KArgs &a, const UnitInfo &u, const double *sval,
-                                             const int32_t *scol, int cwarp, int lane) {
-    const int k = u.unit & 31;
-    const int nsl = (u.row1 - u.row0 + 31) >> 5;
-    const double *xin = (k == 1 && a.k_offset == 0)
-                            ? a.x0
-                            : a.ybase + (int64_t)((a.k_offset + k - 1) % a.ring) * a.ystride;
-    for (int sl = cwarp; sl < nsl; sl += kCompWarps) {
-        const int64_t r = (int64_t)u.row0 + 32 * sl + lane;
-        if (r < u.row1) {
-            const int64_t off = __ldg(a.slice_ptr + u.slice0 + sl) - u.ebase + lane;
-            const int len = __ldg(a.rowlen + r);
+__device__ __forceinline__ void phase_b(const KArgs &a, const Prefetch<M> &pf, const UnitInfo *s_u,
+                                        const double *sval0, const int32_t *scol0, int *s_done, uint64_t *s_empty,
+                                        int cwarp, int lane) {
+    constexpr int B = Batch<M>::B;
+    const UnitInfo &u = s_u[pf.slot];
+    const int k = pf.unit & 31;
+    const double *xin = input_block<M>(a, k);
+    const double *sval = sval0 + pf.slot * kStageEntries;
+    const int32_t *scol = scol0 + pf.slot * kStageEntries;
+    if (u.staged) {
+        if (pf.r >= 0) {  // first slice: prefetched first batch, then the rest of the row
             double w[M];
-            if (u.staged)
-                row_sum<M, Batch<M>::B>(sval, scol, off, len, xin, w);
-            else
-                row_sum<M, 1>(GVal{a.val + u.ebase}, GCol{a.col + u.ebase}, off, len, xin, w);
+#pragma unroll
+            for (int i = 0; i < M; ++i) w[i] = 0.0;
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+                if (q < pf.width && scol[pf.off + 32 * q] >= 0) {
+                    const double v = sval[pf.off + 32 * q];
+#pragma unroll
+                    for (int i = 0; i < M; ++i) w[i] = fma(v, pf.x[q][i], w[i]);
+                }
+            }
+            if (pf.width > B) row_sum_from<M, 2>(sval, scol, pf.off, B, pf.width, xin, w);  // rare: wide rows
+            row_epilogue<M, MODE>(a, k, pf.r, w, xin);
+            if (k == 1 && a.y0copy) {
+#pragma unroll
+                for (int i = 0; i < M; ++i) a.y0copy[(int64_t)pf.r * M + i] = a.x0[(int64_t)pf.r * M + i];
+            }
+        }
+        for (int sl = cwarp + kCompWarps; sl < u.nsl; sl += kCompWarps) {  // further slices (wide chunks)
+            const int64_t r = (int64_t)u.row0 + 32 * sl + lane;
+            int pre = 0;
+#pragma unroll
+            for (int q = 0; q < kRecSlices; ++q) pre += (q < sl) ? slice_width(u.widths, q) : 0;
+            if (r >= u.row1) continue;
+            double w[M];
+            row_sum<M, 2>(sval, scol, 32 * pre + lane, slice_width(u.widths, sl), xin, w);  // rare: wide chunks
             row_epilogue<M, MODE>(a, k, r, w, xin);
             if (k == 1 && a.y0copy) {
 #pragma unroll
                 for (int i = 0; i < M; ++i) a.y0copy[r * M + i] = a.x0[r * M + i];
             }
         }
+    } else {  // entries in global memory (chunk too large to stage)
+        for (int sl = cwarp; sl < u.nsl; sl += kCompWarps) {
+            const int64_t r = (int64_t)u.row0 + 32 * sl + lane;
+            if (r >= u.row1) continue;
+            const int64_t s0 = __ldg(a.slice_ptr + u.slice0 + sl), s1 = __ldg(a.slice_ptr + u.slice0 + sl + 1);
+            double w[M];
+            row_sum<M, 1>(GVal{a.val + u.ebase}, GCol{a.col + u.ebase}, s0 - u.ebase + lane, (int)((s1 - s0) >> 5),
+                          xin, w);
+            row_epilogue<M, MODE>(a, k, r, w, xin);
+            if (k == 1 && a.y0copy) {
+#pragma unroll
+                for (int i = 0; i < M; ++i) a.y0copy[r * M + i] = a.x0[r * M + i];
+            }
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        // the last compute warp to finish the unit publishes it (release at gpu scope after
+        // the other warps' stores were ordered at block scope), then the slot is released
+        __threadfence_block();
+        if (atomicAdd(&s_done[pf.slot], 1) == kCompWarps - 1) {
+            s_done[pf.slot] = 0;
+            fence_acq_rel_gpu();
+            if (pf.unit != a.drop_unit)
+                st_relaxed(a.flags + (int64_t)k * a.nchunks + (pf.unit >> 5), a.epoch);
+        }
+        mbar_arrive(&s_empty[pf.slot]);
     }
 }
 
@@ -261,25 +403,30 @@ __device__ __forceinline__ bool deps_ready(const KArgs &a, int k, const int (&lo
 }
 
 template <int M, int MODE>
-__global__ void __launch_bounds__(kBS, 2) k_mpk(const KArgs a) {
+__global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t s_full[2];
-    __shared__ __align__(8) uint64_t s_empty[2];
-    __shared__ UnitInfo s_u[2];
+    __shared__ __align__(8) uint64_t s_full[kSlots];
+    __shared__ __align__(8) uint64_t s_empty[kSlots];
+    __shared__ UnitInfo s_u[kSlots];
     __shared__ volatile int s_final;  // units handed over in total; -1 while the control warp runs
-    __shared__ int s_done[2];         // compute warps finished with the slot's unit
+    __shared__ int s_done[kSlots];    // compute warps finished with the slot's unit
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double *const sval0 = reinterpret_cast<double *>(smem);
-    int32_t *const scol0 = reinterpret_cast<int32_t *>(smem + 2 * kStageEntries * 8);
+    int32_t *const scol0 = reinterpret_cast<int32_t *>(smem + kSlots * kStageEntries * 8);
 
+    const uint64_t t_start = a.trace ? globaltimer() : 0;
+    __shared__ unsigned long long s_tr[6];  // units, poll ns, failed polls, slot wait ns, unit wait ns, busy ns
+    auto tr_add = [&](int q, unsigned long long v) {
+        if (a.trace) atomicAdd(&s_tr[q], v);
+    };
+    if (tid < 6) s_tr[tid] = 0;
     if (tid == 0) {
         s_final = -1;
-        s_done[0] = 0;
-        s_done[1] = 0;
-        mbar_init(&s_full[0], 1);
-        mbar_init(&s_full[1], 1);
-        mbar_init(&s_empty[0], kCompWarps);
-        mbar_init(&s_empty[1], kCompWarps);
+        for (int q = 0; q < kSlots; ++q) {
+            s_done[q] = 0;
+            mbar_init(&s_full[q], 1);
+            mbar_init(&s_empty[q], kCompWarps);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -287,38 +434,39 @@ __global__ void __launch_bounds__(kBS, 2) k_mpk(const KArgs a) {
     if (warp == 0) {
         // ------------------------------------------------------------------ control warp
         const int32_t *rec = reinterpret_cast<const int32_t *>(a.chunk_rec);
-        bool slot_busy[2] = {false, false};  // a handed-over unit may still be computed
-        int slot_use[2] = {0, 0};            // phase index (i >> 1) of that hand-over
+        bool slot_busy[kSlots] = {};  // a handed-over unit may still be computed
+        int slot_use[kSlots] = {};    // phase index (i / kSlots) of that hand-over
         bool aborted = false;
         auto record_timeout = [&]() {
             if (lane == 0 && atomicExch(a.err, a.epoch) != a.epoch) st_relaxed(a.err + 1, (int)MPK_ERR_TIMEOUT);
         };
         auto unit_at = [&](unsigned int t) -> int { return (int64_t)t < a.nunits ? __ldg(a.units + t) : -1; };
-        // claims run ahead: u_cur (record in lanes), u_nxt, ticket t_nn of the unit after
-        int u_cur = -1, u_nxt = -1;
-        unsigned int t_nn = 0;
+        // claim pipeline, three units deep: unit i (id u_cur, record r_cur), unit i+1 (u_nxt,
+        // r_nxt), unit i+2 (id u_nn, held by lane 0) and the ticket t of unit i+3.  At the end
+        // of iteration i the record of unit i+2, the id of unit i+3 and one more ticket are
+        // fetched, each a full iteration before it is needed.
+        auto rec_at = [&](int un) -> int {
+            return (un >= 0 && lane < kRecInts) ? __ldg(rec + kRecInts * (int64_t)(un >> 5) + lane) : 0;
+        };
+        int u_cur = -1, u_nxt = -1, u_nn = -1;
+        unsigned int t = 0;
         if (lane == 0) {
             const unsigned int t0 = atomicAdd(a.ticket, 1u);
             const unsigned int t1 = atomicAdd(a.ticket, 1u);
-            t_nn = atomicAdd(a.ticket, 1u);
+            const unsigned int t2 = atomicAdd(a.ticket, 1u);
+            t = atomicAdd(a.ticket, 1u);
             u_cur = unit_at(t0);
             u_nxt = unit_at(t1);
+            u_nn = unit_at(t2);
         }
         u_cur = __shfl_sync(0xffffffffu, u_cur, 0);
-        int r_cur = (u_cur >= 0 && lane < 16) ? __ldg(rec + 16 * (int64_t)(u_cur >> 5) + lane) : 0;
+        u_nxt = __shfl_sync(0xffffffffu, u_nxt, 0);
+        int r_cur = rec_at(u_cur);
+        int r_nxt = rec_at(u_nxt);
         int i = 0;
         for (;; ++i) {
             if (u_cur < 0) break;  // no more work
-            const int b = i & 1;
-            // prefetch: record of the next unit, unit after next, next ticket
-            const int un = __shfl_sync(0xffffffffu, u_nxt, 0);
-            const int r_nxt = (un >= 0 && lane < 16) ? __ldg(rec + 16 * (int64_t)(un >> 5) + lane) : 0;
-            int u_nn = -1;
-            unsigned int t_nnn = t_nn;
-            if (lane == 0) {
-                u_nn = unit_at(t_nn);
-                if (u_nn >= 0) t_nnn = atomicAdd(a.ticket, 1u);
-            }
+            const int b = i % kSlots;
             // current unit
             UnitInfo u;
             u.unit = u_cur;
@@ -329,6 +477,9 @@ __global__ void __launch_bounds__(kBS, 2) k_mpk(const KArgs a) {
             u.ebase = (long long)(unsigned int)__shfl_sync(0xffffffffu, r_cur, 4) |
                       ((long long)__shfl_sync(0xffffffffu, r_cur, 5) << 32);
             u.staged = __shfl_sync(0xffffffffu, r_cur, 6);
+            u.nsl = __shfl_sync(0xffffffffu, r_cur, 7);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) u.widths[q] = __shfl_sync(0xffffffffu, r_cur, 16 + q);
             int dlo[kDepRanges], dlen[kDepRanges];
             int total = 0;
 #pragma unroll
@@ -337,12 +488,13 @@ __global__ void __launch_bounds__(kBS, 2) k_mpk(const KArgs a) {
                 dlen[r] = max(0, __shfl_sync(0xffffffffu, r_cur, 9 + 2 * r) - dlo[r] + 1);
                 total += dlen[r];
             }
-            // slot b held unit i-2: wait until it is computed before reusing the slot
+            // slot b held unit i-kSlots: wait until it is computed before reusing the slot
             if (slot_busy[b]) {
                 const uint64_t t0 = globaltimer();
                 bool ok;
                 while (!(ok = mbar_try_wait(&s_empty[b], slot_use[b] & 1)))
                     if (timed_out(t0, a.wait_ns)) break;
+                if (a.trace && lane == 0) tr_add(3, globaltimer() - t0);
                 if (!ok) {
                     record_timeout();
                     aborted = true;
@@ -365,6 +517,7 @@ __global__ void __launch_bounds__(kBS, 2) k_mpk(const KArgs a) {
             if (k > 1) {
                 const uint64_t t0 = globaltimer();
                 while (!deps_ready(a, k, dlo, dlen, total, lane)) {
+                    if (lane == 0) tr_add(2, 1);
                     const bool stop = ld_relaxed(a.err) == a.epoch || timed_out(t0, a.wait_ns);
                     if (__any_sync(0xffffffffu, stop)) {
                         aborted = true;
@@ -372,7 +525,9 @@ __global__ void __launch_bounds__(kBS, 2) k_mpk(const KArgs a) {
                     }
                     __nanosleep(32);
                 }
+                if (a.trace && lane == 0) tr_add(1, globaltimer() - t0);
             }
+            if (lane == 0) tr_add(0, 1);
             if (aborted) {
                 // unit i is not handed over: the compute warps stop before it.  Complete the
                 // slot's phase so that its bulk copy can be waited for, then wait for it.
@@ -383,7 +538,7 @@ __global__ void __launch_bounds__(kBS, 2) k_mpk(const KArgs a) {
                 }
                 if (u.staged) {
                     const uint64_t t1 = globaltimer();
-                    while (!mbar_try_wait(&s_full[b], (i >> 1) & 1))
+                    while (!mbar_try_wait(&s_full[b], (i / kSlots) & 1))
                         if (timed_out(t1, a.wait_ns)) break;
                 }
                 break;
@@ -392,23 +547,43 @@ __global__ void __launch_bounds__(kBS, 2) k_mpk(const KArgs a) {
             __syncwarp();
             if (lane == 0) mbar_arrive(&s_full[b]);
             slot_busy[b] = true;
-            slot_use[b] = i >> 1;
-            // rotate the claim pipeline
-            u_cur = un;
+            slot_use[b] = i / kSlots;
+            // prefetch after the hand-over, so that these loads and the atomic complete during
+            // the next units' staging and polls instead of delaying this unit's fence
+            const int u2 = __shfl_sync(0xffffffffu, u_nn, 0);
+            const int r2 = rec_at(u2);
+            int u3 = -1;
+            unsigned int t_next = t;
+            if (lane == 0) {
+                u3 = unit_at(t);                   // id of unit i+3
+                t_next = atomicAdd(a.ticket, 1u);  // ticket of unit i+4, claimed whether or not it exists
+            }
+            u_cur = u_nxt;
             r_cur = r_nxt;
-            u_nxt = u_nn;
-            t_nn = t_nnn;
+            u_nxt = u2;
+            r_nxt = r2;
+            u_nn = u3;
+            t = t_next;
         }
         if (lane == 0 && s_final < 0) s_final = i;  // units 0..i-1 were handed over
     } else {
         // ------------------------------------------------------------------ compute warps
         const int cw = warp - 1;
+        Prefetch<M> pf;
+        pf.unit = -1;
         for (int i = 0;; ++i) {
-            const int b = i & 1;
+            const int b = i % kSlots;
+            // The next unit may depend on the pending one (the control warp hands it over
+            // only when its dependencies are published), so when it is not ready at once,
+            // finish the pending unit first instead of waiting with it unpublished.
+            if (pf.unit >= 0 && !mbar_try_wait(&s_full[b], (i / kSlots) & 1)) {
+                phase_b<M, MODE>(a, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane);
+                pf.unit = -1;
+            }
             const uint64_t t0 = globaltimer();
             bool got = false, stop = false;
             while (true) {
-                if (mbar_try_wait(&s_full[b], (i >> 1) & 1)) {
+                if (mbar_try_wait(&s_full[b], (i / kSlots) & 1)) {
                     got = true;
                     break;
                 }
@@ -428,21 +603,31 @@ __global__ void __launch_bounds__(kBS, 2) k_mpk(const KArgs a) {
                 if (lane == 0 && atomicExch(a.err, a.epoch) != a.epoch) st_relaxed(a.err + 1, (int)MPK_ERR_TIMEOUT);
                 break;
             }
-            const UnitInfo u = s_u[b];
-            compute_unit<M, MODE>(a, u, sval0 + b * kStageEntries, scol0 + b * kStageEntries, cw, lane);
-            __syncwarp();
-            if (lane == 0) {
-                // the last compute warp to finish the unit publishes it (release at gpu scope
-                // after the other warps' stores were ordered at block scope)
-                __threadfence_block();
-                if (atomicAdd(&s_done[b], 1) == kCompWarps - 1) {
-                    s_done[b] = 0;
-                    fence_acq_rel_gpu();
-                    if (u.unit != a.drop_unit)
-                        st_relaxed(a.flags + (int64_t)(u.unit & 31) * a.nchunks + (u.unit >> 5), a.epoch);
-                }
-                mbar_arrive(&s_empty[b]);
+            uint64_t t_got = 0;
+            if (a.trace) {
+                t_got = globaltimer();
+                if (lane == 0) tr_add(4, t_got - t0);
             }
+            if (MPK_COMPUTE_PIPELINE) {
+                Prefetch<M> nf;
+                phase_a<M>(a, s_u[b], b, scol0 + b * kStageEntries, cw, lane, nf);
+                if (pf.unit >= 0) phase_b<M, MODE>(a, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane);
+                pf = nf;
+            } else {
+                phase_a<M>(a, s_u[b], b, scol0 + b * kStageEntries, cw, lane, pf);
+                phase_b<M, MODE>(a, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane);
+                pf.unit = -1;
+            }
+            if (a.trace && lane == 0) tr_add(5, globaltimer() - t_got);
+        }
+        if (pf.unit >= 0) phase_b<M, MODE>(a, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane);
+    }
+    if (a.trace) {
+        __syncthreads();
+        if (tid == 0) {
+            for (int q = 0; q < 6; ++q) atomicAdd(a.trace + q, s_tr[q]);
+            atomicAdd(a.trace + 6, (unsigned long long)(globaltimer() - t_start));
+            if (blockIdx.x == 0) atomicAdd(a.trace + 7, 1ull);
         }
     }
     // ---- exit: the last block resets the ticket for the next launch on the stream
@@ -461,15 +646,13 @@ __global__ void __launch_bounds__(kBS, 2) k_mpk(const KArgs a) {
 // ----------------------------------------------------------------------------- K-SpMV
 // One plain SpMV over the plan's sliced copy: y = A x (plan order), same row body with
 // direct (read-only cached) loads of the entries.  Blocks walk chunks, warps walk the
-// chunk's slices.  Optionally also writes yorig[perm[r]].
+// chunk's slices.
 template <int M>
 __global__ void __launch_bounds__(kSpmvBS) k_spmv(const double *__restrict__ val, const int32_t *__restrict__ col,
                                                   const int64_t *__restrict__ slice_ptr,
-                                                  const int32_t *__restrict__ rowlen,
                                                   const int32_t *__restrict__ chunk_row,
                                                   const int32_t *__restrict__ chunk_slice, int32_t nchunks,
-                                                  const double *x, double *y, double *yorig,
-                                                  const int32_t *__restrict__ perm) {
+                                                  const double *x, double *y) {
     const int lane = threadIdx.x & 31;
     for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
         const int r0 = chunk_row[c], r1 = chunk_row[c + 1], sl0 = chunk_slice[c];
@@ -477,16 +660,11 @@ __global__ void __launch_bounds__(kSpmvBS) k_spmv(const double *__restrict__ val
         for (int sl = threadIdx.x >> 5; sl < nsl; sl += kSpmvBS / 32) {
             const int64_t r = (int64_t)r0 + 32 * sl + lane;
             if (r < r1) {
-                const int64_t off = slice_ptr[sl0 + sl] + lane;
+                const int64_t s0 = slice_ptr[sl0 + sl], s1 = slice_ptr[sl0 + sl + 1];
                 double w[M];
-                row_sum<M, Batch<M>::B>(GVal{val}, GCol{col}, off, rowlen[r], x, w);
+                row_sum<M, Batch<M>::B>(GVal{val}, GCol{col}, s0 + lane, (int)((s1 - s0) >> 5), x, w);
 #pragma unroll
                 for (int i = 0; i < M; ++i) y[r * M + i] = w[i];
-                if (yorig) {
-                    double *yo = yorig + (int64_t)perm[r] * M;
-#pragma unroll
-                    for (int i = 0; i < M; ++i) yo[i] = w[i];
-                }
             }
         }
     }
@@ -541,6 +719,44 @@ void launch_scatter_rows(const double *src, const int32_t *iperm, double *dst, i
     launch_gather_rows(src, iperm, dst, n, m, s);
 }
 
+// Y[k][i] = W[k][iperm[i]] for k = 1..p: the powers computed in plan order, written in the
+// matrix's own order.  Stores are full, coalesced rows of the output; the gathered reads
+// come from rows that neighbouring original rows map to (for a BFS order these sit a few
+// levels apart and share cache sectors with the reads of nearby original rows).  One block
+// per SM walks tiles of kScatterTile consecutive original rows, power by power, so that the
+// sectors a tile reads stay in the SM's L1 until its other rows use them.
+constexpr int kScatterBS = 1024, kScatterItems = 16, kScatterTile = kScatterBS * kScatterItems;
+
+__global__ void __launch_bounds__(kScatterBS, 1)
+    k_scatter_powers(const double *W, const int32_t *__restrict__ iperm, double *Y, int32_t n, int32_t m, int32_t p) {
+    const int64_t nm = (int64_t)n * m;
+    for (int64_t base = (int64_t)blockIdx.x * kScatterTile; base < n; base += (int64_t)gridDim.x * kScatterTile) {
+        int32_t src[kScatterItems];
+#pragma unroll
+        for (int q = 0; q < kScatterItems; ++q) {
+            const int64_t i = base + (int64_t)q * kScatterBS + threadIdx.x;
+            src[q] = i < n ? __ldg(iperm + i) : -1;
+        }
+        for (int k = 1; k <= p; ++k) {
+            const double *w = W + k * nm;
+            double *y = Y + k * nm;
+#pragma unroll
+            for (int q = 0; q < kScatterItems; ++q) {
+                const int64_t i = base + (int64_t)q * kScatterBS + threadIdx.x;
+                if (src[q] >= 0)
+                    for (int c = 0; c < m; ++c) y[i * m + c] = w[(int64_t)src[q] * m + c];
+            }
+        }
+    }
+}
+
+void launch_scatter_powers(const double *W, const int32_t *iperm, double *Y, int32_t n, int32_t m, int32_t p,
+                           cudaStream_t s) {
+    if (n <= 0 || p <= 0) return;
+    k_scatter_powers<<<device_sms(), kScatterBS, 0, s>>>(W, iperm, Y, n, m, p);
+    MPK_LAUNCHED();
+}
+
 void launch_cheb_init(const double *v0, double *acc, int32_t n, int32_t m, double c0re, double c0im, int cplx,
                       cudaStream_t s) {
     if (n <= 0) return;
@@ -552,11 +768,10 @@ void launch_cheb_init(const double *v0, double *acc, int32_t n, int32_t m, doubl
 template <int M, int MODE> static void *mpk_fn() { return (void *)k_mpk<M, MODE>; }
 
 static void *select_mpk(int mode, int m) {
-#define SEL(MM)                                            \
-    if (m == MM) {                                         \
-        if (mode == MODE_PLAN) return mpk_fn<MM, MODE_PLAN>();       \
-        if (mode == MODE_SCATTER) return mpk_fn<MM, MODE_SCATTER>(); \
-        return mpk_fn<MM, MODE_CHEB>();                    \
+#define SEL(MM)                                                  \
+    if (m == MM) {                                               \
+        if (mode == MODE_POWERS) return mpk_fn<MM, MODE_POWERS>(); \
+        return mpk_fn<MM, MODE_CHEB>();                          \
     }
     SEL(1) SEL(2) SEL(4) SEL(8)
 #undef SEL
@@ -564,7 +779,7 @@ static void *select_mpk(int mode, int m) {
 }
 
 int occupancy_grid(int mode, int m) {
-    static int cache[3][9] = {};
+    static int cache[2][9] = {};
     if (cache[mode][m]) return cache[mode][m];
     void *fn = select_mpk(mode, m);
     MPK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
@@ -584,14 +799,13 @@ void launch_mpk(const Plan &P, KArgs &a, int mode, cudaStream_t s) {
     MPK_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(kBS), args, kSmemBytes, s));
 }
 
-void launch_spmv(const Plan &P, const double *x, double *y, double *yorig, int64_t orig_off, cudaStream_t s) {
+void launch_spmv(const Plan &P, const double *x, double *y, cudaStream_t s) {
     if (P.num_chunks <= 0) return;
-    int grid = P.num_chunks;
-    double *yo = yorig ? yorig + orig_off : nullptr;
-#define L(MM)                                                                                                 \
-    case MM:                                                                                                  \
-        k_spmv<MM><<<grid, kSpmvBS, 0, s>>>(P.val, P.col, P.slice_ptr, P.rowlen, P.chunk_row, P.chunk_slice,     \
-                                        P.num_chunks, x, y, yo, P.perm);                                      \
+    const int grid = P.num_chunks;
+#define L(MM)                                                                                               \
+    case MM:                                                                                                \
+        k_spmv<MM><<<grid, kSpmvBS, 0, s>>>(P.val, P.col, P.slice_ptr, P.chunk_row, P.chunk_slice, P.num_chunks, \
+                                            x, y);                                                         \
         break;
     switch (P.m) {
         L(1) L(2) L(4) L(8) default : fail(MPK_ERR_UNSUPPORTED, "nrhs %d", P.m);

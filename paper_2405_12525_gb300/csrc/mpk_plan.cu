@@ -161,19 +161,36 @@ __global__ void k_dep_ranges(int32_t nchunks, const int2 *hull, const int64_t *w
     }
 }
 
-// One 64-byte record per chunk with everything the kernel's control warp needs:
-// [row0, row1, slice0, padded entries, first entry (lo, hi 32 bits), staged, 0,
-//  kDepRanges (lo, hi) dependency ranges].
+// One record of kRecInts ints per chunk with everything the kernel's control warp needs:
+// [row0, row1, slice0, padded entries, first entry (lo, hi 32 bits), staged, slices,
+//  kDepRanges (lo, hi) dependency ranges, slice widths as bytes].  A chunk is staged in
+// shared memory when its entries fit a buffer and its widths fit the record.
 __global__ void k_chunk_records(int32_t nchunks, const int32_t *chunk_row, const int32_t *chunk_slice,
-                                const int64_t *slice_ptr, const int4 *ranges, int4 *rec) {
+                                const int64_t *slice_ptr, const int4 *ranges, int32_t *rec) {
     for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nchunks; c += gridDim.x * blockDim.x) {
-        const int64_t e0 = slice_ptr[chunk_slice[c]], e1 = slice_ptr[chunk_slice[c + 1]];
+        const int32_t sl0 = chunk_slice[c], sl1 = chunk_slice[c + 1], nsl = sl1 - sl0;
+        const int64_t e0 = slice_ptr[sl0], e1 = slice_ptr[sl1];
         const int32_t cnt = (int32_t)(e1 - e0);
-        rec[4 * c + 0] = make_int4(chunk_row[c], chunk_row[c + 1], chunk_slice[c], cnt);
-        rec[4 * c + 1] = make_int4((int32_t)(e0 & 0xffffffffLL), (int32_t)(e0 >> 32),
-                                   (cnt > 0 && cnt <= kStageEntries) ? 1 : 0, 0);
-        rec[4 * c + 2] = ranges[2 * c];
-        rec[4 * c + 3] = ranges[2 * c + 1];
+        const int staged = cnt > 0 && cnt <= kStageEntries && nsl <= kRecSlices;
+        int32_t *o = rec + (int64_t)kRecInts * c;
+        o[0] = chunk_row[c];
+        o[1] = chunk_row[c + 1];
+        o[2] = sl0;
+        o[3] = cnt;
+        o[4] = (int32_t)(e0 & 0xffffffffLL);
+        o[5] = (int32_t)(e0 >> 32);
+        o[6] = staged;
+        o[7] = nsl;
+        const int4 r0 = ranges[2 * c], r1 = ranges[2 * c + 1];
+        o[8] = r0.x; o[9] = r0.y; o[10] = r0.z; o[11] = r0.w;
+        o[12] = r1.x; o[13] = r1.y; o[14] = r1.z; o[15] = r1.w;
+        uint32_t wb[kRecSlices / 4] = {0, 0, 0, 0};
+        if (staged)
+            for (int32_t q = 0; q < nsl; ++q) {
+                const uint32_t w = (uint32_t)((slice_ptr[sl0 + q + 1] - slice_ptr[sl0 + q]) >> 5);
+                wb[q >> 2] |= (w & 0xffu) << (8 * (q & 3));
+            }
+        for (int q = 0; q < kRecSlices / 4; ++q) o[16 + q] = (int32_t)wb[q];
     }
 }
 
@@ -355,7 +372,7 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         P->val = P->arena.alloc_n<double>(P->padded + 32);
         P->col = P->arena.alloc_n<int32_t>(P->padded + 32);
         MPK_CUDA(cudaMemsetAsync(P->val, 0, sizeof(double) * (size_t)(P->padded + 32), s));
-        MPK_CUDA(cudaMemsetAsync(P->col, 0, sizeof(int32_t) * (size_t)(P->padded + 32), s));
+        MPK_CUDA(cudaMemsetAsync(P->col, 0xff, sizeof(int32_t) * (size_t)(P->padded + 32), s));  // padding: col = -1
         P->dep = P->arena.alloc_n<int2>(NC > 0 ? NC : 1);
         if (NC > 0) {
             k_dep_init<<<grid_n(NC), 256, 0, s>>>(P->dep, NC);
@@ -399,10 +416,10 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
             }
         }
 
-        P->chunk_rec = P->arena.alloc_n<int4>(4 * (int64_t)(NC > 0 ? NC : 1));
+        P->chunk_rec = reinterpret_cast<int4 *>(P->arena.alloc_n<int32_t>((int64_t)kRecInts * (NC > 0 ? NC : 1)));
         if (NC > 0) {
             k_chunk_records<<<grid_n(NC), 256, 0, s>>>(NC, P->chunk_row, P->chunk_slice, P->slice_ptr, P->dep_ranges,
-                                                      P->chunk_rec);
+                                                      reinterpret_cast<int32_t *>(P->chunk_rec));
             MPK_LAUNCHED();
         }
 
@@ -427,9 +444,14 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         // ---- synchronisation state and vector workspace
         P->flags = P->arena.alloc_n<int32_t>((int64_t)(pmax + 1) * (NC > 0 ? NC : 1));
         MPK_CUDA(cudaMemsetAsync(P->flags, 0, sizeof(int32_t) * (size_t)(pmax + 1) * (NC > 0 ? NC : 1), s));
+        if (o->trace) {
+            P->trace = P->arena.alloc_n<unsigned long long>(MPK_TRACE_COUNTERS);
+            MPK_CUDA(cudaMemsetAsync(P->trace, 0, sizeof(unsigned long long) * MPK_TRACE_COUNTERS, s));
+        }
         P->ctl = P->arena.alloc_n<unsigned int>(4);
         MPK_CUDA(cudaMemsetAsync(P->ctl, 0, 4 * sizeof(unsigned int), s));
-        P->work = P->arena.alloc_n<double>(4 * (int64_t)n * m + 1);
+        P->work_slots = std::max(pmax + 1, 4);  // all powers (original order) or ring of 3 + accumulator
+        P->work = P->arena.alloc_n<double>((int64_t)P->work_slots * n * m + 1);
         MPK_CUDA(cudaStreamSynchronize(s));  // host vectors above must outlive their copies
     } catch (...) {
         P->arena.release();
