@@ -163,6 +163,24 @@ void mpk_plan_destroy(mpk_plan_t *P);
  * ------------------------------------------------------------------------------------- */
 mpk_status mpk_apply(const mpk_plan_t *P, const double *X, int32_t p, double *Y, mpk_stream stream);
 
+/* mpk_apply_noalloc: mpk_apply for callers that must not allocate device memory while the
+ * call runs (the paper has no counterpart).  Such callers include code running while a
+ * device allocator is locked or must keep a fixed footprint, and latency-critical loops that
+ * cannot afford the implicit device synchronisation of cudaMalloc/cudaFree.  The plan is
+ * built beforehand and must use MPK_ORDER_PLAN (or no levels); X, p and Y are as for
+ * mpk_apply.  The kernel's synchronisation state lives in one fixed array of 2^20 32-bit words
+ * (4 MiB) of device memory that the library declares statically, held by every GPU that
+ * loads the library until the process exits; a call needs 4 + (p+1) * num_chunks words and
+ * fails with MPK_ERR_TOO_LARGE beyond that (larger chunk_rows means fewer chunks).  The
+ * call allocates nothing: it clears the part of the array it uses, launches the kernel and,
+ * if `status` (device int, caller-owned, may be NULL) is given, writes MPK_OK or
+ * MPK_ERR_TIMEOUT there when the work completes on `stream`.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress); make that first call before
+ * any stream capture.  All calls on a device share the array: calls that overlap on the
+ * GPU (other streams, other threads) race and must be serialised by the caller. */
+mpk_status mpk_apply_noalloc(const mpk_plan_t *P, const double *X, int32_t p, double *Y,
+                             int32_t *status, mpk_stream stream);
+
 /* Plain comparator (Alg. 1 without halo exchange): p separate SpMV launches over the
  * plan's matrix copy, same row arithmetic as mpk_apply.  Arguments as for mpk_apply. */
 mpk_status mpk_spmv_powers(const mpk_plan_t *P, const double *X, int32_t p, double *Y,

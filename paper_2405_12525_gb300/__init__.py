@@ -32,7 +32,7 @@ EXPORTED_SYMBOLS = [
     "mpk_build_levels", "mpk_levels_get", "mpk_levels_destroy", "mpk_plan_opts_default", "mpk_plan",
     "mpk_plan_describe", "mpk_plan_export_csr", "mpk_plan_destroy", "mpk_apply", "mpk_spmv_powers",
     "mpk_cheb_filter", "mpk_sync_status", "mpk_probe_load", "mpk_probe_dfma", "mpk_device_info",
-    "mpk_status_string", "mpk_last_error", "mpk_debug_drop_release", "mpk_read_trace",
+    "mpk_status_string", "mpk_last_error", "mpk_debug_drop_release", "mpk_read_trace", "mpk_apply_noalloc",
 ]
 
 
@@ -97,6 +97,7 @@ def load():
         "mpk_device_info": [C.POINTER(i32), C.POINTER(i64)],
         "mpk_debug_drop_release": [vp, i32, i32],
         "mpk_read_trace": [vp, vp, vp],
+        "mpk_apply_noalloc": [vp, vp, i32, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -285,6 +286,15 @@ class Plan:
         if Y is None:
             Y = torch.empty((p + 1, self.n, self.nrhs), dtype=torch.float64, device=X.device)
         _check(self._lib.mpk_apply(self._h, _ptr(X), int(p), _ptr(Y), _stream(stream)))
+        return Y
+
+    def apply_noalloc(self, X, p: int, Y, status=None, stream=None):
+        """mpk_apply without device allocation during the call (plan-order plans only).
+        Y must be given; status, if given, is a one-element int32 CUDA tensor that receives
+        the launch's status code."""
+        self._block(X)
+        _check(self._lib.mpk_apply_noalloc(self._h, _ptr(X), int(p), _ptr(Y), _ptr(status) if status is not None
+                                           else None, _stream(stream)))
         return Y
 
     def spmv_powers(self, X, p: int, Y=None, stream=None):

@@ -28,13 +28,6 @@ using namespace mpk;
         return MPK_ERR_CUDA;                                           \
     }
 
-struct mpk_levels_s {
-    Levels *impl;
-};
-struct mpk_plan_s {
-    Plan *impl;
-};
-
 static cudaStream_t as_stream(mpk_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 
 // ---------------------------------------------------------------------------------------- levels

@@ -211,3 +211,11 @@ void probe_load(const void *buf, int64_t bytes, int reps, int ctas_per_sm, int32
 void probe_dfma(int blocks, int iters, double *sink, cudaStream_t s);
 
 }  // namespace mpk
+
+// handles behind the opaque types of the C ABI
+struct mpk_levels_s {
+    mpk::Levels *impl;
+};
+struct mpk_plan_s {
+    mpk::Plan *impl;
+};

@@ -1,0 +1,113 @@
+// mpk_apply_noalloc: the level-blocked MPK of mpk_apply for callers that must not allocate
+// device memory during a call.  Examples are code that runs while an allocator is
+// locked or must not grow its footprint, latency-critical loops that forbid the implicit
+// synchronisation cudaMalloc/cudaFree cause, and hosts that hand the library only
+// pre-allocated buffers.  The plan is built beforehand; at call time the kernel's
+// synchronisation state (per-chunk completion flags, ticket, exit counter, error word)
+// lives in one fixed array in device memory instead of in the plan.
+#include "mpk_internal.h"
+
+#include <cstring>
+#include <mutex>
+
+namespace mpk {
+
+// Scratch shared by every call on a device: kNoAllocInts 32-bit words (4 MiB).  Every GPU
+// that loads the library holds this array until the process exits.
+constexpr int64_t kNoAllocInts = int64_t(1) << 20;
+static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocInts];
+
+// Host-side device address of the array, looked up once per device (the symbol's name is
+// only a host-side stand-in and must not be passed to a kernel).
+constexpr int kMaxDevices = 64;
+static int32_t *g_scratch_addr[kMaxDevices] = {};
+static std::mutex g_scratch_mutex;
+
+static int32_t *scratch_address() {
+    int dev = 0;
+    MPK_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) fail(MPK_ERR_UNSUPPORTED, "device index %d beyond %d", dev, kMaxDevices);
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_addr[dev]) {
+        void *ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr)
+            fail(MPK_ERR_CUDA, "cudaGetSymbolAddress of the no-allocation scratch failed: %s", cudaGetErrorString(e));
+        g_scratch_addr[dev] = static_cast<int32_t *>(ptr);
+    }
+    return g_scratch_addr[dev];
+}
+
+// copies the launch's error code (0 or MPK_ERR_TIMEOUT) to the caller's status word
+__global__ void k_noalloc_status(const int32_t *err, int32_t *status) {
+    *status = (err[0] == 1) ? (err[1] ? err[1] : (int32_t)MPK_ERR_TIMEOUT) : (int32_t)MPK_OK;
+}
+
+}  // namespace mpk
+
+using namespace mpk;
+
+extern "C" mpk_status mpk_apply_noalloc(const mpk_plan_t *Ph, const double *X, int32_t p, double *Y,
+                                        int32_t *status, mpk_stream stream) {
+    try {
+        if (!Ph || !Ph->impl) fail(MPK_ERR_INVALID, "plan is NULL");
+        const Plan &P = *Ph->impl;
+        if (!(P.identity || P.order == MPK_ORDER_PLAN))
+            fail(MPK_ERR_UNSUPPORTED, "mpk_apply_noalloc needs a plan in MPK_ORDER_PLAN (or without levels)");
+        if (p < 1 || p > P.p_max) fail(MPK_ERR_INVALID, "p = %d outside [1, p_max = %d]", p, P.p_max);
+        if (P.n > 0 && (!X || !Y)) fail(MPK_ERR_INVALID, "NULL X or Y");
+        // scratch layout: [0..3] ticket, exit count, error epoch, error code; then the
+        // completion flags of powers 0..p for every chunk
+        const int64_t need = 4 + (int64_t)(p + 1) * (P.num_chunks > 0 ? P.num_chunks : 1);
+        if (need > kNoAllocInts)
+            fail(MPK_ERR_TOO_LARGE,
+                 "mpk_apply_noalloc needs %lld scratch words for %d chunks and p = %d; the fixed scratch holds %lld "
+                 "(use mpk_apply, or fewer chunks: larger chunk_rows)",
+                 (long long)need, P.num_chunks, p, (long long)kNoAllocInts);
+        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+        int32_t *scratch = scratch_address();
+        // the previous call's flags and counters are still in the array: start from zero
+        MPK_CUDA(cudaMemsetAsync(scratch, 0, sizeof(int32_t) * (size_t)need, s));
+        if (P.n > 0) {
+            KArgs a;
+            std::memset(&a, 0, sizeof(a));
+            a.val = P.val;
+            a.col = P.col;
+            a.slice_ptr = P.slice_ptr;
+            a.rowlen = P.rowlen;
+            a.chunk_row = P.chunk_row;
+            a.chunk_slice = P.chunk_slice;
+            a.dep = P.dep;
+            a.dep_ranges = P.dep_ranges;
+            a.chunk_rec = P.chunk_rec;
+            a.n = P.n;
+            a.nchunks = P.num_chunks;
+            a.units = P.units + P.unit_off[p];
+            a.nunits = P.unit_off[p + 1] - P.unit_off[p];
+            a.flags = scratch + 4;
+            a.epoch = 1;
+            a.ticket = reinterpret_cast<unsigned int *>(scratch);
+            a.exit_count = reinterpret_cast<unsigned int *>(scratch + 1);
+            a.err = scratch + 2;
+            a.wait_ns = P.wait_ns;
+            a.drop_unit = -1;
+            a.trace = nullptr;
+            a.x0 = X;
+            a.ybase = Y;
+            a.ystride = (int64_t)P.n * P.m;
+            a.ring = p + 1;
+            a.y0copy = (Y != X) ? Y : nullptr;
+            launch_mpk(P, a, 0, s);
+        }
+        if (status) {
+            k_noalloc_status<<<1, 1, 0, s>>>(scratch + 2, status);
+            MPK_LAUNCHED();
+        }
+        return MPK_OK;
+    } catch (const Fail &f) {
+        return f.status;
+    } catch (...) {
+        set_error("unexpected internal error");
+        return MPK_ERR_CUDA;
+    }
+}
