@@ -204,11 +204,17 @@ mpk_status mpk_cheb_filter(const mpk_plan_t *P, const double *X, int32_t degree,
 
 /* Timing counters of a plan built with opts.trace = 1, accumulated over all launches since
  * the plan was created (host array of MPK_TRACE_COUNTERS int64): 0 units, 1 ns the control
- * warps spent polling dependencies, 2 failed dependency checks, 3 ns control warps waited for
- * a free slot, 4 ns compute warps waited for a unit, 5 ns compute warps spent computing,
- * 6 ns summed over blocks from start to exit, 7 launches.  Synchronises `stream`.
- * MPK_ERR_UNSUPPORTED if the plan has no trace. */
-#define MPK_TRACE_COUNTERS 8
+ * warps spent polling dependencies, 2 units whose dependencies were not all met at the first
+ * check, 3 ns control warps waited for a free slot, 4 ns compute warps waited for a unit,
+ * 5 ns compute warps spent on units, 6 ns summed over blocks from start to exit, 7 launches,
+ * 8 SM cycles control warps spent staging, 9 cycles in the acquire fence and hand-over,
+ * 10 cycles fetching later tickets, records and flags, 11 cycles decoding the current record,
+ * 12 cycles compute warps spent until the x entries of their first batch arrived, 13 cycles
+ * from then to the end of the unit (FMAs, stores, publication), 14 ns from a hand-over to
+ * the first compute warp seeing it (units the warp waited for), 15 such units, 16 SM cycles
+ * summed over blocks from start to exit (cycles per ns = counter 16 / counter 6).
+ * Synchronises `stream`.  MPK_ERR_UNSUPPORTED if the plan has no trace. */
+#define MPK_TRACE_COUNTERS 17
 mpk_status mpk_read_trace(const mpk_plan_t *P, int64_t *counters, mpk_stream stream);
 
 /* Synchronises `stream` and reports a device-side failure of the plan's calls since the

@@ -328,12 +328,14 @@ class Plan:
         _check(self._lib.mpk_debug_drop_release(self._h, int(chunk), int(k)))
 
     TRACE_FIELDS = ("units", "ctrl_poll_ns", "ctrl_poll_retries", "ctrl_slot_wait_ns", "comp_wait_ns",
-                    "comp_busy_ns", "block_ns", "launches")
+                    "comp_busy_ns", "block_ns", "launches", "ctrl_stage_cyc", "ctrl_handover_cyc",
+                    "ctrl_prefetch_cyc", "ctrl_decode_cyc", "comp_gather_cyc", "comp_fma_cyc",
+                    "handover_lag_ns", "handover_lag_units", "block_cyc")
 
     def read_trace(self, stream=None) -> dict:
         """Timing counters of a plan built with trace=1 (accumulated over its launches)."""
         import numpy as np
-        out = np.zeros(8, dtype=np.int64)
+        out = np.zeros(len(self.TRACE_FIELDS), dtype=np.int64)
         _check(self._lib.mpk_read_trace(self._h, out.ctypes.data, _stream(stream)))
         return dict(zip(self.TRACE_FIELDS, out.tolist()))
 

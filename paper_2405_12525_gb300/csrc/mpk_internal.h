@@ -95,6 +95,8 @@ constexpr int kMaxP = 31;
 constexpr int kStageEntries = MPK_STAGE_ENTRIES;
 // dependency ranges kept per chunk (exact sets compressed to this many index ranges)
 constexpr int kDepRanges = 4;
+// trace counters accumulated in shared memory (the last one, SM cycles, is added directly)
+constexpr int kTraceShared = MPK_TRACE_COUNTERS - 1;
 // compute warps of the level-blocked kernel; the default chunk is one 32-row slice per warp
 #ifndef MPK_COMP_WARPS
 #define MPK_COMP_WARPS 15
@@ -196,7 +198,7 @@ void launch_scatter_rows(const double *src, const int32_t *iperm, double *dst, i
                          cudaStream_t s);
 void launch_cheb_init(const double *v0, double *acc, int32_t n, int32_t m, double c0re, double c0im,
                       int complex_coeff, cudaStream_t s);
-int occupancy_grid(int mode, int m);
+int occupancy_grid(int mode, int m, bool trace);
 
 // level builder (mpk_levels.cu)
 Levels *build_levels(const mpk_csr *A, int32_t root, cudaStream_t s);

@@ -18,12 +18,8 @@ namespace mpk {
 constexpr int kBS = 32 * (1 + kCompWarps);  // level-blocked kernel: 1 control warp + compute warps
 constexpr int kBlocksPerSM = 1024 / kBS;     // register budget: 64 per thread at 2048 threads per SM
 constexpr int kSpmvBS = 256;        // threads per block of the plain SpMV kernel
-#ifndef MPK_COMPUTE_PIPELINE
-#define MPK_COMPUTE_PIPELINE 0
-#endif
-// Staging slots: the control warp fills one while the compute warps hold the others (two
-// when compute warps software-pipeline consecutive units, one otherwise).
-constexpr int kSlots = MPK_COMPUTE_PIPELINE ? 3 : 2;
+// Staging slots: the control warp fills one while the compute warps work on the other.
+constexpr int kSlots = 2;
 constexpr int kStageBytes = kStageEntries * 12;          // one slot: values + columns
 constexpr int kSmemBytes = kSlots * kStageBytes;
 
@@ -206,10 +202,10 @@ __device__ __forceinline__ void row_epilogue(const KArgs &a, int k, int64_t r, c
 
 // ----------------------------------------------------------------------------- K-MPK
 // Work unit = (row chunk c, local power k).  Units are claimed through one atomic ticket
-// in the order of the unit table, which lists the Lp-diagram cells (group g, power k)
-// diagonal by diagonal (g + k ascending) and, inside a diagonal, k ascending.  Every
-// dependency of a unit (chunks holding the rows it reads, at power k-1) lies on an earlier
-// diagonal or earlier in the same one, so it has a smaller ticket: the unit holding the
+// in the order of the unit table, which lists the Lp-diagram cells (group g, power k) line
+// by line (g + kSlotSkew * k ascending) and, inside a line, k ascending.  Every dependency
+// of a unit (chunks holding the rows it reads, at power k-1) lies on an earlier line, so it
+// has a smaller ticket: the unit holding the
 // smallest unfinished ticket can always run, whichever blocks are resident, and the
 // schedule cannot deadlock.  A finished unit publishes flags[k][c] = epoch (release); a
 // unit waits until the flags of its dependency ranges at power k-1 equal the epoch
@@ -220,9 +216,8 @@ __device__ __forceinline__ void row_epilogue(const KArgs &a, int k, int64_t r, c
 // warps 1..kCompWarps (compute) compute rows, and the last of them to finish a unit
 // publishes its completion flag.  Slot b has two mbarriers: full[b] completes when the
 // entries have landed and the dependencies are met, empty[b] when every compute warp is
-// done with the slot.  The control warp prepares unit i+1 while compute warps finish unit
-// i-1 and start unit i (their software pipeline holds two slots); its
-// claims run three units ahead (tickets, unit ids and chunk records are fetched an
+// done with the slot.  The control warp prepares unit i+1 while compute warps work on unit
+// i; its claims run three units ahead (tickets, unit ids and chunk records are fetched an
 // iteration before they are needed), so only the dependency poll is on its critical path.
 // A block processes its tickets in claim order and claims are increasing, so the block
 // holding the smallest unfinished ticket is working on it: the schedule stays deadlock
@@ -252,12 +247,9 @@ __device__ __forceinline__ int slice_width(const int (&w)[4], int q) {
 // A compute warp handles a unit in two phases.  Phase A reads the column indices of the
 // warp's first row batch from shared memory and issues the x gathers; phase B runs the
 // FMAs on those x values, finishes any further batches or slices, stores the results and
-// publishes the unit.  By default phase B follows phase A of the same unit.  Built with
-// MPK_COMPUTE_PIPELINE=1, phase B of unit i-1 runs after phase A of unit i, so the gather
-// latency of one unit hides behind the FMA chains of the previous one (three slots); when
-// the next unit is not ready yet, the pending unit is finished before waiting (a unit can
-// depend on the previous unit of the same block), so the pipeline never holds back a flag
-// that the control warp waits for.
+// publishes the unit.  Phase B directly follows phase A of the same unit: a warp holds no
+// unit across a wait, so its lanes, which wait on the slot's mbarrier one by one, always
+// work on the same unit.
 template <int M> struct Prefetch {
     static constexpr int B = Batch<M>::B;
     int unit;             // -1: nothing pending
@@ -376,34 +368,53 @@ __device__ __forceinline__ void phase_b(const KArgs &a, const Prefetch<M> &pf, c
     }
 }
 
+// dependency flags v0 .. v0+127 of a unit (4 per lane); flags past `total` read as ready
+__device__ __forceinline__ void dep_load(const KArgs &a, int k, const int (&lo)[kDepRanges],
+                                         const int (&len)[kDepRanges], int total, int v0, int lane, int (&got)[4]) {
+    const int32_t *f = a.flags + (int64_t)(k - 1) * a.nchunks;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int v = v0 + 32 * q + lane;
+        int idx = -1;
+        if (v < total) {
+#pragma unroll
+            for (int r = 0; r < kDepRanges; ++r) {
+                if (idx < 0 && v < len[r]) idx = lo[r] + v;
+                if (idx < 0) v -= len[r];
+            }
+        }
+        got[q] = idx >= 0 ? ld_relaxed(f + idx) : a.epoch;
+    }
+}
+
 // all lanes of the control warp: true when every flag of the unit's ranges equals epoch
 __device__ __forceinline__ bool deps_ready(const KArgs &a, int k, const int (&lo)[kDepRanges],
                                            const int (&len)[kDepRanges], int total, int lane) {
-    const int32_t *f = a.flags + (int64_t)(k - 1) * a.nchunks;
     bool ok = true;
     for (int v0 = 0; v0 < total; v0 += 128) {
         int got[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            int v = v0 + 32 * q + lane;
-            int idx = -1;
-            if (v < total) {
-#pragma unroll
-                for (int r = 0; r < kDepRanges; ++r) {
-                    if (idx < 0 && v < len[r]) idx = lo[r] + v;
-                    if (idx < 0) v -= len[r];
-                }
-            }
-            got[q] = idx >= 0 ? ld_relaxed(f + idx) : a.epoch;
-        }
+        dep_load(a, k, lo, len, total, v0, lane, got);
 #pragma unroll
         for (int q = 0; q < 4; ++q) ok = ok && got[q] == a.epoch;
     }
     return __all_sync(0xffffffffu, ok);
 }
 
-template <int M, int MODE>
+// dependency ranges of a chunk record (ints 8..15, shuffled from the lanes holding them)
+__device__ __forceinline__ int dep_ranges_of(int rec, int (&lo)[kDepRanges], int (&len)[kDepRanges]) {
+    int total = 0;
+#pragma unroll
+    for (int r = 0; r < kDepRanges; ++r) {
+        lo[r] = __shfl_sync(0xffffffffu, rec, 8 + 2 * r);
+        len[r] = max(0, __shfl_sync(0xffffffffu, rec, 9 + 2 * r) - lo[r] + 1);
+        total += len[r];
+    }
+    return total;
+}
+
+template <int M, int MODE, bool TRACE>
 __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
+    const bool tr = TRACE && a.trace != nullptr;  // timing counters (instantiated separately)
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t s_full[kSlots];
     __shared__ __align__(8) uint64_t s_empty[kSlots];
@@ -414,12 +425,15 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
     double *const sval0 = reinterpret_cast<double *>(smem);
     int32_t *const scol0 = reinterpret_cast<int32_t *>(smem + kSlots * kStageEntries * 8);
 
-    const uint64_t t_start = a.trace ? globaltimer() : 0;
-    __shared__ unsigned long long s_tr[6];  // units, poll ns, failed polls, slot wait ns, unit wait ns, busy ns
+    const uint64_t t_start = tr ? globaltimer() : 0;
+    // trace counters (see mpk_read_trace); s_tarr: time of each slot's last hand-over
+    __shared__ unsigned long long s_tr[kTraceShared];
+    __shared__ unsigned long long s_tarr[kSlots];
     auto tr_add = [&](int q, unsigned long long v) {
-        if (a.trace) atomicAdd(&s_tr[q], v);
+        if (tr) atomicAdd(&s_tr[q], v);
     };
-    if (tid < 6) s_tr[tid] = 0;
+    const long long c_start = tr ? clock64() : 0;
+    if (tid < kTraceShared) s_tr[tid] = 0;
     if (tid == 0) {
         s_final = -1;
         for (int q = 0; q < kSlots; ++q) {
@@ -467,6 +481,7 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
         for (;; ++i) {
             if (u_cur < 0) break;  // no more work
             const int b = i % kSlots;
+            const long long c0 = tr ? clock64() : 0;
             // current unit
             UnitInfo u;
             u.unit = u_cur;
@@ -481,20 +496,15 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
 #pragma unroll
             for (int q = 0; q < 4; ++q) u.widths[q] = __shfl_sync(0xffffffffu, r_cur, 16 + q);
             int dlo[kDepRanges], dlen[kDepRanges];
-            int total = 0;
-#pragma unroll
-            for (int r = 0; r < kDepRanges; ++r) {
-                dlo[r] = __shfl_sync(0xffffffffu, r_cur, 8 + 2 * r);
-                dlen[r] = max(0, __shfl_sync(0xffffffffu, r_cur, 9 + 2 * r) - dlo[r] + 1);
-                total += dlen[r];
-            }
+            const int total = dep_ranges_of(r_cur, dlo, dlen);
+            if (tr && lane == 0) tr_add(11, clock64() - c0);
             // slot b held unit i-kSlots: wait until it is computed before reusing the slot
             if (slot_busy[b]) {
                 const uint64_t t0 = globaltimer();
                 bool ok;
                 while (!(ok = mbar_try_wait(&s_empty[b], slot_use[b] & 1)))
                     if (timed_out(t0, a.wait_ns)) break;
-                if (a.trace && lane == 0) tr_add(3, globaltimer() - t0);
+                if (tr && lane == 0) tr_add(3, globaltimer() - t0);
                 if (!ok) {
                     record_timeout();
                     aborted = true;
@@ -503,6 +513,7 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
                 slot_busy[b] = false;
             }
             // stage the entries
+            const long long c2 = tr ? clock64() : 0;
             if (lane == 0) {
                 s_u[b] = u;
                 if (u.staged) {
@@ -512,6 +523,7 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
                     bulk_g2s(scol0 + b * kStageEntries, a.col + u.ebase, (uint32_t)u.ecount * 4u, &s_full[b]);
                 }
             }
+            if (tr && lane == 0) tr_add(8, clock64() - c2);
             // dependencies of unit i
             const int k = u.unit & 31;
             if (k > 1) {
@@ -525,7 +537,7 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
                     }
                     __nanosleep(32);
                 }
-                if (a.trace && lane == 0) tr_add(1, globaltimer() - t0);
+                if (tr && lane == 0) tr_add(1, globaltimer() - t0);
             }
             if (lane == 0) tr_add(0, 1);
             if (aborted) {
@@ -543,9 +555,13 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
                 }
                 break;
             }
+            const long long c4 = tr ? clock64() : 0;
             fence_acq_rel_gpu();  // acquire: flags before the compute warps' reads (via full[b])
             __syncwarp();
+            if (tr && lane == 0) s_tarr[b] = globaltimer();
             if (lane == 0) mbar_arrive(&s_full[b]);
+            const long long c5 = tr ? clock64() : 0;
+            if (tr && lane == 0) tr_add(9, c5 - c4);
             slot_busy[b] = true;
             slot_use[b] = i / kSlots;
             // prefetch after the hand-over, so that these loads and the atomic complete during
@@ -564,6 +580,7 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
             r_nxt = r2;
             u_nn = u3;
             t = t_next;
+            if (tr && lane == 0) tr_add(10, clock64() - c5);
         }
         if (lane == 0 && s_final < 0) s_final = i;  // units 0..i-1 were handed over
     } else {
@@ -573,13 +590,9 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
         pf.unit = -1;
         for (int i = 0;; ++i) {
             const int b = i % kSlots;
-            // The next unit may depend on the pending one (the control warp hands it over
-            // only when its dependencies are published), so when it is not ready at once,
-            // finish the pending unit first instead of waiting with it unpublished.
-            if (pf.unit >= 0 && !mbar_try_wait(&s_full[b], (i / kSlots) & 1)) {
-                phase_b<M, MODE>(a, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane);
-                pf.unit = -1;
-            }
+            // Each lane waits for itself; whichever iteration a lane leaves the loop in, every
+            // lane then runs the same phases of the same unit (one __syncwarp each), so the
+            // warp's lanes never hold different units.
             const uint64_t t0 = globaltimer();
             bool got = false, stop = false;
             while (true) {
@@ -604,30 +617,43 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
                 break;
             }
             uint64_t t_got = 0;
-            if (a.trace) {
+            if (tr) {
                 t_got = globaltimer();
                 if (lane == 0) tr_add(4, t_got - t0);
+                if (lane == 0 && cw == 0 && t_got - t0 > 1000) {  // waited: how long after the hand-over
+                    const unsigned long long ta = s_tarr[b];
+                    tr_add(14, t_got > ta ? t_got - ta : 0);
+                    tr_add(15, 1);
+                }
             }
-            if (MPK_COMPUTE_PIPELINE) {
-                Prefetch<M> nf;
-                phase_a<M>(a, s_u[b], b, scol0 + b * kStageEntries, cw, lane, nf);
-                if (pf.unit >= 0) phase_b<M, MODE>(a, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane);
-                pf = nf;
-            } else {
+            {
+                const long long c0 = tr ? clock64() : 0;
                 phase_a<M>(a, s_u[b], b, scol0 + b * kStageEntries, cw, lane, pf);
-                phase_b<M, MODE>(a, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane);
+                if (tr) {  // wait for the gathers (integer ops only) to split the unit time
+                    int h = 0;
+#pragma unroll
+                    for (int q = 0; q < Batch<M>::B; ++q) h ^= __double2hiint(pf.x[q][0]);
+                    int d;
+                    asm volatile("add.u32 %0, %1, 0;" : "=r"(d) : "r"(h));
+                    const long long c1 = clock64();
+                    if (lane == 0) tr_add(12, c1 - c0);
+                    phase_b<M, MODE>(a, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane);
+                    if (lane == 0) tr_add(13, clock64() - c1);
+                } else {
+                    phase_b<M, MODE>(a, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane);
+                }
                 pf.unit = -1;
             }
-            if (a.trace && lane == 0) tr_add(5, globaltimer() - t_got);
+            if (tr && lane == 0) tr_add(5, globaltimer() - t_got);
         }
-        if (pf.unit >= 0) phase_b<M, MODE>(a, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane);
     }
-    if (a.trace) {
+    if (tr) {
         __syncthreads();
         if (tid == 0) {
-            for (int q = 0; q < 6; ++q) atomicAdd(a.trace + q, s_tr[q]);
-            atomicAdd(a.trace + 6, (unsigned long long)(globaltimer() - t_start));
-            if (blockIdx.x == 0) atomicAdd(a.trace + 7, 1ull);
+            s_tr[6] = globaltimer() - t_start;
+            s_tr[7] = blockIdx.x == 0;
+            for (int q = 0; q < kTraceShared; ++q) atomicAdd(a.trace + q, s_tr[q]);
+            atomicAdd(a.trace + kTraceShared, (unsigned long long)(clock64() - c_start));
         }
     }
     // ---- exit: the last block resets the ticket for the next launch on the stream
@@ -765,36 +791,40 @@ void launch_cheb_init(const double *v0, double *acc, int32_t n, int32_t m, doubl
 }
 
 // ----------------------------------------------------------------------------- launches
-template <int M, int MODE> static void *mpk_fn() { return (void *)k_mpk<M, MODE>; }
+template <int M, int MODE> static void *mpk_fn(bool trace) {
+    return trace ? (void *)k_mpk<M, MODE, true> : (void *)k_mpk<M, MODE, false>;
+}
 
-static void *select_mpk(int mode, int m) {
-#define SEL(MM)                                                  \
-    if (m == MM) {                                               \
-        if (mode == MODE_POWERS) return mpk_fn<MM, MODE_POWERS>(); \
-        return mpk_fn<MM, MODE_CHEB>();                          \
+static void *select_mpk(int mode, int m, bool trace) {
+#define SEL(MM)                                                         \
+    if (m == MM) {                                                      \
+        if (mode == MODE_POWERS) return mpk_fn<MM, MODE_POWERS>(trace); \
+        return mpk_fn<MM, MODE_CHEB>(trace);                            \
     }
     SEL(1) SEL(2) SEL(4) SEL(8)
 #undef SEL
     fail(MPK_ERR_UNSUPPORTED, "nrhs %d", m);
 }
 
-int occupancy_grid(int mode, int m) {
-    static int cache[2][9] = {};
-    if (cache[mode][m]) return cache[mode][m];
-    void *fn = select_mpk(mode, m);
+int occupancy_grid(int mode, int m, bool trace) {
+    static int cache[2][2][9] = {};
+    int &c = cache[mode][trace ? 1 : 0][m];
+    if (c) return c;
+    void *fn = select_mpk(mode, m, trace);
     MPK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
     int per_sm = 0;
     MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBS, kSmemBytes));
     if (per_sm < 1) fail(MPK_ERR_CUDA, "level-blocked kernel cannot be resident (occupancy 0)");
-    cache[mode][m] = per_sm * device_sms();
-    return cache[mode][m];
+    c = per_sm * device_sms();
+    return c;
 }
 
 void launch_mpk(const Plan &P, KArgs &a, int mode, cudaStream_t s) {
     if (a.nunits <= 0) return;
-    int grid = occupancy_grid(mode, P.m);
+    const bool trace = a.trace != nullptr;
+    int grid = occupancy_grid(mode, P.m, trace);
     if ((int64_t)grid > a.nunits) grid = (int)a.nunits;
-    void *fn = select_mpk(mode, P.m);
+    void *fn = select_mpk(mode, P.m, trace);
     void *args[] = {&a};
     MPK_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(kBS), args, kSmemBytes, s));
 }

@@ -204,6 +204,67 @@ def test_apply_nrhs_and_chunks(mpk, m, chunk_rows):
     _check_powers(Y, oracle.mpk(A, X, 8))
 
 
+def _arrowhead(side=40, width=1500):
+    # 2-D Laplacian plus a dense first row and column: row 0 stores `width` + 1 entries, so
+    # its slice is wider than one shared-memory slot and its chunk is read from global memory
+    A = gen.laplacian_2d(side, side)
+    n = A.n
+    rows = np.repeat(np.arange(n), np.diff(A.row_ptr))
+    cols = np.asarray(A.col)
+    vals = np.asarray(A.val)
+    tgt = np.arange(1, width + 1)
+    w = gen.uniform(gen.derive_seed(85), width, 0.001, 0.01)
+    r = np.concatenate([rows, np.zeros(width, np.int64), tgt])
+    c = np.concatenate([cols, tgt, np.zeros(width, np.int64)])
+    v = np.concatenate([vals, w, w[::-1]])
+    return gen.from_coo(n, r, c, v)
+
+
+@pytest.mark.parametrize("m", [1, 2, 8])
+@pytest.mark.parametrize("chunk_rows,cache_bytes", [(640, 1 << 30), (1920, 1 << 30), (2048, 1 << 30),
+                                                     (1920, 2_000_000)])
+def test_apply_large_chunks(mpk, m, chunk_rows, cache_bytes):
+    # chunks of up to 20, 60 and 64 slices (cut further by the shared-memory slot): compute
+    # warps take several slices of a unit, chunks of more than 16 slices are read from global
+    # memory, the last chunk of each group is ragged, and a smaller budget cuts groups short
+    A = gen.laplacian_3d(40, 30, 20)
+    dA = _dev(A, mpk, True)
+    L = mpk.build_levels(dA, 0)
+    P = mpk.plan(dA, L, p_max=8, nrhs=m, cache_bytes=cache_bytes, chunk_rows=chunk_rows, order=mpk.ORDER_PLAN)
+    d = P.describe()
+    cr = P.chunk_row_ptr.cpu().numpy()
+    assert np.diff(cr).max() <= chunk_rows
+    if cache_bytes == 1 << 30:
+        assert d["num_groups"] == 1 and np.diff(cr).max() > 16 * 32
+    X = gen.vector(A.n, m, stream=84)
+    pe = mpk.build_levels(dA, 0).perm.cpu().numpy()
+    Xp = np.ascontiguousarray(X[pe])
+    Y = P.apply(torch.from_numpy(Xp).cuda(), 8, Y=_poisoned((9, A.n, m)))
+    P.sync_status()
+    _check_powers(Y, oracle.mpk(A, X, 8)[:, pe, :])
+
+
+@pytest.mark.parametrize("chunk_rows", [64, 1024])
+def test_apply_unstaged_wide_row(mpk, chunk_rows):
+    A = _arrowhead()
+    assert np.diff(A.row_ptr).max() > 1000  # one slice of 32 such rows exceeds a shared-memory slot
+    dA = _dev(A, mpk, True)
+    L = mpk.build_levels(dA, 0)
+    X = gen.vector(A.n, 1, stream=86)
+    Yo = oracle.mpk(A, X, 6)
+    for order in (mpk.ORDER_ORIGINAL, mpk.ORDER_PLAN):
+        P = mpk.plan(dA, L, p_max=6, cache_bytes=50000, chunk_rows=chunk_rows, order=order)
+        if order == mpk.ORDER_PLAN:
+            pe = L.perm.cpu().numpy()
+            Y = P.apply(torch.from_numpy(np.ascontiguousarray(X[pe])).cuda(), 6, Y=_poisoned((7, A.n, 1)))
+            P.sync_status()
+            _check_powers(Y, Yo[:, pe, :])
+        else:
+            Y = P.apply(torch.from_numpy(X).cuda(), 6, Y=_poisoned((7, A.n, 1)))
+            P.sync_status()
+            _check_powers(Y, Yo)
+
+
 def test_apply_small_config_many_groups(mpk):
     # 64x64 5-point Laplacian, p = 4 (the small configuration), groups of single levels
     A, p = gen.config_small()
