@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="laplace3d", choices=["laplace3d", "cheb_xxz"])
+    ap.add_argument("--values", default="f64", choices=["f64", "f32", "bf16"],
+                    help="storage type of the matrix values (accumulation stays float64); the Laplacian's "
+                         "{6, -1} are exact in all three")
     ap.add_argument("--xxz-L", type=int, default=24, help="chain length of the XXZ workload")
     ap.add_argument("--degree", type=int, default=64, help="Chebyshev degree of the XXZ workload")
     return ap.parse_args()
@@ -386,7 +389,10 @@ def main():
 
     A, X = build_workload(args.side)
     flops, a_bytes, v_bytes = algorithmic(A, p)
-    dA = mpk.CsrMatrix.from_host(A, is_symmetric=True)
+    vbytes = {"f64": 8, "f32": 4, "bf16": 2}[args.values]
+    a_bytes = (vbytes + 4.0) * A.nnz + 4.0 * (A.n + 1)
+    vtype = {"f64": mpk.MPK_F64, "f32": mpk.MPK_F32, "bf16": mpk.MPK_BF16}[args.values]
+    dA = mpk.CsrMatrix.from_host(A, is_symmetric=True, value_type=vtype)
     Xd = torch.from_numpy(X).cuda()
     stream = torch.cuda.current_stream()
 
@@ -473,9 +479,11 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"3-D 7-point Laplacian {args.side}^3 lexicographic, FP64 CSR, x~U[-1,1), "
-                                   f"p={p}, nrhs=1, level-blocked apply with vectors in BFS order",
+                                   f"p={p}, nrhs=1, level-blocked apply with vectors in BFS order"
+                                   + ("" if args.values == "f64" else f", values stored as {args.values}"),
+                       "values": args.values,
                        "n": A.n, "nnz": A.nnz, "p": p, "nrhs": 1, "parallelism": f"replicas x{world}",
-                       "l2": "no flush: inputs exceed L2 (matrix 1.47 GB, L2 129 MB)",
+                       "l2": f"no flush: inputs exceed L2 (matrix {a_bytes / 1e9:.2f} GB, L2 129 MB)",
                        "levels": desc["num_levels"], "groups": desc["num_groups"], "chunks": desc["num_chunks"],
                        "cache_bytes": desc["cache_bytes"], "window": desc["window"]},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",

@@ -59,14 +59,21 @@ typedef void *mpk_stream;
  * (row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz); col has nnz entries in [0, n); val
  * has nnz entries of val_type.  Column order inside a row is free and duplicates are
  * allowed: entries are summed in stored order.  is_symmetric = 1 declares that the
- * sparsity pattern is symmetric, which skips the A + A^T step of the level builder. */
+ * sparsity pattern is symmetric, which skips the A + A^T step of the level builder.
+ * Precision: a plan stores the values in val_type (8, 4 or 2 bytes an entry) and every
+ * kernel widens each value to float64 exactly before its FMA; vectors and accumulation are
+ * float64.  The results are those of the float64 computation on the widened values, bit for
+ * bit; values exactly representable in the narrow type (e.g. the {6, -1} or {26, -1}
+ * stencil coefficients in bfloat16) therefore give the float64 results unchanged.  In the
+ * narrow types every value must be zero or a normal number: mpk_plan fails with
+ * MPK_ERR_UNSUPPORTED on a subnormal, infinite or NaN value. */
 typedef struct {
     int32_t n;
     int32_t nnz;
     const int32_t *row_ptr;
     const int32_t *col;
     const void *val;
-    int32_t val_type;    /* mpk_dtype; this build accepts MPK_F64 */
+    int32_t val_type;    /* mpk_dtype of val: MPK_F64, MPK_F32 or MPK_BF16 (bfloat16 bits)  */
     int32_t is_symmetric;
 } mpk_csr;
 
@@ -145,7 +152,8 @@ typedef struct {
 mpk_status mpk_plan_describe(const mpk_plan_t *P, mpk_plan_desc *out);
 
 /* Writes the plan's permuted matrix P A P^T as CSR into caller buffers (device):
- * row_ptr[n+1], col[nnz], val[nnz] (float64).  Asynchronous on `stream`. */
+ * row_ptr[n+1], col[nnz], val[nnz] (float64, the stored values widened).  Asynchronous on
+ * `stream`. */
 mpk_status mpk_plan_export_csr(const mpk_plan_t *P, int32_t *row_ptr, int32_t *col, double *val,
                                mpk_stream stream);
 
@@ -238,6 +246,11 @@ mpk_status mpk_debug_drop_release(mpk_plan_t *P, int32_t chunk, int32_t k);
 mpk_status mpk_probe_load(const void *buf, int64_t bytes, int32_t reps, int32_t ctas_per_sm,
                           int32_t *sink, mpk_stream stream);
 mpk_status mpk_probe_dfma(int32_t blocks, int32_t iters, double *sink, mpk_stream stream);
+
+/* dst[i] = src[i] widened to float64 for i < n, with the conversion the kernels use (src of
+ * mpk_dtype val_type, device memory; MPK_ERR_UNSUPPORTED for another type).  Asynchronous
+ * on `stream`. */
+mpk_status mpk_widen_values(int32_t val_type, const void *src, int64_t n, double *dst, mpk_stream stream);
 
 /* Number of SMs and L2 bytes of the current device. */
 mpk_status mpk_device_info(int32_t *num_sms, int64_t *l2_bytes);

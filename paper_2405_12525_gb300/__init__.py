@@ -21,7 +21,7 @@ from ._build import LIB as _LIB_PATH
 from ._build import build as _build_lib
 
 __all__ = ["build", "load", "CsrMatrix", "Levels", "Plan", "build_levels", "plan", "MpkError",
-           "probe_load", "probe_dfma", "device_info", "EXPORTED_SYMBOLS"]
+           "probe_load", "probe_dfma", "device_info", "widen_values", "EXPORTED_SYMBOLS"]
 
 MPK_OK, MPK_ERR_INVALID, MPK_ERR_TOO_LARGE, MPK_ERR_OOM, MPK_ERR_TIMEOUT = 0, 1, 2, 3, 4
 MPK_ERR_CUDA, MPK_ERR_BUDGET, MPK_ERR_UNSUPPORTED = 5, 6, 7
@@ -33,6 +33,7 @@ EXPORTED_SYMBOLS = [
     "mpk_plan_describe", "mpk_plan_export_csr", "mpk_plan_destroy", "mpk_apply", "mpk_spmv_powers",
     "mpk_cheb_filter", "mpk_sync_status", "mpk_probe_load", "mpk_probe_dfma", "mpk_device_info",
     "mpk_status_string", "mpk_last_error", "mpk_debug_drop_release", "mpk_read_trace", "mpk_apply_noalloc",
+    "mpk_widen_values",
 ]
 
 
@@ -98,6 +99,7 @@ def load():
         "mpk_debug_drop_release": [vp, i32, i32],
         "mpk_read_trace": [vp, vp, vp],
         "mpk_apply_noalloc": [vp, vp, i32, vp, vp, vp],
+        "mpk_widen_values": [i32, vp, i64, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -138,9 +140,18 @@ def _ptr(t) -> int:
     return int(t.data_ptr()) if t is not None and t.numel() > 0 else 0
 
 
+def _value_type(t) -> int:
+    torch = _torch()
+    types = {torch.float64: MPK_F64, torch.float32: MPK_F32, torch.bfloat16: MPK_BF16}
+    if t.dtype not in types:
+        raise TypeError("matrix values must be float64, float32 or bfloat16")
+    return types[t.dtype]
+
+
 @dataclass
 class CsrMatrix:
-    """Device CSR matrix: row_ptr (n+1) and col (nnz) int32, val (nnz) float64 CUDA tensors."""
+    """Device CSR matrix: row_ptr (n+1) and col (nnz) int32 CUDA tensors, val (nnz) float64,
+    float32 or bfloat16 (the plan stores values in that type and widens them exactly)."""
     row_ptr: object
     col: object
     val: object
@@ -156,19 +167,22 @@ class CsrMatrix:
 
     def _c(self) -> _Csr:
         torch = _torch()
-        for t, dt in ((self.row_ptr, torch.int32), (self.col, torch.int32), (self.val, torch.float64)):
+        vt = _value_type(self.val)
+        for t, dt in ((self.row_ptr, torch.int32), (self.col, torch.int32), (self.val, self.val.dtype)):
             if t.dtype != dt or not t.is_cuda or not t.is_contiguous():
-                raise TypeError("CsrMatrix wants contiguous CUDA tensors: int32 row_ptr/col, float64 val")
-        return _Csr(self.n, self.nnz, _ptr(self.row_ptr), _ptr(self.col), _ptr(self.val), MPK_F64,
+                raise TypeError("CsrMatrix wants contiguous CUDA tensors: int32 row_ptr/col")
+        return _Csr(self.n, self.nnz, _ptr(self.row_ptr), _ptr(self.col), _ptr(self.val), vt,
                     1 if self.is_symmetric else 0)
 
     @staticmethod
-    def from_host(A, device="cuda", is_symmetric=False) -> "CsrMatrix":
-        """From any object with row_ptr/col/val numpy arrays (e.g. gen.CSR)."""
+    def from_host(A, device="cuda", is_symmetric=False, value_type=MPK_F64) -> "CsrMatrix":
+        """From any object with row_ptr/col/val numpy arrays (e.g. gen.CSR); float64 values are
+        rounded to nearest-even when value_type is MPK_F32 or MPK_BF16."""
         torch = _torch()
+        dt = {MPK_F64: torch.float64, MPK_F32: torch.float32, MPK_BF16: torch.bfloat16}[value_type]
         return CsrMatrix(torch.as_tensor(A.row_ptr, dtype=torch.int32).to(device),
                          torch.as_tensor(A.col, dtype=torch.int32).to(device),
-                         torch.as_tensor(A.val, dtype=torch.float64).to(device), is_symmetric)
+                         torch.as_tensor(A.val, dtype=torch.float64).to(dt).to(device), is_symmetric)
 
 
 class Levels:
@@ -371,6 +385,16 @@ def probe_load(buf, reps: int, ctas_per_sm: int, sink, stream=None):
 
 def probe_dfma(blocks: int, iters: int, sink, stream=None):
     _check(load().mpk_probe_dfma(blocks, iters, _ptr(sink), _stream(stream)))
+
+
+def widen_values(values, stream=None):
+    """float64 copy of a float64/float32/bfloat16 CUDA tensor, widened by the library's kernels."""
+    torch = _torch()
+    vt = _value_type(values)
+    values = values.contiguous()
+    out = torch.empty(values.shape, dtype=torch.float64, device=values.device)
+    _check(load().mpk_widen_values(vt, _ptr(values), values.numel(), _ptr(out), _stream(stream)))
+    return out
 
 
 def device_info():

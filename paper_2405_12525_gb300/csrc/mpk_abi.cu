@@ -337,6 +337,16 @@ extern "C" mpk_status mpk_probe_dfma(int32_t blocks, int32_t iters, double *sink
     MPK_GUARD_END
 }
 
+extern "C" mpk_status mpk_widen_values(int32_t val_type, const void *src, int64_t n, double *dst,
+                                       mpk_stream stream) {
+    MPK_GUARD_BEGIN
+    if (n < 0) fail(MPK_ERR_INVALID, "n < 0");
+    if (n > 0 && (!src || !dst)) fail(MPK_ERR_INVALID, "NULL src or dst");
+    widen_values(val_type, src, n, dst, as_stream(stream));
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
 extern "C" mpk_status mpk_device_info(int32_t *num_sms, int64_t *l2_bytes) {
     MPK_GUARD_BEGIN
     if (num_sms) *num_sms = device_sms();

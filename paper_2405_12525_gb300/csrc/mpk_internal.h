@@ -74,6 +74,42 @@ void iota_i32(int32_t *p, int64_t n, cudaStream_t s);
 int device_sms();
 int64_t device_l2_bytes();
 
+// ----------------------------------------------------------------------------- value widening
+// float32 / bfloat16 -> float64 is exact: both are subsets of binary64 (a bfloat16 is the upper
+// half of a binary32).  Done with integer operations on the IEEE 754 encodings, so that it
+// adds no work to the FP64 pipe: a normal binary32 keeps its sign, its 8-bit exponent is
+// rebiased from 127 to 1023 (+896) into the 11-bit field and its 23-bit fraction becomes the
+// top of the 52-bit one.  Zeros, subnormals, infinities and NaNs take separate paths (a
+// signaling NaN comes out quiet, as from any IEEE 754 conversion).
+__device__ __forceinline__ double widen_binary32(uint32_t u) {
+    const uint32_t sign = u & 0x80000000u, e = (u >> 23) & 0xffu, f = u & 0x7fffffu;
+    if (e - 1u < 254u) return __hiloint2double((int)(sign | ((e + 896u) << 20) | (f >> 3)), (int)(f << 29));
+    if (e == 255u)  // infinity, or NaN: payload kept, quiet bit set as an IEEE 754 conversion does
+        return __hiloint2double((int)(sign | 0x7ff00000u | (f >> 3) | (f ? 0x80000u : 0u)), (int)(f << 29));
+    if (f == 0u) return __hiloint2double((int)sign, 0);                                             // +-0
+    // subnormal f * 2^-149: with the leading one of f at bit q the value is 2^(q-149) (1 + rest)
+    const int q = 31 - __clz((int)f);
+    const uint64_t frac = (uint64_t)(f ^ (1u << q)) << (52 - q);
+    return __longlong_as_double((long long)(((uint64_t)sign << 32) | ((uint64_t)(q + 874) << 52) | frac));
+}
+// The kernels' widening, for the values a plan stores (zeros and normal numbers only, checked
+// by the planner): the sign stays, the exponent and fraction move right by 3 bits into the
+// binary64 fields and the exponent is rebiased by adding 896 << 20; zero keeps only its sign.
+// No branch, five integer operations.
+__device__ __forceinline__ double widen_normal32(uint32_t u) {
+    const uint32_t mag = u & 0x7fffffffu;
+    const uint32_t hi = (mag ? (mag >> 3) + 0x38000000u : 0u) | (u & 0x80000000u);
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
+// 1 when the binary32 bits are a subnormal, an infinity or a NaN
+__device__ __forceinline__ int binary32_special(uint32_t u) {
+    const uint32_t e = (u >> 23) & 0xffu;
+    return e == 255u || (e == 0u && (u & 0x7fffffu) != 0u);
+}
+__device__ __forceinline__ double widen_value(double v) { return v; }
+__device__ __forceinline__ double widen_value(float v) { return widen_binary32(__float_as_uint(v)); }
+__device__ __forceinline__ double widen_value(uint16_t v) { return widen_binary32((uint32_t)v << 16); }  // bfloat16 bits
+
 // ----------------------------------------------------------------------------- objects
 struct Levels {
     int32_t n = 0;
@@ -115,7 +151,7 @@ constexpr int kRecSlices = 16;
 constexpr int kRecInts = 8 + 2 * kDepRanges + kRecSlices / 4;
 struct KArgs {
     // sliced matrix copy (plan order)
-    const double *val;
+    const void *val;  // values of the matrix's value type (Plan::val_type)
     const int32_t *col;
     const int64_t *slice_ptr;
     const int32_t *rowlen;
@@ -154,13 +190,14 @@ struct KArgs {
 
 struct Plan {
     int32_t n = 0, nnz = 0, m = 1, p_max = 8, order = MPK_ORDER_ORIGINAL;
+    int32_t val_type = MPK_F64, val_bytes = 8;  // storage of the matrix values (mpk_dtype)
     int32_t num_levels = 0, num_groups = 0, num_chunks = 0, num_slices = 0;
     int32_t chunk_rows = 512;
     int64_t cache_bytes = 0, group_budget = 0, padded = 0, wait_ns = 0;
     int32_t window = 0;  // groups sharing the cache budget: kSlotSkew * p_max + 1
     bool identity = false;
     // device data (owned by arena)
-    double *val = nullptr;
+    void *val = nullptr;  // val_bytes per padded entry
     int32_t *col = nullptr;
     int64_t *slice_ptr = nullptr;
     int32_t *rowlen = nullptr;
@@ -198,7 +235,9 @@ void launch_scatter_rows(const double *src, const int32_t *iperm, double *dst, i
                          cudaStream_t s);
 void launch_cheb_init(const double *v0, double *acc, int32_t n, int32_t m, double c0re, double c0im,
                       int complex_coeff, cudaStream_t s);
-int occupancy_grid(int mode, int m, bool trace);
+int occupancy_grid(int mode, int m, bool trace, int vtype);
+// dst[i] = src[i] widened to float64 (src of mpk_dtype vtype), exact
+void widen_values(int vtype, const void *src, int64_t n, double *dst, cudaStream_t s);
 
 // level builder (mpk_levels.cu)
 Levels *build_levels(const mpk_csr *A, int32_t root, cudaStream_t s);

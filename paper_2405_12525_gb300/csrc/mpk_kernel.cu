@@ -20,8 +20,8 @@ constexpr int kBlocksPerSM = 1024 / kBS;     // register budget: 64 per thread a
 constexpr int kSpmvBS = 256;        // threads per block of the plain SpMV kernel
 // Staging slots: the control warp fills one while the compute warps work on the other.
 constexpr int kSlots = 2;
-constexpr int kStageBytes = kStageEntries * 12;          // one slot: values + columns
-constexpr int kSmemBytes = kSlots * kStageBytes;
+// one slot: kStageEntries values of the matrix's value type, then as many column indices
+template <class VT> constexpr int smem_bytes() { return kSlots * kStageEntries * (int)(sizeof(typename VT::T) + 4); }
 
 enum Mode { MODE_POWERS = 0, MODE_CHEB = 1 };
 
@@ -147,10 +147,32 @@ __device__ __forceinline__ void row_sum_from(VP val, CP col, int64_t off, int j_
     }
 }
 
-// read-only global views (immutable matrix copy)
-struct GVal {
-    const double *p;
-    __device__ __forceinline__ double operator[](int64_t i) const { return __ldg(p + i); }
+// ----------------------------------------------------------------------------- value types
+// Matrix values are stored as float64, float32 or bfloat16 and widened to float64 before
+// their FMA, exactly and with integer operations only (widen_normal32: the planner admits
+// zeros and normal numbers in the narrow types).
+struct ValF64 {
+    using T = double;
+    static __device__ __forceinline__ double widen(double v) { return v; }
+};
+struct ValF32 {
+    using T = float;
+    static __device__ __forceinline__ double widen(float v) { return widen_normal32(__float_as_uint(v)); }
+};
+struct ValBF16 {
+    using T = uint16_t;  // bfloat16 bits
+    static __device__ __forceinline__ double widen(uint16_t v) { return widen_normal32((uint32_t)v << 16); }
+};
+
+// read-only views returning widened values: the immutable matrix copy in global memory, or a
+// staged slot in shared memory
+template <class VT> struct GVal {
+    const typename VT::T *p;
+    __device__ __forceinline__ double operator[](int64_t i) const { return VT::widen(__ldg(p + i)); }
+};
+template <class VT> struct SVal {
+    const typename VT::T *p;
+    __device__ __forceinline__ double operator[](int64_t i) const { return VT::widen(p[i]); }
 };
 struct GCol {
     const int32_t *p;
@@ -294,15 +316,15 @@ __device__ __forceinline__ void phase_a(const KArgs &a, const UnitInfo &u, int b
 }
 
 // phase B: finish unit pf (all of the warp's rows), then publish and release its slot
-template <int M, int MODE>
+template <int M, int MODE, class VT>
 __device__ __forceinline__ void phase_b(const KArgs &a, const Prefetch<M> &pf, const UnitInfo *s_u,
-                                        const double *sval0, const int32_t *scol0, int *s_done, uint64_t *s_empty,
+                                        const typename VT::T *sval0, const int32_t *scol0, int *s_done, uint64_t *s_empty,
                                         int cwarp, int lane) {
     constexpr int B = Batch<M>::B;
     const UnitInfo &u = s_u[pf.slot];
     const int k = pf.unit & 31;
     const double *xin = input_block<M>(a, k);
-    const double *sval = sval0 + pf.slot * kStageEntries;
+    const SVal<VT> sval{sval0 + pf.slot * kStageEntries};
     const int32_t *scol = scol0 + pf.slot * kStageEntries;
     if (u.staged) {
         if (pf.r >= 0) {  // first slice: prefetched first batch, then the rest of the row
@@ -344,7 +366,7 @@ __device__ __forceinline__ void phase_b(const KArgs &a, const Prefetch<M> &pf, c
             if (r >= u.row1) continue;
             const int64_t s0 = __ldg(a.slice_ptr + u.slice0 + sl), s1 = __ldg(a.slice_ptr + u.slice0 + sl + 1);
             double w[M];
-            row_sum<M, 1>(GVal{a.val + u.ebase}, GCol{a.col + u.ebase}, s0 - u.ebase + lane, (int)((s1 - s0) >> 5),
+            row_sum<M, 1>(GVal<VT>{static_cast<const typename VT::T *>(a.val) + u.ebase}, GCol{a.col + u.ebase}, s0 - u.ebase + lane, (int)((s1 - s0) >> 5),
                           xin, w);
             row_epilogue<M, MODE>(a, k, r, w, xin);
             if (k == 1 && a.y0copy) {
@@ -412,8 +434,9 @@ __device__ __forceinline__ int dep_ranges_of(int rec, int (&lo)[kDepRanges], int
     return total;
 }
 
-template <int M, int MODE, bool TRACE>
+template <int M, int MODE, bool TRACE, class VT>
 __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
+    using T = typename VT::T;
     const bool tr = TRACE && a.trace != nullptr;  // timing counters (instantiated separately)
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t s_full[kSlots];
@@ -422,8 +445,8 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
     __shared__ volatile int s_final;  // units handed over in total; -1 while the control warp runs
     __shared__ int s_done[kSlots];    // compute warps finished with the slot's unit
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    double *const sval0 = reinterpret_cast<double *>(smem);
-    int32_t *const scol0 = reinterpret_cast<int32_t *>(smem + kSlots * kStageEntries * 8);
+    T *const sval0 = reinterpret_cast<T *>(smem);
+    int32_t *const scol0 = reinterpret_cast<int32_t *>(smem + kSlots * kStageEntries * sizeof(T));
 
     const uint64_t t_start = tr ? globaltimer() : 0;
     // trace counters (see mpk_read_trace); s_tarr: time of each slot's last hand-over
@@ -518,8 +541,9 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
                 s_u[b] = u;
                 if (u.staged) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    mbar_expect_tx_only(&s_full[b], (uint32_t)u.ecount * 12u);
-                    bulk_g2s(sval0 + b * kStageEntries, a.val + u.ebase, (uint32_t)u.ecount * 8u, &s_full[b]);
+                    mbar_expect_tx_only(&s_full[b], (uint32_t)u.ecount * (uint32_t)(sizeof(T) + 4));
+                    bulk_g2s(sval0 + b * kStageEntries, static_cast<const T *>(a.val) + u.ebase,
+                             (uint32_t)(u.ecount * sizeof(T)), &s_full[b]);
                     bulk_g2s(scol0 + b * kStageEntries, a.col + u.ebase, (uint32_t)u.ecount * 4u, &s_full[b]);
                 }
             }
@@ -637,10 +661,10 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
                     asm volatile("add.u32 %0, %1, 0;" : "=r"(d) : "r"(h));
                     const long long c1 = clock64();
                     if (lane == 0) tr_add(12, c1 - c0);
-                    phase_b<M, MODE>(a, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane);
+                    phase_b<M, MODE, VT>(a, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane);
                     if (lane == 0) tr_add(13, clock64() - c1);
                 } else {
-                    phase_b<M, MODE>(a, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane);
+                    phase_b<M, MODE, VT>(a, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane);
                 }
                 pf.unit = -1;
             }
@@ -673,8 +697,8 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
 // One plain SpMV over the plan's sliced copy: y = A x (plan order), same row body with
 // direct (read-only cached) loads of the entries.  Blocks walk chunks, warps walk the
 // chunk's slices.
-template <int M>
-__global__ void __launch_bounds__(kSpmvBS) k_spmv(const double *__restrict__ val, const int32_t *__restrict__ col,
+template <int M, class VT>
+__global__ void __launch_bounds__(kSpmvBS) k_spmv(const typename VT::T *__restrict__ val, const int32_t *__restrict__ col,
                                                   const int64_t *__restrict__ slice_ptr,
                                                   const int32_t *__restrict__ chunk_row,
                                                   const int32_t *__restrict__ chunk_slice, int32_t nchunks,
@@ -688,7 +712,7 @@ __global__ void __launch_bounds__(kSpmvBS) k_spmv(const double *__restrict__ val
             if (r < r1) {
                 const int64_t s0 = slice_ptr[sl0 + sl], s1 = slice_ptr[sl0 + sl + 1];
                 double w[M];
-                row_sum<M, Batch<M>::B>(GVal{val}, GCol{col}, s0 + lane, (int)((s1 - s0) >> 5), x, w);
+                row_sum<M, Batch<M>::B>(GVal<VT>{val}, GCol{col}, s0 + lane, (int)((s1 - s0) >> 5), x, w);
 #pragma unroll
                 for (int i = 0; i < M; ++i) y[r * M + i] = w[i];
             }
@@ -791,29 +815,42 @@ void launch_cheb_init(const double *v0, double *acc, int32_t n, int32_t m, doubl
 }
 
 // ----------------------------------------------------------------------------- launches
-template <int M, int MODE> static void *mpk_fn(bool trace) {
-    return trace ? (void *)k_mpk<M, MODE, true> : (void *)k_mpk<M, MODE, false>;
+template <int M, int MODE, class VT> static void *mpk_fn(bool trace) {
+    return trace ? (void *)k_mpk<M, MODE, true, VT> : (void *)k_mpk<M, MODE, false, VT>;
 }
 
-static void *select_mpk(int mode, int m, bool trace) {
-#define SEL(MM)                                                         \
-    if (m == MM) {                                                      \
-        if (mode == MODE_POWERS) return mpk_fn<MM, MODE_POWERS>(trace); \
-        return mpk_fn<MM, MODE_CHEB>(trace);                            \
+template <class VT> static void *select_mpk_vt(int mode, int m, bool trace) {
+#define SEL(MM)                                                             \
+    if (m == MM) {                                                          \
+        if (mode == MODE_POWERS) return mpk_fn<MM, MODE_POWERS, VT>(trace); \
+        return mpk_fn<MM, MODE_CHEB, VT>(trace);                            \
     }
     SEL(1) SEL(2) SEL(4) SEL(8)
 #undef SEL
     fail(MPK_ERR_UNSUPPORTED, "nrhs %d", m);
 }
 
-int occupancy_grid(int mode, int m, bool trace) {
-    static int cache[2][2][9] = {};
-    int &c = cache[mode][trace ? 1 : 0][m];
+static void *select_mpk(int mode, int m, bool trace, int vtype) {
+    if (vtype == MPK_F64) return select_mpk_vt<ValF64>(mode, m, trace);
+    if (vtype == MPK_F32) return select_mpk_vt<ValF32>(mode, m, trace);
+    if (vtype == MPK_BF16) return select_mpk_vt<ValBF16>(mode, m, trace);
+    fail(MPK_ERR_UNSUPPORTED, "value type %d", vtype);
+}
+
+static int mpk_smem_bytes(int vtype) {
+    return vtype == MPK_F64 ? smem_bytes<ValF64>() : (vtype == MPK_F32 ? smem_bytes<ValF32>() : smem_bytes<ValBF16>());
+}
+
+int occupancy_grid(int mode, int m, bool trace, int vtype) {
+    static int cache[3][2][2][9] = {};
+    if (vtype < 0 || vtype > 2) fail(MPK_ERR_UNSUPPORTED, "value type %d", vtype);
+    int &c = cache[vtype][mode][trace ? 1 : 0][m];
     if (c) return c;
-    void *fn = select_mpk(mode, m, trace);
-    MPK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes));
+    void *fn = select_mpk(mode, m, trace, vtype);
+    const int smem = mpk_smem_bytes(vtype);
+    MPK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
-    MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBS, kSmemBytes));
+    MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBS, smem));
     if (per_sm < 1) fail(MPK_ERR_CUDA, "level-blocked kernel cannot be resident (occupancy 0)");
     c = per_sm * device_sms();
     return c;
@@ -822,26 +859,33 @@ int occupancy_grid(int mode, int m, bool trace) {
 void launch_mpk(const Plan &P, KArgs &a, int mode, cudaStream_t s) {
     if (a.nunits <= 0) return;
     const bool trace = a.trace != nullptr;
-    int grid = occupancy_grid(mode, P.m, trace);
+    int grid = occupancy_grid(mode, P.m, trace, P.val_type);
     if ((int64_t)grid > a.nunits) grid = (int)a.nunits;
-    void *fn = select_mpk(mode, P.m, trace);
+    void *fn = select_mpk(mode, P.m, trace, P.val_type);
     void *args[] = {&a};
-    MPK_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(kBS), args, kSmemBytes, s));
+    MPK_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(kBS), args, mpk_smem_bytes(P.val_type), s));
 }
 
-void launch_spmv(const Plan &P, const double *x, double *y, cudaStream_t s) {
-    if (P.num_chunks <= 0) return;
+template <class VT> static void launch_spmv_vt(const Plan &P, const double *x, double *y, cudaStream_t s) {
     const int grid = P.num_chunks;
-#define L(MM)                                                                                               \
-    case MM:                                                                                                \
-        k_spmv<MM><<<grid, kSpmvBS, 0, s>>>(P.val, P.col, P.slice_ptr, P.chunk_row, P.chunk_slice, P.num_chunks, \
-                                            x, y);                                                         \
+    const auto *val = static_cast<const typename VT::T *>(P.val);
+#define L(MM)                                                                                                 \
+    case MM:                                                                                                  \
+        k_spmv<MM, VT><<<grid, kSpmvBS, 0, s>>>(val, P.col, P.slice_ptr, P.chunk_row, P.chunk_slice, P.num_chunks, \
+                                                x, y);                                                       \
         break;
     switch (P.m) {
         L(1) L(2) L(4) L(8) default : fail(MPK_ERR_UNSUPPORTED, "nrhs %d", P.m);
     }
 #undef L
     MPK_LAUNCHED();
+}
+
+void launch_spmv(const Plan &P, const double *x, double *y, cudaStream_t s) {
+    if (P.num_chunks <= 0) return;
+    if (P.val_type == MPK_F64) return launch_spmv_vt<ValF64>(P, x, y, s);
+    if (P.val_type == MPK_F32) return launch_spmv_vt<ValF32>(P, x, y, s);
+    return launch_spmv_vt<ValBF16>(P, x, y, s);
 }
 
 // ----------------------------------------------------------------------------- probes

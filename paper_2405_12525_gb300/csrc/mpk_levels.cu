@@ -28,7 +28,8 @@ __global__ void k_validate(int32_t n, int32_t nnz, const int32_t *rp, const int3
 void validate_csr(const mpk_csr *A, cudaStream_t s) {
     if (!A) fail(MPK_ERR_INVALID, "matrix is NULL");
     if (A->n < 0 || A->nnz < 0) fail(MPK_ERR_INVALID, "negative n (%d) or nnz (%d)", A->n, A->nnz);
-    if (A->val_type != MPK_F64) fail(MPK_ERR_UNSUPPORTED, "only MPK_F64 values are supported by this build");
+    if (A->val_type != MPK_F64 && A->val_type != MPK_F32 && A->val_type != MPK_BF16)
+        fail(MPK_ERR_UNSUPPORTED, "value type %d (MPK_F64, MPK_F32 or MPK_BF16)", A->val_type);
     if (A->n == 0) return;
     if (!A->row_ptr || (A->nnz > 0 && (!A->col || !A->val)))
         fail(MPK_ERR_INVALID, "NULL CSR array");

@@ -46,10 +46,15 @@ __global__ void k_slice_width(const int32_t *slice_row, int32_t nslices, const i
 // relabelling columns through iperm, and folds the chunks each row reads into the
 // dependency range of its chunk.  When A is not known to be symmetric, a chunk is also
 // added to the ranges of the chunks it reads, so that ranges cover both directions.
-__global__ void k_fill(int32_t n, const int32_t *rp, const int32_t *ci, const double *va, const int32_t *perm,
+__device__ __forceinline__ int value_special(double) { return 0; }
+__device__ __forceinline__ int value_special(float v) { return binary32_special(__float_as_uint(v)); }
+__device__ __forceinline__ int value_special(uint16_t v) { return binary32_special((uint32_t)v << 16); }
+
+template <class T>
+__global__ void k_fill(int32_t n, const int32_t *rp, const int32_t *ci, const T *va, const int32_t *perm,
                        const int32_t *iperm, const int32_t *chunk_row, const int32_t *chunk_slice,
-                       const int32_t *chunk_of_row, const int64_t *slice_ptr, double *sval, int32_t *scol,
-                       int2 *dep, int symmetric) {
+                       const int32_t *chunk_of_row, const int64_t *slice_ptr, T *sval, int32_t *scol,
+                       int2 *dep, int symmetric, int32_t *special) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
         const int32_t c = chunk_of_row[r];
@@ -62,6 +67,7 @@ __global__ void k_fill(int32_t n, const int32_t *rp, const int32_t *ci, const do
             const int32_t nc = iperm ? iperm[ci[e]] : ci[e];
             const int64_t dst = base + 32 * (int64_t)(e - e0);
             sval[dst] = va[e];
+            if (value_special(va[e])) *special = 1;  // narrow types: subnormal, infinity or NaN
             scol[dst] = nc;
             const int32_t cc = chunk_of_row[nc];
             lo = min(lo, cc);
@@ -194,9 +200,28 @@ __global__ void k_chunk_records(int32_t nchunks, const int32_t *chunk_row, const
     }
 }
 
-// sliced copy -> CSR (for inspection and tests)
+template <class T> __global__ void k_widen(const T *src, int64_t n, double *dst) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = widen_value(src[i]);
+}
+
+void widen_values(int vtype, const void *src, int64_t n, double *dst, cudaStream_t s) {
+    if (n <= 0) return;
+    if (vtype == MPK_F64)
+        k_widen<double><<<grid_n(n), 256, 0, s>>>(static_cast<const double *>(src), n, dst);
+    else if (vtype == MPK_F32)
+        k_widen<float><<<grid_n(n), 256, 0, s>>>(static_cast<const float *>(src), n, dst);
+    else if (vtype == MPK_BF16)
+        k_widen<uint16_t><<<grid_n(n), 256, 0, s>>>(static_cast<const uint16_t *>(src), n, dst);
+    else
+        fail(MPK_ERR_UNSUPPORTED, "value type %d", vtype);
+    MPK_LAUNCHED();
+}
+
+// sliced copy -> CSR (for inspection and tests), values widened to float64
+template <class T>
 __global__ void k_export(int32_t n, const int32_t *rowlen, const int32_t *chunk_row, const int32_t *chunk_slice,
-                         const int32_t *chunk_of_row, const int64_t *slice_ptr, const double *sval,
+                         const int32_t *chunk_of_row, const int64_t *slice_ptr, const T *sval,
                          const int32_t *scol, const int32_t *rp, int32_t *ci, double *va) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
@@ -205,7 +230,7 @@ __global__ void k_export(int32_t n, const int32_t *rowlen, const int32_t *chunk_
         const int64_t base = slice_ptr[chunk_slice[c] + (local >> 5)] + (local & 31);
         for (int32_t j = 0; j < rowlen[r]; ++j) {
             ci[rp[r] + j] = scol[base + 32 * (int64_t)j];
-            va[rp[r] + j] = sval[base + 32 * (int64_t)j];
+            va[rp[r] + j] = widen_value(sval[base + 32 * (int64_t)j]);
         }
     }
 }
@@ -217,8 +242,16 @@ void export_csr(const Plan &P, int32_t *rp, int32_t *ci, double *va, cudaStream_
     Tmp<int32_t> cor(P.n);
     k_chunk_of_row<<<grid_n(P.num_chunks * 256), 256, 0, s>>>(P.chunk_row, P.num_chunks, cor.p);
     MPK_LAUNCHED();
-    k_export<<<grid_n(P.n), 256, 0, s>>>(P.n, P.rowlen, P.chunk_row, P.chunk_slice, cor.p, P.slice_ptr, P.val,
-                                         P.col, rp, ci, va);
+#define EXPORT(T)                                                                                              \
+    k_export<T><<<grid_n(P.n), 256, 0, s>>>(P.n, P.rowlen, P.chunk_row, P.chunk_slice, cor.p, P.slice_ptr, \
+                                            static_cast<const T *>(P.val), P.col, rp, ci, va)
+    if (P.val_type == MPK_F64)
+        EXPORT(double);
+    else if (P.val_type == MPK_F32)
+        EXPORT(float);
+    else
+        EXPORT(uint16_t);
+#undef EXPORT
     MPK_LAUNCHED();
     MPK_CUDA(cudaStreamSynchronize(s));
 }
@@ -244,6 +277,8 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         P->nnz = A->nnz;
         P->m = m;
         P->p_max = pmax;
+        P->val_type = A->val_type;
+        P->val_bytes = A->val_type == MPK_F64 ? 8 : (A->val_type == MPK_F32 ? 4 : 2);
         P->order = o->order;
         P->identity = (L == nullptr);
         P->chunk_rows = chunk_rows;
@@ -283,7 +318,7 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
             MPK_CUDA(cudaStreamSynchronize(s));
             const std::vector<int32_t> &lp = L->h_level_ptr;
             const int64_t B = P->group_budget;
-            const int64_t vb = 8;  // value bytes (float64)
+            const int64_t vb = P->val_bytes;  // value bytes of the stored type
             int64_t cur = 0;
             g_level.push_back(0);
             for (int32_t l = 0; l < NL; ++l) {
@@ -369,9 +404,9 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         P->slice_ptr = P->arena.alloc_n<int64_t>((int64_t)NS + 1);
         MPK_CUDA(cudaMemcpyAsync(P->slice_ptr, sptr.data(), sizeof(int64_t) * ((size_t)NS + 1), cudaMemcpyHostToDevice, s));
         Tmp<int32_t> cor(n);
-        P->val = P->arena.alloc_n<double>(P->padded + 32);
+        P->val = P->arena.alloc((P->padded + 32) * P->val_bytes);
         P->col = P->arena.alloc_n<int32_t>(P->padded + 32);
-        MPK_CUDA(cudaMemsetAsync(P->val, 0, sizeof(double) * (size_t)(P->padded + 32), s));
+        MPK_CUDA(cudaMemsetAsync(P->val, 0, (size_t)P->val_bytes * (size_t)(P->padded + 32), s));  // +0 in every type
         MPK_CUDA(cudaMemsetAsync(P->col, 0xff, sizeof(int32_t) * (size_t)(P->padded + 32), s));  // padding: col = -1
         P->dep = P->arena.alloc_n<int2>(NC > 0 ? NC : 1);
         if (NC > 0) {
@@ -379,10 +414,27 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
             MPK_LAUNCHED();
             k_chunk_of_row<<<grid_n((int64_t)NC * 256), 256, 0, s>>>(P->chunk_row, NC, cor.p);
             MPK_LAUNCHED();
-            k_fill<<<grid_n(n), 256, 0, s>>>(n, A->row_ptr, A->col, static_cast<const double *>(A->val), P->perm,
-                                             P->iperm, P->chunk_row, P->chunk_slice, cor.p, P->slice_ptr, P->val,
-                                             P->col, P->dep, A->is_symmetric ? 1 : 0);
+#define FILL(T)                                                                                            \
+    k_fill<T><<<grid_n(n), 256, 0, s>>>(n, A->row_ptr, A->col, static_cast<const T *>(A->val), P->perm,    \
+                                        P->iperm, P->chunk_row, P->chunk_slice, cor.p, P->slice_ptr,         \
+                                        static_cast<T *>(P->val), P->col, P->dep, A->is_symmetric ? 1 : 0, special.p)
+            Tmp<int32_t> special(1);
+            MPK_CUDA(cudaMemsetAsync(special.p, 0, sizeof(int32_t), s));
+            if (P->val_type == MPK_F64)
+                FILL(double);
+            else if (P->val_type == MPK_F32)
+                FILL(float);
+            else
+                FILL(uint16_t);
+#undef FILL
             MPK_LAUNCHED();
+            int32_t has_special = 0;
+            MPK_CUDA(cudaMemcpyAsync(&has_special, special.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            MPK_CUDA(cudaStreamSynchronize(s));
+            if (has_special)
+                fail(MPK_ERR_UNSUPPORTED,
+                     "float32/bfloat16 storage holds zeros and normal numbers only (a value is subnormal, "
+                     "infinite or NaN in the narrow type): use MPK_F64 values");
         }
         // ---- dependency ranges: exact chunk sets as bitmaps over each hull, compressed
         P->dep_ranges = P->arena.alloc_n<int4>(2 * (int64_t)(NC > 0 ? NC : 1));
