@@ -226,7 +226,10 @@ mpk_status mpk_cheb_filter(const mpk_plan_t *P, const double *X, int32_t degree,
 mpk_status mpk_read_trace(const mpk_plan_t *P, int64_t *counters, mpk_stream stream);
 
 /* Synchronises `stream` and reports a device-side failure of the plan's calls since the
- * last mpk_sync_status (MPK_ERR_TIMEOUT), else MPK_OK or a CUDA error. */
+ * last mpk_sync_status (MPK_ERR_TIMEOUT), else MPK_OK or a CUDA error.  The plan keeps its
+ * launch epoch on the device, so calls captured in a CUDA graph can be replayed: every replay
+ * is a new launch.  (After 2^30 launches made through the API the plan clears its flags;
+ * graph replays are not counted.) */
 mpk_status mpk_sync_status(const mpk_plan_t *P, mpk_stream stream);
 
 /* Fault injection for tests of the failure path (no counterpart in the paper): in the next

@@ -132,14 +132,15 @@ extern "C" void mpk_plan_destroy(mpk_plan_t *P) {
 }
 
 // ---------------------------------------------------------------------------------------- apply
+// Each launch of the level-blocked kernel takes the next epoch on the device (ctl[4]); before
+// the epochs could wrap, the flags and the epoch are cleared (launches replayed from a CUDA
+// graph are not counted here).
 static void next_epoch(Plan &P, cudaStream_t s) {
-    if (P.epoch == INT_MAX) {  // flags hold old epochs: clear them before reuse
+    if (++P.launches >= ((int64_t)1 << 30)) {
         MPK_CUDA(cudaMemsetAsync(P.flags, 0, sizeof(int32_t) * (size_t)(P.p_max + 1) * std::max(1, P.num_chunks), s));
-        MPK_CUDA(cudaMemsetAsync(P.ctl + 2, 0, 2 * sizeof(unsigned int), s));
-        P.epoch = 0;
-        P.last_checked_epoch = 0;
+        MPK_CUDA(cudaMemsetAsync(P.ctl + 2, 0, 3 * sizeof(unsigned int), s));
+        P.launches = 1;
     }
-    ++P.epoch;
 }
 
 static KArgs base_args(Plan &P, int32_t p) {
@@ -159,7 +160,7 @@ static KArgs base_args(Plan &P, int32_t p) {
     a.units = P.units + P.unit_off[p];
     a.nunits = P.unit_off[p + 1] - P.unit_off[p];
     a.flags = P.flags;
-    a.epoch = P.epoch;
+    a.epoch_word = P.ctl + 4;
     a.ticket = P.ctl;
     a.exit_count = P.ctl + 1;
     a.err = reinterpret_cast<int32_t *>(P.ctl + 2);
@@ -298,14 +299,13 @@ extern "C" mpk_status mpk_sync_status(const mpk_plan_t *Ph, mpk_stream stream) {
     if (!Ph || !Ph->impl) fail(MPK_ERR_INVALID, "plan is NULL");
     Plan &P = *const_cast<Plan *>(Ph->impl);
     MPK_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    // ctl[2..3]: epoch and code of the last failed launch, kept until read here
     unsigned int h[2] = {0, 0};
     MPK_CUDA(cudaMemcpy(h, P.ctl + 2, sizeof(h), cudaMemcpyDeviceToHost));
-    const int32_t err_epoch = (int32_t)h[0];
-    const int32_t checked = P.last_checked_epoch;
-    P.last_checked_epoch = P.epoch;
-    if (err_epoch > checked && err_epoch <= P.epoch) {
-        set_error("a bounded device wait expired in launch %d", err_epoch);
-        return h[1] ? (mpk_status)h[1] : MPK_ERR_TIMEOUT;
+    if (h[1] != 0) {
+        MPK_CUDA(cudaMemset(P.ctl + 2, 0, 2 * sizeof(unsigned int)));
+        set_error("a bounded device wait expired in a launch of this plan (device epoch %u)", h[0]);
+        return (mpk_status)h[1];
     }
     return MPK_OK;
     MPK_GUARD_END

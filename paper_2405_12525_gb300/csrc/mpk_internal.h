@@ -166,7 +166,7 @@ struct KArgs {
     const int32_t *units;
     int64_t nunits;
     int32_t *flags;  // (p+1) x nchunks, epoch-valued
-    int32_t epoch;
+    unsigned int *epoch_word;  // the last launch's epoch: this launch uses *epoch_word + 1
     unsigned int *ticket;
     unsigned int *exit_count;
     int32_t *err;    // err[0] = epoch of a failed launch, err[1] = status code
@@ -216,8 +216,7 @@ struct Plan {
     unsigned int *ctl = nullptr;  // [0] ticket, [1] exit count, [2] err epoch, [3] err code
     double *work = nullptr;       // work_slots blocks of n*m: powers in plan order, or Chebyshev ring + accumulator
     int32_t work_slots = 0;
-    int32_t epoch = 0;
-    int32_t last_checked_epoch = 0;
+    int64_t launches = 0;  // launches since the flags were last cleared (wrap guard of the epochs)
     int32_t drop_unit = -1;  // armed by mpk_debug_drop_release for the next launch
     unsigned long long *trace = nullptr;  // counters when built with opts.trace
     int grid_mpk[4] = {0, 0, 0, 0};  // persistent grid size per mode

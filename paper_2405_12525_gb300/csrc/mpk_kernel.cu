@@ -317,7 +317,7 @@ __device__ __forceinline__ void phase_a(const KArgs &a, const UnitInfo &u, int b
 
 // phase B: finish unit pf (all of the warp's rows), then publish and release its slot
 template <int M, int MODE, class VT>
-__device__ __forceinline__ void phase_b(const KArgs &a, const Prefetch<M> &pf, const UnitInfo *s_u,
+__device__ __forceinline__ void phase_b(const KArgs &a, int32_t epoch, const Prefetch<M> &pf, const UnitInfo *s_u,
                                         const typename VT::T *sval0, const int32_t *scol0, int *s_done, uint64_t *s_empty,
                                         int cwarp, int lane) {
     constexpr int B = Batch<M>::B;
@@ -384,14 +384,14 @@ __device__ __forceinline__ void phase_b(const KArgs &a, const Prefetch<M> &pf, c
             s_done[pf.slot] = 0;
             fence_acq_rel_gpu();
             if (pf.unit != a.drop_unit)
-                st_relaxed(a.flags + (int64_t)k * a.nchunks + (pf.unit >> 5), a.epoch);
+                st_relaxed(a.flags + (int64_t)k * a.nchunks + (pf.unit >> 5), epoch);
         }
         mbar_arrive(&s_empty[pf.slot]);
     }
 }
 
 // dependency flags v0 .. v0+127 of a unit (4 per lane); flags past `total` read as ready
-__device__ __forceinline__ void dep_load(const KArgs &a, int k, const int (&lo)[kDepRanges],
+__device__ __forceinline__ void dep_load(const KArgs &a, int32_t epoch, int k, const int (&lo)[kDepRanges],
                                          const int (&len)[kDepRanges], int total, int v0, int lane, int (&got)[4]) {
     const int32_t *f = a.flags + (int64_t)(k - 1) * a.nchunks;
 #pragma unroll
@@ -405,19 +405,19 @@ __device__ __forceinline__ void dep_load(const KArgs &a, int k, const int (&lo)[
                 if (idx < 0) v -= len[r];
             }
         }
-        got[q] = idx >= 0 ? ld_relaxed(f + idx) : a.epoch;
+        got[q] = idx >= 0 ? ld_relaxed(f + idx) : epoch;
     }
 }
 
 // all lanes of the control warp: true when every flag of the unit's ranges equals epoch
-__device__ __forceinline__ bool deps_ready(const KArgs &a, int k, const int (&lo)[kDepRanges],
+__device__ __forceinline__ bool deps_ready(const KArgs &a, int32_t epoch, int k, const int (&lo)[kDepRanges],
                                            const int (&len)[kDepRanges], int total, int lane) {
     bool ok = true;
     for (int v0 = 0; v0 < total; v0 += 128) {
         int got[4];
-        dep_load(a, k, lo, len, total, v0, lane, got);
+        dep_load(a, epoch, k, lo, len, total, v0, lane, got);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) ok = ok && got[q] == a.epoch;
+        for (int q = 0; q < 4; ++q) ok = ok && got[q] == epoch;
     }
     return __all_sync(0xffffffffu, ok);
 }
@@ -457,7 +457,11 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
     };
     const long long c_start = tr ? clock64() : 0;
     if (tid < kTraceShared) s_tr[tid] = 0;
+    // Epochs live on the device, so that launches replayed from a CUDA graph stay distinct:
+    // the last block of a launch stores its epoch, the next launch uses that plus one.
+    __shared__ int32_t s_epoch;
     if (tid == 0) {
+        s_epoch = (int32_t)ld_relaxed(reinterpret_cast<const int32_t *>(a.epoch_word)) + 1;
         s_final = -1;
         for (int q = 0; q < kSlots; ++q) {
             s_done[q] = 0;
@@ -467,6 +471,7 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
+    const int32_t epoch = s_epoch;
 
     if (warp == 0) {
         // ------------------------------------------------------------------ control warp
@@ -475,7 +480,7 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
         int slot_use[kSlots] = {};    // phase index (i / kSlots) of that hand-over
         bool aborted = false;
         auto record_timeout = [&]() {
-            if (lane == 0 && atomicExch(a.err, a.epoch) != a.epoch) st_relaxed(a.err + 1, (int)MPK_ERR_TIMEOUT);
+            if (lane == 0 && atomicExch(a.err, epoch) != epoch) st_relaxed(a.err + 1, (int)MPK_ERR_TIMEOUT);
         };
         auto unit_at = [&](unsigned int t) -> int { return (int64_t)t < a.nunits ? __ldg(a.units + t) : -1; };
         // claim pipeline, three units deep: unit i (id u_cur, record r_cur), unit i+1 (u_nxt,
@@ -552,9 +557,9 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
             const int k = u.unit & 31;
             if (k > 1) {
                 const uint64_t t0 = globaltimer();
-                while (!deps_ready(a, k, dlo, dlen, total, lane)) {
+                while (!deps_ready(a, epoch, k, dlo, dlen, total, lane)) {
                     if (lane == 0) tr_add(2, 1);
-                    const bool stop = ld_relaxed(a.err) == a.epoch || timed_out(t0, a.wait_ns);
+                    const bool stop = ld_relaxed(a.err) == epoch || timed_out(t0, a.wait_ns);
                     if (__any_sync(0xffffffffu, stop)) {
                         aborted = true;
                         break;
@@ -637,7 +642,7 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
             }
             if (stop) break;
             if (!got) {  // the control warp gave no sign of life: give up
-                if (lane == 0 && atomicExch(a.err, a.epoch) != a.epoch) st_relaxed(a.err + 1, (int)MPK_ERR_TIMEOUT);
+                if (lane == 0 && atomicExch(a.err, epoch) != epoch) st_relaxed(a.err + 1, (int)MPK_ERR_TIMEOUT);
                 break;
             }
             uint64_t t_got = 0;
@@ -661,10 +666,10 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
                     asm volatile("add.u32 %0, %1, 0;" : "=r"(d) : "r"(h));
                     const long long c1 = clock64();
                     if (lane == 0) tr_add(12, c1 - c0);
-                    phase_b<M, MODE, VT>(a, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane);
+                    phase_b<M, MODE, VT>(a, epoch, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane);
                     if (lane == 0) tr_add(13, clock64() - c1);
                 } else {
-                    phase_b<M, MODE, VT>(a, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane);
+                    phase_b<M, MODE, VT>(a, epoch, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane);
                 }
                 pf.unit = -1;
             }
@@ -680,7 +685,7 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
             atomicAdd(a.trace + kTraceShared, (unsigned long long)(clock64() - c_start));
         }
     }
-    // ---- exit: the last block resets the ticket for the next launch on the stream
+    // ---- exit: the last block resets the ticket and stores the epoch for the next launch
     __syncthreads();
     if (tid == 0) {
         __threadfence();
@@ -688,6 +693,7 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
         if (done == gridDim.x - 1) {
             *a.ticket = 0u;
             *a.exit_count = 0u;
+            *a.epoch_word = (unsigned int)epoch;
             __threadfence();
         }
     }

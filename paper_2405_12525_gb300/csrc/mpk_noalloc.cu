@@ -56,9 +56,10 @@ extern "C" mpk_status mpk_apply_noalloc(const mpk_plan_t *Ph, const double *X, i
             fail(MPK_ERR_UNSUPPORTED, "mpk_apply_noalloc needs a plan in MPK_ORDER_PLAN (or without levels)");
         if (p < 1 || p > P.p_max) fail(MPK_ERR_INVALID, "p = %d outside [1, p_max = %d]", p, P.p_max);
         if (P.n > 0 && (!X || !Y)) fail(MPK_ERR_INVALID, "NULL X or Y");
-        // scratch layout: [0..3] ticket, exit count, error epoch, error code; then the
-        // completion flags of powers 0..p for every chunk
-        const int64_t need = 4 + (int64_t)(p + 1) * (P.num_chunks > 0 ? P.num_chunks : 1);
+        // scratch layout: [0..4] ticket, exit count, error epoch, error code, epoch of the last
+        // launch (zero: this launch is epoch 1); from [8] the completion flags of powers 0..p
+        // for every chunk
+        const int64_t need = 8 + (int64_t)(p + 1) * (P.num_chunks > 0 ? P.num_chunks : 1);
         if (need > kNoAllocInts)
             fail(MPK_ERR_TOO_LARGE,
                  "mpk_apply_noalloc needs %lld scratch words for %d chunks and p = %d; the fixed scratch holds %lld "
@@ -84,8 +85,8 @@ extern "C" mpk_status mpk_apply_noalloc(const mpk_plan_t *Ph, const double *X, i
             a.nchunks = P.num_chunks;
             a.units = P.units + P.unit_off[p];
             a.nunits = P.unit_off[p + 1] - P.unit_off[p];
-            a.flags = scratch + 4;
-            a.epoch = 1;
+            a.flags = scratch + 8;
+            a.epoch_word = reinterpret_cast<unsigned int *>(scratch + 4);
             a.ticket = reinterpret_cast<unsigned int *>(scratch);
             a.exit_count = reinterpret_cast<unsigned int *>(scratch + 1);
             a.err = scratch + 2;

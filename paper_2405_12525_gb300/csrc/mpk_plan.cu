@@ -500,8 +500,9 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
             P->trace = P->arena.alloc_n<unsigned long long>(MPK_TRACE_COUNTERS);
             MPK_CUDA(cudaMemsetAsync(P->trace, 0, sizeof(unsigned long long) * MPK_TRACE_COUNTERS, s));
         }
-        P->ctl = P->arena.alloc_n<unsigned int>(4);
-        MPK_CUDA(cudaMemsetAsync(P->ctl, 0, 4 * sizeof(unsigned int), s));
+        // ticket, exit count, epoch and code of a failed launch, epoch of the last launch
+        P->ctl = P->arena.alloc_n<unsigned int>(8);
+        MPK_CUDA(cudaMemsetAsync(P->ctl, 0, 8 * sizeof(unsigned int), s));
         P->work_slots = std::max(pmax + 1, 4);  // all powers (original order) or ring of 3 + accumulator
         P->work = P->arena.alloc_n<double>((int64_t)P->work_slots * n * m + 1);
         MPK_CUDA(cudaStreamSynchronize(s));  // host vectors above must outlive their copies

@@ -397,3 +397,27 @@ def test_cheb_complex_time_step(mpk):
     z0 = psi[:, 0] + 1j * psi[:, 1]
     g = got.cpu().numpy()
     assert abs(np.linalg.norm(g[:, 0] + 1j * g[:, 1]) / np.linalg.norm(z0) - 1) < 1e-12
+
+
+def test_apply_replays_from_cuda_graph(mpk):
+    # launch epochs live on the device: every replay of a captured apply is a new launch
+    A = gen.laplacian_3d(21, 13, 11)
+    dA = _dev(A, mpk, True)
+    L = mpk.build_levels(dA, 0)
+    P = mpk.plan(dA, L, p_max=6, cache_bytes=200000, order=mpk.ORDER_PLAN)
+    pe = L.perm.cpu().numpy()
+    Xs = torch.zeros((A.n, 1), dtype=torch.float64, device="cuda")
+    Ys = torch.zeros((7, A.n, 1), dtype=torch.float64, device="cuda")
+    P.apply(Xs, 6, Y=Ys)  # outside the capture: kernel attributes and occupancy are set up
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        P.apply(Xs, 6, Y=Ys)
+    for seed in (401, 402, 403):
+        X = gen.vector(A.n, 1, stream=seed)
+        Xs.copy_(torch.from_numpy(np.ascontiguousarray(X[pe])))
+        Ys.fill_(float("nan"))
+        g.replay()
+        torch.cuda.synchronize()
+        P.sync_status()
+        _check_powers(Ys, oracle.mpk(A, X, 6)[:, pe, :])
