@@ -225,6 +225,29 @@ mpk_status mpk_cheb_filter(const mpk_plan_t *P, const double *X, int32_t degree,
 #define MPK_TRACE_COUNTERS 17
 mpk_status mpk_read_trace(const mpk_plan_t *P, int64_t *counters, mpk_stream stream);
 
+/* ---------------------------------------------------------------------------------------
+ * Batched MPK: `count` independent matrices with their own sizes and powers in one plan and
+ * one persistent launch per apply.  The plan is that of the block-diagonal direct sum of the
+ * matrices (Sec. 3's level blocking applies to it unchanged): block i keeps its own BFS
+ * levels and row range, groups never span two blocks, and the blocks' Lp-diagram cells are
+ * merged line by line into one ticket space, so that small blocks run side by side.
+ * mats[i]: device CSR as for mpk_plan, all of one val_type; p_each[i] in [1, opts->p_max];
+ * opts->nrhs applies to every block and opts->order to each block's own numbering (in plan
+ * order block i uses the numbering of its own levels, mpk_build_levels(mats[i], 0)).
+ * Synchronises.  The plan runs through mpk_batch_apply only (mpk_apply and the others fail
+ * with MPK_ERR_INVALID on it).
+ * ------------------------------------------------------------------------------------- */
+mpk_status mpk_batch_plan(const mpk_csr *mats, int32_t count, const int32_t *p_each,
+                          const mpk_plan_opts *opts, mpk_stream stream, mpk_plan_t **out);
+
+/* X[i], Y[i]: host arrays of `count` device pointers; X[i] is n_i x nrhs and Y[i] receives
+ * (p_each[i] + 1) x n_i x nrhs, powers 0..p_each[i] of block i (row-major, float64).
+ * Asynchronous on `stream` (capturable in a CUDA graph); errors as for mpk_apply. */
+mpk_status mpk_batch_apply(const mpk_plan_t *P, const double *const *X, double *const *Y, mpk_stream stream);
+
+/* Number of blocks, their row offsets (count + 1 entries) and powers; NULL outputs are skipped. */
+mpk_status mpk_batch_describe(const mpk_plan_t *P, int32_t *count, int32_t *row_offsets, int32_t *powers);
+
 /* Synchronises `stream` and reports a device-side failure of the plan's calls since the
  * last mpk_sync_status (MPK_ERR_TIMEOUT), else MPK_OK or a CUDA error.  The plan keeps its
  * launch epoch on the device, so calls captured in a CUDA graph can be replayed: every replay

@@ -21,7 +21,8 @@ from ._build import LIB as _LIB_PATH
 from ._build import build as _build_lib
 
 __all__ = ["build", "load", "CsrMatrix", "Levels", "Plan", "build_levels", "plan", "MpkError",
-           "probe_load", "probe_dfma", "device_info", "widen_values", "EXPORTED_SYMBOLS"]
+           "probe_load", "probe_dfma", "device_info", "widen_values", "BatchPlan", "batch_plan",
+           "EXPORTED_SYMBOLS"]
 
 MPK_OK, MPK_ERR_INVALID, MPK_ERR_TOO_LARGE, MPK_ERR_OOM, MPK_ERR_TIMEOUT = 0, 1, 2, 3, 4
 MPK_ERR_CUDA, MPK_ERR_BUDGET, MPK_ERR_UNSUPPORTED = 5, 6, 7
@@ -33,7 +34,7 @@ EXPORTED_SYMBOLS = [
     "mpk_plan_describe", "mpk_plan_export_csr", "mpk_plan_destroy", "mpk_apply", "mpk_spmv_powers",
     "mpk_cheb_filter", "mpk_sync_status", "mpk_probe_load", "mpk_probe_dfma", "mpk_device_info",
     "mpk_status_string", "mpk_last_error", "mpk_debug_drop_release", "mpk_read_trace", "mpk_apply_noalloc",
-    "mpk_widen_values",
+    "mpk_widen_values", "mpk_batch_plan", "mpk_batch_apply", "mpk_batch_describe",
 ]
 
 
@@ -100,6 +101,9 @@ def load():
         "mpk_read_trace": [vp, vp, vp],
         "mpk_apply_noalloc": [vp, vp, i32, vp, vp, vp],
         "mpk_widen_values": [i32, vp, i64, vp, vp],
+        "mpk_batch_plan": [vp, i32, vp, C.POINTER(_Opts), vp, C.POINTER(vp)],
+        "mpk_batch_apply": [vp, vp, vp, vp],
+        "mpk_batch_describe": [vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -385,6 +389,74 @@ def probe_load(buf, reps: int, ctas_per_sm: int, sink, stream=None):
 
 def probe_dfma(blocks: int, iters: int, sink, stream=None):
     _check(load().mpk_probe_dfma(blocks, iters, _ptr(sink), _stream(stream)))
+
+
+class BatchPlan:
+    """Plan of several matrices run together (mpk_batch_plan); owns the library handle."""
+
+    def __init__(self, handle, lib, mats, p_each, nrhs):
+        self._h = handle
+        self._lib = lib
+        self.sizes = [A.n for A in mats]
+        self.p_each = list(p_each)
+        self.nrhs = nrhs
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            self._lib.mpk_plan_destroy(self._h)
+            self._h = None
+
+    def describe(self) -> dict:
+        import numpy as np
+        cnt = C.c_int32()
+        _check(self._lib.mpk_batch_describe(self._h, C.byref(cnt), None, None))
+        offs = np.zeros(cnt.value + 1, np.int32)
+        pw = np.zeros(cnt.value, np.int32)
+        _check(self._lib.mpk_batch_describe(self._h, None, offs.ctypes.data, pw.ctypes.data))
+        d = _Desc()
+        _check(self._lib.mpk_plan_describe(self._h, C.byref(d)))
+        out = {f: getattr(d, f) for f, _ in _Desc._fields_ if not f.endswith("_dev")}
+        out.update(count=cnt.value, row_offsets=offs.tolist(), powers=pw.tolist())
+        return out
+
+    @property
+    def group_row_ptr(self):
+        d = _Desc()
+        _check(self._lib.mpk_plan_describe(self._h, C.byref(d)))
+        return _device_i32_copy(d.group_row_ptr_dev, d.num_groups + 1)
+
+    def apply(self, Xs, Ys=None, stream=None):
+        """Ys[i] = powers 0..p_i of block i applied to Xs[i] (lists of CUDA tensors)."""
+        torch = _torch()
+        if len(Xs) != len(self.sizes):
+            raise ValueError("one X per matrix")
+        if Ys is None:
+            Ys = [torch.empty((p + 1, n, self.nrhs), dtype=torch.float64, device=X.device)
+                  for X, n, p in zip(Xs, self.sizes, self.p_each)]
+        for X, n in zip(Xs, self.sizes):
+            if X.dtype != torch.float64 or not X.is_cuda or not X.is_contiguous() or X.numel() != n * self.nrhs:
+                raise TypeError("each X must be a contiguous float64 CUDA tensor of n x nrhs")
+        xp = (C.c_void_p * len(Xs))(*[_ptr(X) for X in Xs])
+        yp = (C.c_void_p * len(Ys))(*[_ptr(Y) for Y in Ys])
+        _check(self._lib.mpk_batch_apply(self._h, C.cast(xp, C.c_void_p), C.cast(yp, C.c_void_p), _stream(stream)))
+        return Ys
+
+
+def batch_plan(mats, p_each, p_max: int = 0, nrhs: int = 1, cache_bytes: int = 0, order: int = ORDER_ORIGINAL,
+               chunk_rows: int = 0, wait_limit_ns: int = 0, mem_budget: int = 0, stream=None) -> BatchPlan:
+    """One plan and one launch for several matrices (list of CsrMatrix, powers per matrix)."""
+    lib = load()
+    o = _Opts()
+    lib.mpk_plan_opts_default(C.byref(o))
+    o.p_max = p_max or max(p_each)
+    o.nrhs, o.cache_bytes, o.order = nrhs, cache_bytes, order
+    o.chunk_rows, o.wait_limit_ns, o.mem_budget = chunk_rows, wait_limit_ns, mem_budget
+    cs = (_Csr * len(mats))(*[A._c() for A in mats])
+    pe = (C.c_int32 * len(mats))(*[int(p) for p in p_each])
+    h = C.c_void_p()
+    _check(lib.mpk_batch_plan(C.cast(cs, C.c_void_p), len(mats), C.cast(pe, C.c_void_p), C.byref(o),
+                              _stream(stream), C.byref(h)))
+    return BatchPlan(h, lib, mats, p_each, nrhs)
 
 
 def widen_values(values, stream=None):

@@ -13,22 +13,6 @@ const char *last_error_text();
 
 using namespace mpk;
 
-#define MPK_GUARD_BEGIN try {
-#define MPK_GUARD_END                                                  \
-    }                                                                  \
-    catch (const Fail &f) {                                            \
-        return f.status;                                               \
-    }                                                                  \
-    catch (const std::bad_alloc &) {                                   \
-        set_error("host allocation failed");                           \
-        return MPK_ERR_OOM;                                            \
-    }                                                                  \
-    catch (...) {                                                      \
-        set_error("unexpected internal error");                        \
-        return MPK_ERR_CUDA;                                           \
-    }
-
-static cudaStream_t as_stream(mpk_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 
 // ---------------------------------------------------------------------------------------- levels
 extern "C" mpk_status mpk_build_levels(const mpk_csr *A, int32_t root, mpk_stream stream, mpk_levels **out) {
@@ -135,7 +119,7 @@ extern "C" void mpk_plan_destroy(mpk_plan_t *P) {
 // Each launch of the level-blocked kernel takes the next epoch on the device (ctl[4]); before
 // the epochs could wrap, the flags and the epoch are cleared (launches replayed from a CUDA
 // graph are not counted here).
-static void next_epoch(Plan &P, cudaStream_t s) {
+void mpk::next_epoch(Plan &P, cudaStream_t s) {
     if (++P.launches >= ((int64_t)1 << 30)) {
         MPK_CUDA(cudaMemsetAsync(P.flags, 0, sizeof(int32_t) * (size_t)(P.p_max + 1) * std::max(1, P.num_chunks), s));
         MPK_CUDA(cudaMemsetAsync(P.ctl + 2, 0, 3 * sizeof(unsigned int), s));
@@ -143,7 +127,7 @@ static void next_epoch(Plan &P, cudaStream_t s) {
     }
 }
 
-static KArgs base_args(Plan &P, int32_t p) {
+KArgs mpk::base_args(Plan &P, int32_t p) {
     KArgs a;
     std::memset(&a, 0, sizeof(a));
     a.val = P.val;
@@ -175,6 +159,7 @@ static KArgs base_args(Plan &P, int32_t p) {
 static void check_apply_args(const mpk_plan_t *Ph, const double *X, int32_t p, const double *Y) {
     if (!Ph || !Ph->impl) fail(MPK_ERR_INVALID, "plan is NULL");
     const Plan &P = *Ph->impl;
+    if (!P.inst_row.empty()) fail(MPK_ERR_INVALID, "a batch plan runs through mpk_batch_apply");
     if (p < 0 || p > P.p_max) fail(MPK_ERR_INVALID, "p = %d outside [0, p_max = %d]", p, P.p_max);
     if (P.n > 0 && (!X || !Y)) fail(MPK_ERR_INVALID, "NULL X or Y");
 }
@@ -238,6 +223,7 @@ extern "C" mpk_status mpk_cheb_filter(const mpk_plan_t *Ph, const double *X, int
     MPK_GUARD_BEGIN
     if (!Ph || !Ph->impl) fail(MPK_ERR_INVALID, "plan is NULL");
     Plan &P = *const_cast<Plan *>(Ph->impl);
+    if (!P.inst_row.empty()) fail(MPK_ERR_INVALID, "a batch plan runs through mpk_batch_apply");
     if (degree < 0) fail(MPK_ERR_INVALID, "degree must be >= 0");
     if (!coeff_re) fail(MPK_ERR_INVALID, "coeff_re is NULL");
     if (!(scale != 0.0)) fail(MPK_ERR_INVALID, "scale must be non-zero");

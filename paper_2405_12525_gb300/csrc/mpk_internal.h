@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdarg>
+#include <new>
 #include <cstdint>
 #include <cstdio>
 #include <vector>
@@ -31,6 +32,24 @@ void set_error(const char *fmt, ...);
     } while (0)
 
 #define MPK_LAUNCHED() MPK_CUDA(cudaGetLastError())
+
+// extern "C" entry points: internal failures become an mpk_status
+#define MPK_GUARD_BEGIN try {
+#define MPK_GUARD_END                                                  \
+    }                                                                  \
+    catch (const ::mpk::Fail &f) {                                     \
+        return f.status;                                               \
+    }                                                                  \
+    catch (const std::bad_alloc &) {                                   \
+        ::mpk::set_error("host allocation failed");                    \
+        return MPK_ERR_OOM;                                            \
+    }                                                                  \
+    catch (...) {                                                      \
+        ::mpk::set_error("unexpected internal error");                 \
+        return MPK_ERR_CUDA;                                           \
+    }
+
+inline cudaStream_t as_stream(mpk_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 
 // ----------------------------------------------------------------------------- memory
 // Device allocation with byte accounting against an optional budget.
@@ -217,6 +236,9 @@ struct Plan {
     double *work = nullptr;       // work_slots blocks of n*m: powers in plan order, or Chebyshev ring + accumulator
     int32_t work_slots = 0;
     int64_t launches = 0;  // launches since the flags were last cleared (wrap guard of the epochs)
+    // batch plans (direct sum of several matrices, mpk_batch_plan): instance i owns rows
+    // [inst_row[i], inst_row[i+1]) in both numberings and takes powers 1..inst_p[i]
+    std::vector<int32_t> inst_row, inst_p;
     int32_t drop_unit = -1;  // armed by mpk_debug_drop_release for the next launch
     unsigned long long *trace = nullptr;  // counters when built with opts.trace
     int grid_mpk[4] = {0, 0, 0, 0};  // persistent grid size per mode
@@ -226,10 +248,13 @@ struct Plan {
 // kernels (mpk_kernel.cu)
 void launch_mpk(const Plan &P, KArgs &a, int mode, cudaStream_t s);
 void launch_spmv(const Plan &P, const double *x, double *y, cudaStream_t s);
+// Y[k][i] = W[k][iperm[i]] (iperm NULL: W[k][base + i]) for k = 1..p, i < n; W's powers are
+// w_pstride doubles apart (< 0: n * m), Y's n * m
 void launch_scatter_powers(const double *W, const int32_t *iperm, double *Y, int32_t n, int32_t m, int32_t p,
-                           cudaStream_t s);
+                           cudaStream_t s, int64_t w_pstride = -1, int32_t base = 0);
+// dst[r] = src[perm[r] - base] for r < n (m values a row; perm NULL: the identity)
 void launch_gather_rows(const double *src, const int32_t *perm, double *dst, int32_t n, int32_t m,
-                        cudaStream_t s);
+                        cudaStream_t s, int32_t base = 0);
 void launch_scatter_rows(const double *src, const int32_t *iperm, double *dst, int32_t n, int32_t m,
                          cudaStream_t s);
 void launch_cheb_init(const double *v0, double *acc, int32_t n, int32_t m, double c0re, double c0im,
@@ -243,7 +268,13 @@ Levels *build_levels(const mpk_csr *A, int32_t root, cudaStream_t s);
 void validate_csr(const mpk_csr *A, cudaStream_t s);
 
 // planner (mpk_plan.cu)
-Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cudaStream_t s);
+// inst_row / inst_p: batch plans only (instance row offsets, count + 1 entries; powers per instance)
+// the next launch epoch of P (clears the flags before the epochs could wrap)
+void next_epoch(Plan &P, cudaStream_t s);
+// kernel arguments of P for the unit table of power p
+KArgs base_args(Plan &P, int32_t p);
+Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cudaStream_t s,
+                 const std::vector<int32_t> *inst_row = nullptr, const std::vector<int32_t> *inst_p = nullptr);
 void export_csr(const Plan &P, int32_t *rp, int32_t *ci, double *va, cudaStream_t s);
 
 // probes (mpk_kernel.cu)

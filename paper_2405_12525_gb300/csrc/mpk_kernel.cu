@@ -727,12 +727,13 @@ __global__ void __launch_bounds__(kSpmvBS) k_spmv(const typename VT::T *__restri
 }
 
 // ----------------------------------------------------------------------------- row moves
-// dst[r] = src[perm[r]] (m values per row); coalesced writes
-__global__ void k_gather_rows(const double *src, const int32_t *perm, double *dst, int32_t n, int32_t m) {
+// dst[r] = src[perm[r] - base] (m values per row; perm NULL: the identity); coalesced writes
+__global__ void k_gather_rows(const double *src, const int32_t *perm, int32_t base, double *dst, int32_t n,
+                              int32_t m) {
     const int64_t total = (int64_t)n * m, stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += stride) {
         const int64_t r = t / m, i = t - r * m;
-        dst[t] = src[(int64_t)(perm ? perm[r] : r) * m + i];
+        dst[t] = src[(int64_t)((perm ? perm[r] : (int32_t)r) - base) * m + i];
     }
 }
 
@@ -764,9 +765,10 @@ static int grid_rows(int64_t n) {
     return (int)(g < 1 ? 1 : g);
 }
 
-void launch_gather_rows(const double *src, const int32_t *perm, double *dst, int32_t n, int32_t m, cudaStream_t s) {
+void launch_gather_rows(const double *src, const int32_t *perm, double *dst, int32_t n, int32_t m, cudaStream_t s,
+                        int32_t base) {
     if (n <= 0) return;
-    k_gather_rows<<<grid_rows((int64_t)n * m), 256, 0, s>>>(src, perm, dst, n, m);
+    k_gather_rows<<<grid_rows((int64_t)n * m), 256, 0, s>>>(src, perm, base, dst, n, m);
     MPK_LAUNCHED();
 }
 
@@ -784,17 +786,18 @@ void launch_scatter_rows(const double *src, const int32_t *iperm, double *dst, i
 constexpr int kScatterBS = 1024, kScatterItems = 16, kScatterTile = kScatterBS * kScatterItems;
 
 __global__ void __launch_bounds__(kScatterBS, 1)
-    k_scatter_powers(const double *W, const int32_t *__restrict__ iperm, double *Y, int32_t n, int32_t m, int32_t p) {
+    k_scatter_powers(const double *W, int64_t w_pstride, const int32_t *__restrict__ iperm, int32_t w_row0, double *Y,
+                     int32_t n, int32_t m, int32_t p) {
     const int64_t nm = (int64_t)n * m;
     for (int64_t base = (int64_t)blockIdx.x * kScatterTile; base < n; base += (int64_t)gridDim.x * kScatterTile) {
         int32_t src[kScatterItems];
 #pragma unroll
         for (int q = 0; q < kScatterItems; ++q) {
             const int64_t i = base + (int64_t)q * kScatterBS + threadIdx.x;
-            src[q] = i < n ? __ldg(iperm + i) : -1;
+            src[q] = i < n ? (iperm ? __ldg(iperm + i) : w_row0 + (int32_t)i) : -1;
         }
         for (int k = 1; k <= p; ++k) {
-            const double *w = W + k * nm;
+            const double *w = W + k * w_pstride;
             double *y = Y + k * nm;
 #pragma unroll
             for (int q = 0; q < kScatterItems; ++q) {
@@ -807,9 +810,10 @@ __global__ void __launch_bounds__(kScatterBS, 1)
 }
 
 void launch_scatter_powers(const double *W, const int32_t *iperm, double *Y, int32_t n, int32_t m, int32_t p,
-                           cudaStream_t s) {
+                           cudaStream_t s, int64_t w_pstride, int32_t base) {
     if (n <= 0 || p <= 0) return;
-    k_scatter_powers<<<device_sms(), kScatterBS, 0, s>>>(W, iperm, Y, n, m, p);
+    if (w_pstride < 0) w_pstride = (int64_t)n * m;
+    k_scatter_powers<<<device_sms(), kScatterBS, 0, s>>>(W, w_pstride, iperm, base, Y, n, m, p);
     MPK_LAUNCHED();
 }
 

@@ -52,6 +52,7 @@ extern "C" mpk_status mpk_apply_noalloc(const mpk_plan_t *Ph, const double *X, i
     try {
         if (!Ph || !Ph->impl) fail(MPK_ERR_INVALID, "plan is NULL");
         const Plan &P = *Ph->impl;
+        if (!P.inst_row.empty()) fail(MPK_ERR_INVALID, "a batch plan runs through mpk_batch_apply");
         if (!(P.identity || P.order == MPK_ORDER_PLAN))
             fail(MPK_ERR_UNSUPPORTED, "mpk_apply_noalloc needs a plan in MPK_ORDER_PLAN (or without levels)");
         if (p < 1 || p > P.p_max) fail(MPK_ERR_INVALID, "p = %d outside [1, p_max = %d]", p, P.p_max);

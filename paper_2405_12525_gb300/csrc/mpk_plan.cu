@@ -256,7 +256,8 @@ void export_csr(const Plan &P, int32_t *rp, int32_t *ci, double *va, cudaStream_
     MPK_CUDA(cudaStreamSynchronize(s));
 }
 
-Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cudaStream_t s) {
+Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cudaStream_t s,
+                 const std::vector<int32_t> *inst_row, const std::vector<int32_t> *inst_p) {
     if (!o) fail(MPK_ERR_INVALID, "options are NULL");
     validate_csr(A, s);
     if (o->p_max < 1 || o->p_max > kMaxP) fail(MPK_ERR_INVALID, "p_max must be in [1, %d]", kMaxP);
@@ -287,6 +288,13 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         P->group_budget = P->cache_bytes / P->window;
         P->wait_ns = o->wait_limit_ns ? o->wait_limit_ns : 2000000000LL;
         P->num_levels = L ? L->num_levels : 0;
+        const bool batch = inst_row != nullptr;
+        if (batch) {
+            if (!L || !inst_p || inst_row->size() != inst_p->size() + 1 || inst_row->back() != n)
+                fail(MPK_ERR_INVALID, "inconsistent batch description");
+            P->inst_row = *inst_row;
+            P->inst_p = *inst_p;
+        }
 
         // ---- permutation (plan-owned copies)
         if (!P->identity && n > 0) {
@@ -319,13 +327,25 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
             const std::vector<int32_t> &lp = L->h_level_ptr;
             const int64_t B = P->group_budget;
             const int64_t vb = P->val_bytes;  // value bytes of the stored type
+            // batch plans: a group never holds levels of two instances (every instance is a
+            // union of components, numbered after the previous one, so it starts a level)
+            std::vector<char> inst_start((size_t)NL, 0);
+            if (batch) {
+                for (size_t i = 0; i + 1 < P->inst_row.size(); ++i) {
+                    if (P->inst_row[i + 1] == P->inst_row[i]) continue;  // empty instance
+                    const auto it = std::lower_bound(lp.begin(), lp.begin() + NL, P->inst_row[i]);
+                    if (it == lp.begin() + NL || *it != P->inst_row[i])
+                        fail(MPK_ERR_INVALID, "instance %zu does not start a level", i);
+                    inst_start[it - lp.begin()] = 1;
+                }
+            }
             int64_t cur = 0;
             g_level.push_back(0);
             for (int32_t l = 0; l < NL; ++l) {
                 const int64_t rows = lp[l + 1] - lp[l];
                 const int64_t nz = (int64_t)h_nz[l + 1] - h_nz[l];
                 const int64_t b = (vb + 4) * nz + 4 * rows + 16 * (int64_t)m * rows;
-                if (l > 0 && cur + b <= B) {
+                if (l > 0 && !inst_start[l] && cur + b <= B) {
                     cur += b;
                 } else {
                     if (l > 0) g_level.push_back(l);
@@ -479,7 +499,31 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         //      ascending, k ascending inside a line, chunks in row order; unit = chunk << 5 | k
         P->unit_off.assign((size_t)pmax + 2, 0);
         std::vector<int32_t> units;
-        for (int32_t p = 1; p <= pmax; ++p) {
+        if (batch) {
+            // one table: every instance's cells up to its own power, the instances' lines
+            // (counted from each instance's first group) merged, so that all instances advance
+            // together; each instance keeps its own order, so dependencies keep smaller tickets
+            const int32_t NI = (int32_t)P->inst_p.size();
+            std::vector<int32_t> gi0((size_t)NI), gi1((size_t)NI);
+            int32_t dmax = 0;
+            for (int32_t i = 0; i < NI; ++i) {
+                gi0[i] = (int32_t)(std::lower_bound(g_row.begin(), g_row.end() - 1, P->inst_row[i]) - g_row.begin());
+                gi1[i] = (int32_t)(std::lower_bound(g_row.begin(), g_row.end() - 1, P->inst_row[i + 1]) - g_row.begin());
+                if (P->inst_row[i + 1] == n) gi1[i] = G;
+                const int32_t pi = P->inst_p[i];
+                if (pi < 1 || pi > pmax) fail(MPK_ERR_INVALID, "instance %d: p = %d outside [1, p_max]", i, pi);
+                if (gi1[i] > gi0[i]) dmax = std::max(dmax, gi1[i] - gi0[i] - 1 + kSlotSkew * pi);
+            }
+            for (int32_t d = kSlotSkew; d <= dmax; ++d)
+                for (int32_t i = 0; i < NI; ++i)
+                    for (int32_t k = 1; k <= P->inst_p[i]; ++k) {
+                        const int32_t g = gi0[i] + d - kSlotSkew * k;
+                        if (g < gi0[i] || g >= gi1[i]) continue;
+                        for (int32_t c = g_chunk[g]; c < g_chunk[g + 1]; ++c) units.push_back((c << 5) | k);
+                    }
+            P->unit_off[pmax + 1] = (int64_t)units.size();  // the table of p = p_max is the batch table
+        }
+        for (int32_t p = 1; p <= pmax && !batch; ++p) {
             P->unit_off[p] = (int64_t)units.size();
             for (int32_t d = kSlotSkew; d <= G - 1 + kSlotSkew * p; ++d)
                 for (int32_t k = 1; k <= p; ++k) {
@@ -488,7 +532,7 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
                     for (int32_t c = g_chunk[g]; c < g_chunk[g + 1]; ++c) units.push_back((c << 5) | k);
                 }
         }
-        P->unit_off[pmax + 1] = (int64_t)units.size();
+        if (!batch) P->unit_off[pmax + 1] = (int64_t)units.size();
         P->units = P->arena.alloc_n<int32_t>((int64_t)units.size() + 1);
         if (!units.empty())
             MPK_CUDA(cudaMemcpyAsync(P->units, units.data(), sizeof(int32_t) * units.size(), cudaMemcpyHostToDevice, s));
