@@ -65,7 +65,9 @@ def parse():
     ap.add_argument("--p", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="laplace3d", choices=["laplace3d", "cheb_xxz"])
+    ap.add_argument("--workload", default="laplace3d", choices=["laplace3d", "cheb_xxz", "batch_cfg3"])
+    ap.add_argument("--batch-count", type=int, default=64, help="matrices of the batch workload")
+    ap.add_argument("--batch-nmax", type=float, default=2e6, help="largest matrix size of the batch workload")
     ap.add_argument("--values", default="f64", choices=["f64", "f32", "bf16"],
                     help="storage type of the matrix values (accumulation stays float64); the Laplacian's "
                          "{6, -1} are exact in all three")
@@ -367,6 +369,130 @@ def main_cheb(args):
         dist.destroy_process_group()
 
 
+def batch_workload(count: int, nmin: float, nmax: float):
+    """Config 3: `count` matrices, sizes log-uniform in [nmin, nmax]; even index a 27-point
+    stencil {26, -1} stored as bfloat16 (exact), odd index a symmetric banded random graph
+    (7 upper entries a row within n/100, N(0,1) values, mirrored, plus the diagonal) stored as
+    float32; right-hand sides 1, 4, 8, 16 in turn, powers p ~ U{4..12}."""
+    import numpy as np
+    import gen
+    logn = gen.uniform(gen.derive_seed(600), count, np.log(nmin), np.log(nmax))
+    pu = gen.uniform(gen.derive_seed(601), count, 0.0, 1.0)
+    out = []
+    for i in range(count):
+        n = float(np.exp(logn[i]))
+        p = 4 + min(8, int(pu[i] * 9))
+        m = [1, 4, 8, 16][i % 4]
+        if i % 2 == 0:
+            A, vt = gen.stencil27(max(3, int(round(n ** (1.0 / 3.0))))), "bf16"
+        else:
+            A, vt = gen.banded_random(int(n), stream=620 + i), "f32"
+        out.append((A, vt, m, p))
+    return out
+
+
+def main_batch(args):
+    """Batched uneven MPK (config 3): one launch per (value type, width) batch plan, all of a
+    step's launches replayed from one CUDA graph; compared with one plan per matrix."""
+    import numpy as np
+    import torch
+    import gen
+    import paper_2405_12525_gb300 as mpk
+    from paper_2405_12525_gb300 import autotune
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    mpk.build()
+    t0 = time.perf_counter()
+    work = batch_workload(args.batch_count, 1e4, args.batch_nmax)
+    t_gen = time.perf_counter() - t0
+    vt_code = {"bf16": mpk.MPK_BF16, "f32": mpk.MPK_F32}
+    # blocks: 16 right-hand sides run as two blocks of 8 (same matrix, other columns)
+    groups = {}
+    flops = 0.0
+    for i, (A, vt, m, p) in enumerate(work):
+        dA = mpk.CsrMatrix.from_host(A, is_symmetric=True, value_type=vt_code[vt])
+        for half in range(2 if m == 16 else 1):
+            mm = 8 if m == 16 else m
+            X = torch.from_numpy(gen.vector(A.n, mm, stream=700 + 2 * i + half)).cuda()
+            groups.setdefault((vt, mm), []).append((dA, p, X))
+        flops += 2.0 * A.nnz * m * p
+    plans, tune = {}, {}
+    for key, blocks in groups.items():
+        B, rep = autotune.tune_batch([b[0] for b in blocks], [b[1] for b in blocks], [b[2] for b in blocks],
+                                     nrhs=key[1], order=mpk.ORDER_PLAN)
+        plans[key] = (B, [b[2] for b in blocks], B.apply([b[2] for b in blocks], in_place=True))
+        tune[f"{key[0]}_m{key[1]}"] = {"blocks": len(blocks), "best": rep[0][1], "ms": [round(r[0], 3) for r in rep]}
+
+    def batched_step():  # results stay in each batch plan's workspace (views), as singles write their Y
+        for B, Xs, Ys in plans.values():
+            B.apply(Xs, in_place=True)
+
+    # one plan per block, applied one after the other (the same work without batching)
+    singles = []
+    for blocks in groups.values():
+        for dA, p, X in blocks:
+            P = mpk.plan(dA, mpk.build_levels(dA, 0), p_max=p, nrhs=X.shape[1], order=mpk.ORDER_PLAN)
+            singles.append((P, p, X, torch.empty((p + 1, dA.n, X.shape[1]), dtype=torch.float64, device="cuda")))
+
+    def single_step():
+        for P, p, X, Y in singles:
+            P.apply(X, p, Y=Y)
+
+    def plain_step():
+        for P, p, X, Y in singles:
+            P.spmv_powers(X, p, Y=Y)
+
+    stream = torch.cuda.current_stream()
+
+    def graph_of(fn):
+        fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        return g
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    g_batch = graph_of(batched_step)
+    g_single = graph_of(single_step)
+    with ClockSampler(local) as clk:
+        ms = timed(g_batch.replay, args.steps, args.warmup)
+    ms_single = timed(g_single.replay, max(3, args.steps // 2), 2)
+    ms_plain = timed(plain_step, max(3, args.steps // 2), 2)
+    # the batch equals the matrices run alone
+    same = all(torch.equal(Y1[:, :, :], Yb) for (P, p, X, Y1), Yb in
+               zip(singles, [Y for B, Xs, Ys in plans.values() for Y in Ys]))
+    launches = sum(1 for _ in plans)
+    line = {
+        "metric": "Batched uneven MPK Gflop/s (FP64 accumulation) on 1 GB300", "value": flops / (ms * 1e-3) / 1e9,
+        "unit": "Gflop/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.batch_count} matrices, n log-uniform in [1e4, {args.batch_nmax:.0e}]: 27-point "
+                               "stencils in bfloat16 and banded random graphs in float32, RHS 1/4/8/16, p 4..12, "
+                               "vectors in BFS order",
+                   "total_rows": int(sum(A.n for A, _, _, _ in work)), "total_nnz": int(sum(A.nnz for A, _, _, _ in work)),
+                   "batch_plans": len(plans), "generation_s": round(t_gen, 1), "autotune": tune},
+        "comparator": {"one_plan_per_matrix_ms": ms_single, "plain_spmv_ms": ms_plain,
+                       "speedup_vs_one_plan_per_matrix": ms_single / ms, "speedup_vs_plain": ms_plain / ms,
+                       "bit_identical_to_one_plan_per_matrix": bool(same)},
+        "clocks": clk.summary(), "gpu_launches": args.steps * (launches + sum(len(Xs) for B, Xs, Ys in plans.values())),
+        "cpu_baseline": None, "e2e": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.warmup < 3:
@@ -375,6 +501,8 @@ def main():
         return run_reference(args)
     if args.workload == "cheb_xxz":
         return main_cheb(args)
+    if args.workload == "batch_cfg3":
+        return main_batch(args)
     rank, world, local = dist_env()
     import numpy as np
     import torch

@@ -242,8 +242,15 @@ mpk_status mpk_batch_plan(const mpk_csr *mats, int32_t count, const int32_t *p_e
 
 /* X[i], Y[i]: host arrays of `count` device pointers; X[i] is n_i x nrhs and Y[i] receives
  * (p_each[i] + 1) x n_i x nrhs, powers 0..p_each[i] of block i (row-major, float64).
- * Asynchronous on `stream` (capturable in a CUDA graph); errors as for mpk_apply. */
+ * Y[i] = NULL leaves block i's powers in the plan's workspace only (see mpk_batch_workspace),
+ * which saves their copy.  Asynchronous on `stream` (capturable in a CUDA graph); errors as
+ * for mpk_apply. */
 mpk_status mpk_batch_apply(const mpk_plan_t *P, const double *const *X, double *const *Y, mpk_stream stream);
+
+/* The batch plan's workspace: power k of block i, row r, column j is
+ * work[k * power_stride + (row_offsets[i] + r) * nrhs + j] (in plan order) after an apply,
+ * valid until the next call on the plan. */
+mpk_status mpk_batch_workspace(const mpk_plan_t *P, const double **work, int64_t *power_stride);
 
 /* Number of blocks, their row offsets (count + 1 entries) and powers; NULL outputs are skipped. */
 mpk_status mpk_batch_describe(const mpk_plan_t *P, int32_t *count, int32_t *row_offsets, int32_t *powers);

@@ -34,7 +34,7 @@ EXPORTED_SYMBOLS = [
     "mpk_plan_describe", "mpk_plan_export_csr", "mpk_plan_destroy", "mpk_apply", "mpk_spmv_powers",
     "mpk_cheb_filter", "mpk_sync_status", "mpk_probe_load", "mpk_probe_dfma", "mpk_device_info",
     "mpk_status_string", "mpk_last_error", "mpk_debug_drop_release", "mpk_read_trace", "mpk_apply_noalloc",
-    "mpk_widen_values", "mpk_batch_plan", "mpk_batch_apply", "mpk_batch_describe",
+    "mpk_widen_values", "mpk_batch_plan", "mpk_batch_apply", "mpk_batch_describe", "mpk_batch_workspace",
 ]
 
 
@@ -104,6 +104,7 @@ def load():
         "mpk_batch_plan": [vp, i32, vp, C.POINTER(_Opts), vp, C.POINTER(vp)],
         "mpk_batch_apply": [vp, vp, vp, vp],
         "mpk_batch_describe": [vp, vp, vp, vp],
+        "mpk_batch_workspace": [vp, C.POINTER(vp), C.POINTER(i64)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -241,6 +242,12 @@ def _device_i32_copy(ptr: int, count: int):
     if not ptr or count == 0:
         return torch.empty(count, dtype=torch.int32, device="cuda")
     return torch.as_tensor(_DeviceArray(ptr, count, "<i4"), device="cuda").clone()
+
+
+def _wrap_device_f64(ptr: int, count: int):
+    """A float64 torch view (no copy) of library-owned device memory."""
+    torch = _torch()
+    return torch.as_tensor(_DeviceArray(ptr, count, "<f8"), device="cuda")
 
 
 def build_levels(A: CsrMatrix, root: int = 0, stream=None) -> Levels:
@@ -425,11 +432,35 @@ class BatchPlan:
         _check(self._lib.mpk_plan_describe(self._h, C.byref(d)))
         return _device_i32_copy(d.group_row_ptr_dev, d.num_groups + 1)
 
-    def apply(self, Xs, Ys=None, stream=None):
-        """Ys[i] = powers 0..p_i of block i applied to Xs[i] (lists of CUDA tensors)."""
+    def views(self):
+        """Block i's powers 0..p_i as a (p_i + 1, n_i, nrhs) view of the plan's workspace (plan
+        order), valid until the next call on the plan (for apply(..., in_place=True))."""
+        torch = _torch()
+        w, stride = C.c_void_p(), C.c_int64()
+        _check(self._lib.mpk_batch_workspace(self._h, C.byref(w), C.byref(stride)))
+        cnt = (max(self.p_each) + 1) * stride.value
+        base = _wrap_device_f64(w.value, cnt)
+        out, off = [], 0
+        for n, p in zip(self.sizes, self.p_each):
+            out.append(torch.as_strided(base, (p + 1, n, self.nrhs), (stride.value, self.nrhs, 1), off * self.nrhs))
+            off += n
+        return out
+
+    def apply(self, Xs, Ys=None, stream=None, in_place=False):
+        """Ys[i] = powers 0..p_i of block i applied to Xs[i] (lists of CUDA tensors).  With
+        in_place=True the powers stay in the workspace and views of it are returned."""
         torch = _torch()
         if len(Xs) != len(self.sizes):
             raise ValueError("one X per matrix")
+        if in_place:
+            for X, n in zip(Xs, self.sizes):
+                if X.dtype != torch.float64 or not X.is_cuda or not X.is_contiguous() or X.numel() != n * self.nrhs:
+                    raise TypeError("each X must be a contiguous float64 CUDA tensor of n x nrhs")
+            xp = (C.c_void_p * len(Xs))(*[_ptr(X) for X in Xs])
+            yp = (C.c_void_p * len(Xs))(*([None] * len(Xs)))
+            _check(self._lib.mpk_batch_apply(self._h, C.cast(xp, C.c_void_p), C.cast(yp, C.c_void_p),
+                                             _stream(stream)))
+            return self.views()
         if Ys is None:
             Ys = [torch.empty((p + 1, n, self.nrhs), dtype=torch.float64, device=X.device)
                   for X, n, p in zip(Xs, self.sizes, self.p_each)]

@@ -1,0 +1,63 @@
+"""Autotuner for plan parameters: the group budget C (cache_bytes) and the rows per chunk.
+
+The paper studies p and C by hand (Sec. 6, the p x C parameter scan); here each candidate
+plan is built, timed on the device with CUDA events over a few applies of the caller's
+vectors, and the fastest is kept.  Works for single plans and for batch plans.
+"""
+from __future__ import annotations
+
+import itertools
+
+from . import ORDER_PLAN, batch_plan, device_info, plan
+
+
+def _time(fn, reps: int):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def default_candidates():
+    """Group budgets of 1/4, 1/2, 1 and 2 times the L2 size; the default chunk and twice it."""
+    _, l2 = device_info()
+    return {"cache_bytes": [l2 // 4, l2 // 2, l2, 2 * l2], "chunk_rows": [0, 960]}
+
+
+def tune_plan(dA, levels, p: int, X, nrhs: int = 1, order: int = ORDER_PLAN, candidates=None, reps: int = 3):
+    """Best single plan for Y = A^k X, k <= p; returns (plan, [(ms, options), ...])."""
+    import torch
+    cands = candidates or default_candidates()
+    report, best = [], None
+    Y = torch.empty((p + 1, dA.n, nrhs), dtype=torch.float64, device=X.device)
+    for cb, cr in itertools.product(cands["cache_bytes"], cands["chunk_rows"]):
+        P = plan(dA, levels, p_max=p, nrhs=nrhs, order=order, cache_bytes=cb, chunk_rows=cr)
+        ms = _time(lambda: P.apply(X, p, Y=Y), reps)
+        P.sync_status()
+        report.append((ms, {"cache_bytes": cb, "chunk_rows": cr}))
+        if best is None or ms < best[0]:
+            best = (ms, P)
+        else:
+            del P
+    return best[1], sorted(report, key=lambda t: t[0])
+
+
+def tune_batch(mats, p_each, Xs, nrhs: int = 1, order: int = ORDER_PLAN, candidates=None, reps: int = 3):
+    """Best batch plan for the matrices; returns (batch plan, [(ms, options), ...])."""
+    cands = candidates or default_candidates()
+    report, best = [], None
+    for cb, cr in itertools.product(cands["cache_bytes"], cands["chunk_rows"]):
+        B = batch_plan(mats, p_each, nrhs=nrhs, order=order, cache_bytes=cb, chunk_rows=cr)
+        ms = _time(lambda: B.apply(Xs, in_place=True), reps)
+        report.append((ms, {"cache_bytes": cb, "chunk_rows": cr}))
+        if best is None or ms < best[0]:
+            best = (ms, B)
+        else:
+            del B
+    return best[1], sorted(report, key=lambda t: t[0])

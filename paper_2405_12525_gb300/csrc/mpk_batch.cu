@@ -113,10 +113,11 @@ extern "C" mpk_status mpk_batch_apply(const mpk_plan_t *Ph, const double *const 
     if (!Ph || !Ph->impl) fail(MPK_ERR_INVALID, "plan is NULL");
     Plan &P = *const_cast<Plan *>(Ph->impl);
     if (P.inst_row.empty()) fail(MPK_ERR_INVALID, "not a batch plan (use mpk_apply)");
-    if (!X || !Y) fail(MPK_ERR_INVALID, "NULL vector arrays");
+    if (!X) fail(MPK_ERR_INVALID, "NULL input array");
     const int32_t count = (int32_t)P.inst_p.size();
+    if (!Y) fail(MPK_ERR_INVALID, "NULL output array");
     for (int32_t i = 0; i < count; ++i)
-        if (P.inst_row[i + 1] > P.inst_row[i] && (!X[i] || !Y[i])) fail(MPK_ERR_INVALID, "NULL X or Y of matrix %d", i);
+        if (P.inst_row[i + 1] > P.inst_row[i] && !X[i]) fail(MPK_ERR_INVALID, "NULL X of matrix %d", i);
     if (P.n == 0) return MPK_OK;
     cudaStream_t s = as_stream(stream);
     const int32_t m = P.m;
@@ -128,7 +129,7 @@ extern "C" mpk_status mpk_batch_apply(const mpk_plan_t *Ph, const double *const 
         if (ni == 0) continue;
         launch_gather_rows(X[i], plan_order ? nullptr : P.perm + off, P.work + (int64_t)off * m, ni, m, s,
                            plan_order ? 0 : off);
-        if (Y[i] != X[i])
+        if (Y[i] && Y[i] != X[i])
             MPK_CUDA(cudaMemcpyAsync(Y[i], X[i], sizeof(double) * (size_t)ni * m, cudaMemcpyDeviceToDevice, s));
     }
     next_epoch(P, s);
@@ -140,7 +141,7 @@ extern "C" mpk_status mpk_batch_apply(const mpk_plan_t *Ph, const double *const 
     const int64_t pstride = (int64_t)P.n * m;
     for (int32_t i = 0; i < count; ++i) {
         const int32_t off = P.inst_row[i], ni = P.inst_row[i + 1] - off;
-        if (ni == 0) continue;
+        if (ni == 0 || !Y[i]) continue;  // NULL: the caller reads block i in the workspace
         launch_scatter_powers(P.work, plan_order ? nullptr : P.iperm + off, Y[i], ni, m, P.inst_p[i], s, pstride,
                               plan_order ? off : 0);
     }
@@ -156,6 +157,17 @@ extern "C" mpk_status mpk_batch_describe(const mpk_plan_t *Ph, int32_t *count, i
     if (count) *count = c;
     if (row_offsets) std::copy(P.inst_row.begin(), P.inst_row.end(), row_offsets);
     if (powers) std::copy(P.inst_p.begin(), P.inst_p.end(), powers);
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
+extern "C" mpk_status mpk_batch_workspace(const mpk_plan_t *Ph, const double **work, int64_t *power_stride) {
+    MPK_GUARD_BEGIN
+    if (!Ph || !Ph->impl) fail(MPK_ERR_INVALID, "plan is NULL");
+    const Plan &P = *Ph->impl;
+    if (P.inst_row.empty()) fail(MPK_ERR_INVALID, "not a batch plan");
+    if (work) *work = P.work;
+    if (power_stride) *power_stride = (int64_t)P.n * P.m;
     return MPK_OK;
     MPK_GUARD_END
 }

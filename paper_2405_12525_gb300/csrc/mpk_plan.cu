@@ -339,13 +339,18 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
                     inst_start[it - lp.begin()] = 1;
                 }
             }
-            int64_t cur = 0;
+            int64_t cur = 0, Bl = B;
+            size_t inst = 0;
             g_level.push_back(0);
             for (int32_t l = 0; l < NL; ++l) {
+                if (batch) {  // each block's groups share the cache with its own window only
+                    while (inst + 1 < P->inst_p.size() && lp[l] >= P->inst_row[inst + 1]) ++inst;
+                    Bl = P->cache_bytes / (kSlotSkew * P->inst_p[inst] + 1);
+                }
                 const int64_t rows = lp[l + 1] - lp[l];
                 const int64_t nz = (int64_t)h_nz[l + 1] - h_nz[l];
                 const int64_t b = (vb + 4) * nz + 4 * rows + 16 * (int64_t)m * rows;
-                if (l > 0 && !inst_start[l] && cur + b <= B) {
+                if (l > 0 && !inst_start[l] && cur + b <= Bl) {
                     cur += b;
                 } else {
                     if (l > 0) g_level.push_back(l);
@@ -500,9 +505,10 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         P->unit_off.assign((size_t)pmax + 2, 0);
         std::vector<int32_t> units;
         if (batch) {
-            // one table: every instance's cells up to its own power, the instances' lines
-            // (counted from each instance's first group) merged, so that all instances advance
-            // together; each instance keeps its own order, so dependencies keep smaller tickets
+            // one table: every instance's cells up to its own power, instance after instance;
+            // blocks claim the next instance's first units while the previous one drains, and
+            // about one instance at a time holds the cache.  Each instance keeps its own order,
+            // so dependencies keep smaller tickets.
             const int32_t NI = (int32_t)P->inst_p.size();
             std::vector<int32_t> gi0((size_t)NI), gi1((size_t)NI);
             int32_t dmax = 0;
@@ -514,8 +520,8 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
                 if (pi < 1 || pi > pmax) fail(MPK_ERR_INVALID, "instance %d: p = %d outside [1, p_max]", i, pi);
                 if (gi1[i] > gi0[i]) dmax = std::max(dmax, gi1[i] - gi0[i] - 1 + kSlotSkew * pi);
             }
-            for (int32_t d = kSlotSkew; d <= dmax; ++d)
-                for (int32_t i = 0; i < NI; ++i)
+            for (int32_t i = 0; i < NI; ++i)
+                for (int32_t d = kSlotSkew; d <= dmax; ++d)
                     for (int32_t k = 1; k <= P->inst_p[i]; ++k) {
                         const int32_t g = gi0[i] + d - kSlotSkew * k;
                         if (g < gi0[i] || g >= gi1[i]) continue;

@@ -122,3 +122,17 @@ def test_batch_rejects_mixed_types_and_single_plan_calls(mpk):
     X = torch.zeros((A.n, 1), dtype=torch.float64, device="cuda")
     Y = torch.zeros((3, A.n, 1), dtype=torch.float64, device="cuda")
     assert B._lib.mpk_apply(B._h, X.data_ptr(), 2, Y.data_ptr(), None) == mpk.MPK_ERR_INVALID
+
+
+def test_batch_in_place_views(mpk):
+    blocks = _blocks()
+    mats = [mpk.CsrMatrix.from_host(A, is_symmetric=sym) for A, sym, _ in blocks]
+    p_each = [p for _, _, p in blocks]
+    B = mpk.batch_plan(mats, p_each, nrhs=2, order=mpk.ORDER_PLAN)
+    host = [gen.vector(A.n, 2, stream=540 + i) for i, (A, _, _) in enumerate(blocks)]
+    perms = [oracle.levels(A, 0)[1] for A, _, _ in blocks]
+    Xs = [torch.from_numpy(np.ascontiguousarray(h[pe])).cuda() for h, pe in zip(host, perms)]
+    views = B.apply(Xs, in_place=True)
+    torch.cuda.synchronize()
+    for (A, _, p), h, pe, V in zip(blocks, host, perms, views):
+        assert _bits_equal(V.cpu().numpy(), oracle.mpk(A, h, p)[:, pe, :])
