@@ -65,7 +65,10 @@ def parse():
     ap.add_argument("--p", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="laplace3d", choices=["laplace3d", "cheb_xxz", "batch_cfg3"])
+    ap.add_argument("--workload", default="laplace3d", choices=["laplace3d", "cheb_xxz", "batch_cfg3", "serving"])
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="mean Poisson arrival rate (requests/s)")
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="length of the arrival window (s)")
+    ap.add_argument("--serve-rate2", type=float, default=10.0, help="second, sustainable arrival rate")
     ap.add_argument("--batch-count", type=int, default=64, help="matrices of the batch workload")
     ap.add_argument("--batch-nmax", type=float, default=2e6, help="largest matrix size of the batch workload")
     ap.add_argument("--values", default="f64", choices=["f64", "f32", "bf16"],
@@ -493,6 +496,97 @@ def main_batch(args):
         print(json.dumps(line), flush=True)
 
 
+def serving_requests(mats, rate: float, seconds: float, seed: int):
+    """Config 5 stream: Poisson arrivals; matrix family uniform (config 2, 3 or 4), matrix
+    uniform inside it; half MPK with p ~ U{4..16}, half Chebyshev with degree ~ U{16..128};
+    1..8 right-hand sides."""
+    import numpy as np
+    import scipy.special as sp
+    import gen
+    from paper_2405_12525_gb300.serving import Request
+    count = int(rate * seconds * 1.5) + 16
+    gaps = -np.log(gen.uniform(gen.derive_seed(seed), count, 1e-12, 1.0)) / rate
+    t = np.cumsum(gaps)
+    u = gen.uniform(gen.derive_seed(seed + 1), 6 * count, 0.0, 1.0).reshape(count, 6)
+    fams = [[k for k in mats if k.startswith(f)] for f in ("lap", "cfg3", "xxz")]
+    reqs = []
+    for i in range(count):
+        if t[i] > seconds:
+            break
+        fam = fams[min(2, int(u[i, 0] * 3))]
+        name = fam[min(len(fam) - 1, int(u[i, 1] * len(fam)))]
+        nrhs = 1 + min(7, int(u[i, 2] * 8))
+        if u[i, 3] < 0.5:
+            r = Request(i, float(t[i]), name, "mpk", 4 + min(12, int(u[i, 4] * 13)), nrhs)
+        else:
+            deg = 16 + min(112, int(u[i, 4] * 113))
+            r = Request(i, float(t[i]), name, "cheb", deg, nrhs)
+            r.coeffs = sp.jv(np.arange(deg + 1), 0.4 * deg) * np.where(np.arange(deg + 1) > 0, 2.0, 1.0)
+        reqs.append(r)
+    return reqs
+
+
+def main_serving(args):
+    """Config 5: continuous admission of mixed MPK / Chebyshev requests under a 150 GB budget."""
+    import numpy as np
+    import torch
+    import gen
+    import paper_2405_12525_gb300 as mpk
+    from paper_2405_12525_gb300.serving import GpuBackend, Server, request_flops
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    mpk.build()
+    host = {"lap256": gen.laplacian_3d(256, 256, 256), "xxz24": gen.xxz_chain(24, stream=4)}
+    for i, (A, vt, m, p) in enumerate(batch_workload(8, 1e4, 2e6)):
+        host[f"cfg3_{i}_{vt}"] = A
+    mats = {}
+    for name, A in host.items():
+        lo, hi = gen.gershgorin_bounds(A)
+        vt = mpk.MPK_BF16 if name.endswith("bf16") else (mpk.MPK_F32 if name.endswith("f32") else mpk.MPK_F64)
+        mats[name] = (mpk.CsrMatrix.from_host(A, is_symmetric=True, value_type=vt), (hi - lo) / 2 * 1.01,
+                      (hi + lo) / 2)
+    pools = {}  # per matrix and width: one device block of random inputs (shared by requests)
+    for name, A in host.items():
+        base = torch.from_numpy(gen.vector(A.n, 8, stream=900)).cuda()
+        for w in range(1, 9):
+            pools[(name, w)] = base[:, :w].contiguous()
+        del base
+    runs = {}
+    for label, rate, secs, seed in (("config", args.serve_rate, args.serve_seconds, 950),
+                                    ("sustained", args.serve_rate2, max(args.serve_seconds, 10.0), 960)):
+        reqs = serving_requests(mats, rate, secs, seed)
+        for r in reqs:
+            r.x = pools[(r.matrix, r.nrhs)]
+            r.flops = request_flops(host[r.matrix], r)
+        srv = Server(GpuBackend(mats, p_max=16, cheb_block=8, streams=8), hbm_budget=150 * 10 ** 9, max_inflight=8,
+                     keep_results=False)
+        t0 = time.perf_counter()
+        srv.run(reqs)
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+        st.update(rate_rps=rate, window_s=secs, wall_s=wall, rejected=len(srv.rejected))
+        runs[label] = st
+        for r in srv.done:
+            r.result = None
+        del srv
+        torch.cuda.synchronize()
+        torch.cuda.empty_cache()
+    c = runs["config"]
+    line = {
+        "metric": "Serving latency p50/p99 (config 5) on 1 GB300", "value": c["p50_ms"], "unit": "ms",
+        "higher_is_better": False, "n_gpus": world, "steps": c["requests"], "warmup": 0,
+        "ms_per_step": c["mean_ms"], "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "Poisson arrivals of MPK (p 4..16) and Chebyshev (degree 16..128) requests, 1..8 RHS, "
+                               "matrices from the 256^3 Laplacian, 8 config-3 matrices and the XXZ L=24 chain, "
+                               "HBM budget 150 GB, at most 8 requests in flight on 8 streams",
+                   "matrices": {k: [v.n, v.nnz] for k, v in host.items()}},
+        "serving": runs, "p99_ms": c["p99_ms"], "throughput_rps": c["throughput_rps"], "gflops": c["gflops"],
+        "clocks": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.warmup < 3:
@@ -503,6 +597,8 @@ def main():
         return main_cheb(args)
     if args.workload == "batch_cfg3":
         return main_batch(args)
+    if args.workload == "serving":
+        return main_serving(args)
     rank, world, local = dist_env()
     import numpy as np
     import torch
