@@ -65,7 +65,8 @@ def parse():
     ap.add_argument("--p", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="laplace3d", choices=["laplace3d", "cheb_xxz", "batch_cfg3", "serving"])
+    ap.add_argument("--workload", default="laplace3d", choices=["laplace3d", "cheb_xxz", "batch_cfg3", "serving", "dlb"])
+    ap.add_argument("--dlb-parts", type=int, default=4, help="row partitions of the DLB-MPK workload")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="mean Poisson arrival rate (requests/s)")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="length of the arrival window (s)")
     ap.add_argument("--serve-rate2", type=float, default=10.0, help="second, sustainable arrival rate")
@@ -587,6 +588,98 @@ def main_serving(args):
         print(json.dumps(line), flush=True)
 
 
+def main_dlb(args):
+    """DLB-MPK (Alg. 2) with every partition on this device: each step loads x into the local
+    vectors, runs every partition's level-capped launch, the p-1 rounds of halo exchange and
+    per-level row SpMVs, and stores the powers; all of it replayed from one CUDA graph.
+    Compared with TRAD (Alg. 1) on the same partitions and with the unpartitioned kernel."""
+    import numpy as np
+    import torch
+    import paper_2405_12525_gb300 as mpk
+    from paper_2405_12525_gb300.dlb import DlbMpk, mpi_overhead
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    mpk.build()
+    p = args.p
+    A, X = build_workload(args.side)
+    flops = 2.0 * A.nnz * p
+    Xd = torch.from_numpy(X).cuda()
+    t0 = time.perf_counter()
+    D = DlbMpk(A, args.dlb_parts, p)
+    t_setup = time.perf_counter() - t0
+    Y = torch.empty((p + 1, A.n, 1), dtype=torch.float64, device="cuda")
+    Yt = torch.empty_like(Y)
+    stream = torch.cuda.current_stream()
+
+    def graph_of(fn):
+        fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            fn()
+        return g
+
+    def timed(fn, steps, warm):
+        for _ in range(warm):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    D.load(Xd)
+    g_dlb = graph_of(D.run)
+    g_trad = graph_of(D.run_trad)
+    with ClockSampler(local) as clk:
+        ms = timed(g_dlb.replay, args.steps, args.warmup)
+    D.store(Y)
+    ms_trad = timed(g_trad.replay, max(3, args.steps // 2), 2)
+    D.store(Yt)
+    for part in D.parts:
+        part["P"].sync_status()
+    same = bool(torch.equal(Y, Yt))
+    # the same with X and the powers in A's own numbering (scatter into / gather from the
+    # local vectors inside the step)
+    g_glob = graph_of(lambda: D.apply(Xd, Y))
+    ms_glob = timed(g_glob.replay, max(3, args.steps // 2), 2)
+    # phase ii alone (the level-capped launches), for the split of the step
+    ms_ii = timed(lambda: [part["P"].apply(part["Y"][0], p, Y=part["Y"]) for part in D.parts],
+                  max(3, args.steps // 2), 2)
+    # the unpartitioned level-blocked kernel on the same matrix (one launch, plan order)
+    dA = mpk.CsrMatrix.from_host(A, is_symmetric=True)
+    L = mpk.build_levels(dA, 0)
+    P = mpk.plan(dA, L, p_max=p, order=mpk.ORDER_PLAN)
+    Xp = Xd[L.perm.long()].contiguous()
+    ms_one = timed(lambda: P.apply(Xp, p, Y=Yt), max(3, args.steps // 2), 2)
+    n_rows_steps = sum(1 for st in D.steps if st[0] == "rows")
+    launches = 1 + len(D.parts) + (p - 1) + n_rows_steps
+    line = {
+        "metric": "DLB-MPK Gflop/s (FP64) on 1 GB300, partitions emulated on one device", "value": flops / (ms * 1e-3) / 1e9,
+        "unit": "Gflop/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"3-D 7-point Laplacian {args.side}^3, {args.dlb_parts} contiguous row partitions "
+                               f"(nnz-balanced), p_m={p}, nrhs=1; x and the powers resident in the partitions' "
+                               "local vectors (phases i-iii of Alg. 2 per step)",
+                   "n": A.n, "nnz": A.nnz, "parts": args.dlb_parts,
+                   "halo_rows": [int(part["pb"]["nh"]) for part in D.parts],
+                   "local_levels": [int(part["lp"].size - 1) for part in D.parts],
+                   "setup_s": round(t_setup, 2), "l2": "no flush: inputs exceed L2"},
+        "overheads": {"o_dlb_local": D.overhead_local, "o_dlb": D.overhead, "o_mpi": mpi_overhead(D.problems)},
+        "comparator": {"trad_ms": ms_trad, "trad_gflops": flops / (ms_trad * 1e-3) / 1e9,
+                       "speedup_vs_trad": ms_trad / ms, "phase_ii_ms": ms_ii,
+                       "global_numbering_ms": ms_glob,
+                       "unpartitioned_lb_mpk_ms": ms_one, "unpartitioned_gflops": flops / (ms_one * 1e-3) / 1e9,
+                       "bit_identical_dlb_trad": same, "trad_launches_per_step": 2 * p},
+        "clocks": clk.summary(), "gpu_launches": args.steps * launches, "cpu_baseline": None, "e2e": None,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.warmup < 3:
@@ -599,6 +692,8 @@ def main():
         return main_batch(args)
     if args.workload == "serving":
         return main_serving(args)
+    if args.workload == "dlb":
+        return main_dlb(args)
     rank, world, local = dist_env()
     import numpy as np
     import torch

@@ -90,6 +90,12 @@ typedef struct mpk_plan_s mpk_plan_t;     /* opaque, library-owned */
  * ------------------------------------------------------------------------------------- */
 mpk_status mpk_build_levels(const mpk_csr *A, int32_t root, mpk_stream stream, mpk_levels **out);
 
+/* Levels with a set of roots (host array, ascending, distinct) as level 0: level k is the
+ * set of vertices at distance k from the set.  Rooted at a partition's halo rows, level k is
+ * the set I_k of DLB-MPK (Sec. 5): the rows k steps from the boundary. */
+mpk_status mpk_build_levels_from(const mpk_csr *A, const int32_t *roots, int32_t nroots, mpk_stream stream,
+                                 mpk_levels **out);
+
 /* Views into a levels object (device pointers valid until mpk_levels_destroy):
  * level_ptr[num_levels+1] (row offsets of levels in the new order), perm[n], iperm[n],
  * level_of[n].  Any output pointer may be NULL. */
@@ -124,6 +130,12 @@ typedef struct {
     int64_t wait_limit_ns;  /* bound on every device-side wait; 0 = 2 s                     */
     int64_t mem_budget;     /* bytes the plan may allocate on the device; 0 = no limit     */
     int32_t trace;          /* 1: the level-blocked kernel accumulates timing counters      */
+    int32_t level_capped;   /* 1: a row of BFS level L takes powers 1..min(L, p) only, the
+                               local phase of DLB-MPK (Alg. 2) with the levels built from the
+                               halo rows (mpk_build_levels_from); groups are cut at every level
+                               up to p_max; powers above a row's cap are left untouched.
+                               Needs levels and MPK_ORDER_PLAN (else MPK_ERR_INVALID);
+                               mpk_cheb_filter rejects such a plan                           */
 } mpk_plan_opts;
 
 /* Fills the defaults described above (p_max = 8, nrhs = 1, order = ORIGINAL). */
@@ -279,6 +291,35 @@ mpk_status mpk_debug_drop_release(mpk_plan_t *P, int32_t chunk, int32_t k);
 mpk_status mpk_probe_load(const void *buf, int64_t bytes, int32_t reps, int32_t ctas_per_sm,
                           int32_t *sink, mpk_stream stream);
 mpk_status mpk_probe_dfma(int32_t blocks, int32_t iters, double *sink, mpk_stream stream);
+
+/* One SpMV on the plan-order rows [row_begin, row_end): Y[r] = (A X)[r] for those rows only
+ * (X, Y: n x nrhs, plan order, device; other rows of Y untouched).  The per-level steps of
+ * DLB-MPK's third phase (Alg. 2).  Asynchronous on `stream`. */
+mpk_status mpk_spmv_rows(const mpk_plan_t *P, int32_t row_begin, int32_t row_end, const double *X, double *Y,
+                         mpk_stream stream);
+
+/* The row-range SpMV of several plans in one launch: for segment i < count, rows
+ * [row_begin[i], row_end[i]) of Y[i] = A_i X[i] with A_i the matrix of plans[i] (plan order,
+ * n_i x nrhs, device).  The per-level steps of DLB-MPK's third phase (Alg. 2) taken by every
+ * partition at once.  count <= MPK_MAX_ROW_SEGMENTS; the plans of non-empty segments share
+ * one value type and one nrhs (else MPK_ERR_INVALID).  The host arrays are read during the
+ * call only.  Asynchronous on `stream`. */
+#define MPK_MAX_ROW_SEGMENTS 32
+mpk_status mpk_spmv_rows_multi(int32_t count, const mpk_plan_t *const *plans, const int32_t *row_begin,
+                               const int32_t *row_end, const double *const *X, double *const *Y,
+                               mpk_stream stream);
+
+/* dst[dst_idx[t]] = src[src_idx[t]] for t < n, m doubles a row; the index arrays are device
+ * int64 row numbers (the caller keeps them in range and the destinations distinct).  src and
+ * dst may be one buffer when no destination row is also a source row.  The halo exchange of
+ * partitions held on one device.  Asynchronous on `stream`. */
+mpk_status mpk_copy_rows(const double *src, const int64_t *src_idx, double *dst, const int64_t *dst_idx, int64_t n,
+                         int32_t m, mpk_stream stream);
+
+/* dst[r] = src[idx[r]] for r < n, m doubles a row (device arrays): the halo exchange between
+ * partitions held on one device.  Asynchronous on `stream`. */
+mpk_status mpk_gather_rows(const double *src, const int32_t *idx, int32_t n, int32_t m, double *dst,
+                           mpk_stream stream);
 
 /* dst[i] = src[i] widened to float64 for i < n, with the conversion the kernels use (src of
  * mpk_dtype val_type, device memory; MPK_ERR_UNSUPPORTED for another type).  Asynchronous

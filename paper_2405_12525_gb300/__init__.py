@@ -22,6 +22,7 @@ from ._build import build as _build_lib
 
 __all__ = ["build", "load", "CsrMatrix", "Levels", "Plan", "build_levels", "plan", "MpkError",
            "probe_load", "probe_dfma", "device_info", "widen_values", "BatchPlan", "batch_plan",
+           "build_levels_from", "gather_rows", "spmv_rows_multi", "copy_rows",
            "EXPORTED_SYMBOLS"]
 
 MPK_OK, MPK_ERR_INVALID, MPK_ERR_TOO_LARGE, MPK_ERR_OOM, MPK_ERR_TIMEOUT = 0, 1, 2, 3, 4
@@ -35,7 +36,9 @@ EXPORTED_SYMBOLS = [
     "mpk_cheb_filter", "mpk_sync_status", "mpk_probe_load", "mpk_probe_dfma", "mpk_device_info",
     "mpk_status_string", "mpk_last_error", "mpk_debug_drop_release", "mpk_read_trace", "mpk_apply_noalloc",
     "mpk_widen_values", "mpk_batch_plan", "mpk_batch_apply", "mpk_batch_describe", "mpk_batch_workspace",
+    "mpk_build_levels_from", "mpk_spmv_rows", "mpk_gather_rows", "mpk_spmv_rows_multi", "mpk_copy_rows",
 ]
+MAX_ROW_SEGMENTS = 32
 
 
 class MpkError(RuntimeError):
@@ -52,7 +55,7 @@ class _Csr(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("p_max", C.c_int32), ("nrhs", C.c_int32), ("cache_bytes", C.c_int64), ("order", C.c_int32),
                 ("chunk_rows", C.c_int32), ("wait_limit_ns", C.c_int64), ("mem_budget", C.c_int64),
-                ("trace", C.c_int32)]
+                ("trace", C.c_int32), ("level_capped", C.c_int32)]
 
 
 class _Desc(C.Structure):
@@ -105,6 +108,11 @@ def load():
         "mpk_batch_apply": [vp, vp, vp, vp],
         "mpk_batch_describe": [vp, vp, vp, vp],
         "mpk_batch_workspace": [vp, C.POINTER(vp), C.POINTER(i64)],
+        "mpk_build_levels_from": [vp, vp, i32, vp, C.POINTER(vp)],
+        "mpk_spmv_rows": [vp, i32, i32, vp, vp, vp],
+        "mpk_gather_rows": [vp, vp, i32, i32, vp, vp],
+        "mpk_spmv_rows_multi": [i32, vp, vp, vp, vp, vp, vp],
+        "mpk_copy_rows": [vp, vp, vp, vp, i64, i32, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -250,6 +258,49 @@ def _wrap_device_f64(ptr: int, count: int):
     return torch.as_tensor(_DeviceArray(ptr, count, "<f8"), device="cuda")
 
 
+def build_levels_from(A: CsrMatrix, roots, stream=None) -> Levels:
+    """BFS levels with the vertices `roots` (ascending) as level 0."""
+    import numpy as np
+    lib = load()
+    r = np.ascontiguousarray(roots, dtype=np.int32)
+    h = C.c_void_p()
+    csr = A._c()
+    _check(lib.mpk_build_levels_from(C.byref(csr), r.ctypes.data if r.size else None, int(r.size), _stream(stream),
+                                     C.byref(h)))
+    return Levels(h, lib)
+
+
+def gather_rows(src, idx, out, stream=None):
+    """out[r] = src[idx[r]] (rows of m doubles; CUDA tensors, idx int32)."""
+    m = int(src.shape[-1]) if src.dim() > 1 else 1
+    _check(load().mpk_gather_rows(_ptr(src), _ptr(idx), int(idx.numel()), m, _ptr(out), _stream(stream)))
+    return out
+
+
+def spmv_rows_multi(plans, row_begin, row_end, Xs, Ys, stream=None):
+    """Ys[i][r] = (A_i Xs[i])[r] for plan-order rows r in [row_begin[i], row_end[i]), every
+    segment in one launch (plans share value type and nrhs)."""
+    n = len(plans)
+    if not (len(row_begin) == len(row_end) == len(Xs) == len(Ys) == n):
+        raise ValueError("one row range, X and Y per plan")
+    hs = (C.c_void_p * max(n, 1))(*[P._h for P in plans])
+    lo = (C.c_int32 * max(n, 1))(*[int(v) for v in row_begin])
+    hi = (C.c_int32 * max(n, 1))(*[int(v) for v in row_end])
+    xs = (C.c_void_p * max(n, 1))(*[_ptr(X) for X in Xs])
+    ys = (C.c_void_p * max(n, 1))(*[_ptr(Y) for Y in Ys])
+    _check(load().mpk_spmv_rows_multi(n, hs, lo, hi, xs, ys, _stream(stream)))
+
+
+def copy_rows(src, src_idx, dst, dst_idx, stream=None):
+    """dst[dst_idx[t]] = src[src_idx[t]] (rows of m doubles, int64 CUDA index tensors)."""
+    m = int(src.shape[-1]) if src.dim() > 1 else 1
+    if src_idx.numel() != dst_idx.numel():
+        raise ValueError("one destination per source row")
+    _check(load().mpk_copy_rows(_ptr(src), _ptr(src_idx), _ptr(dst), _ptr(dst_idx), int(src_idx.numel()), m,
+                                _stream(stream)))
+    return dst
+
+
 def build_levels(A: CsrMatrix, root: int = 0, stream=None) -> Levels:
     lib = load()
     h = C.c_void_p()
@@ -322,6 +373,11 @@ class Plan:
                                            else None, _stream(stream)))
         return Y
 
+    def spmv_rows(self, row_begin: int, row_end: int, X, Y, stream=None):
+        """Y[r] = (A X)[r] for plan-order rows r in [row_begin, row_end) (other rows untouched)."""
+        _check(self._lib.mpk_spmv_rows(self._h, int(row_begin), int(row_end), _ptr(X), _ptr(Y), _stream(stream)))
+        return Y
+
     def spmv_powers(self, X, p: int, Y=None, stream=None):
         """Comparator: p separate SpMV launches over the same matrix copy."""
         torch = _torch()
@@ -375,13 +431,14 @@ class Plan:
 
 def plan(A: CsrMatrix, levels: Levels | None = None, p_max: int = 8, nrhs: int = 1, cache_bytes: int = 0,
          order: int = ORDER_ORIGINAL, chunk_rows: int = 0, wait_limit_ns: int = 0, mem_budget: int = 0,
-         trace: bool = False, stream=None) -> Plan:
+         trace: bool = False, level_capped: bool = False, stream=None) -> Plan:
     lib = load()
     o = _Opts()
     lib.mpk_plan_opts_default(C.byref(o))
     o.p_max, o.nrhs, o.cache_bytes, o.order = p_max, nrhs, cache_bytes, order
     o.chunk_rows, o.wait_limit_ns, o.mem_budget = chunk_rows, wait_limit_ns, mem_budget
     o.trace = 1 if trace else 0
+    o.level_capped = 1 if level_capped else 0
     h = C.c_void_p()
     csr = A._c()
     _check(lib.mpk_plan(C.byref(csr), levels._h if levels is not None else None, C.byref(o), _stream(stream),

@@ -25,6 +25,19 @@ extern "C" mpk_status mpk_build_levels(const mpk_csr *A, int32_t root, mpk_strea
     MPK_GUARD_END
 }
 
+extern "C" mpk_status mpk_build_levels_from(const mpk_csr *A, const int32_t *roots, int32_t nroots, mpk_stream stream,
+                                         mpk_levels **out) {
+    MPK_GUARD_BEGIN
+    if (!out) fail(MPK_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (nroots < 0 || (nroots > 0 && !roots)) fail(MPK_ERR_INVALID, "bad root list");
+    std::vector<int32_t> r(roots, roots + nroots);
+    Levels *L = build_levels(A, 0, as_stream(stream), &r);
+    *out = new mpk_levels_s{L};
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
 extern "C" mpk_status mpk_levels_get(const mpk_levels *L, int32_t *n, int32_t *num_levels, const int32_t **level_ptr,
                                      const int32_t **perm, const int32_t **iperm, const int32_t **level_of) {
     if (!L || !L->impl) {
@@ -182,6 +195,8 @@ extern "C" mpk_status mpk_apply(const mpk_plan_t *Ph, const double *X, int32_t p
         a.x0 = X;
         a.ybase = Y;
         a.y0copy = (Y != X) ? Y : nullptr;
+        if (a.y0copy && P.level0_rows > 0)  // level 0 of a level-capped plan has no units
+            MPK_CUDA(cudaMemcpyAsync(Y, X, sizeof(double) * (size_t)P.level0_rows * P.m, cudaMemcpyDeviceToDevice, s));
         launch_mpk(P, a, 0, s);
     } else {
         // gather X into plan order, compute every power in plan order in the workspace,
@@ -224,6 +239,7 @@ extern "C" mpk_status mpk_cheb_filter(const mpk_plan_t *Ph, const double *X, int
     if (!Ph || !Ph->impl) fail(MPK_ERR_INVALID, "plan is NULL");
     Plan &P = *const_cast<Plan *>(Ph->impl);
     if (!P.inst_row.empty()) fail(MPK_ERR_INVALID, "a batch plan runs through mpk_batch_apply");
+    if (P.level_capped) fail(MPK_ERR_INVALID, "a level-capped plan computes partial powers only");
     if (degree < 0) fail(MPK_ERR_INVALID, "degree must be >= 0");
     if (!coeff_re) fail(MPK_ERR_INVALID, "coeff_re is NULL");
     if (!(scale != 0.0)) fail(MPK_ERR_INVALID, "scale must be non-zero");
@@ -319,6 +335,68 @@ extern "C" mpk_status mpk_probe_load(const void *buf, int64_t bytes, int32_t rep
 extern "C" mpk_status mpk_probe_dfma(int32_t blocks, int32_t iters, double *sink, mpk_stream stream) {
     MPK_GUARD_BEGIN
     probe_dfma(blocks, iters, sink, as_stream(stream));
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
+extern "C" mpk_status mpk_spmv_rows(const mpk_plan_t *Ph, int32_t row_begin, int32_t row_end, const double *X,
+                                    double *Y, mpk_stream stream) {
+    MPK_GUARD_BEGIN
+    if (!Ph || !Ph->impl) fail(MPK_ERR_INVALID, "plan is NULL");
+    const Plan &P = *Ph->impl;
+    if (row_begin < 0 || row_end > P.n || row_begin > row_end) fail(MPK_ERR_INVALID, "bad row range");
+    if (row_end > row_begin && (!X || !Y)) fail(MPK_ERR_INVALID, "NULL X or Y");
+    const Plan *pp = &P;
+    launch_spmv_rows(&pp, &row_begin, &row_end, &X, &Y, 1, as_stream(stream));
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
+extern "C" mpk_status mpk_spmv_rows_multi(int32_t count, const mpk_plan_t *const *plans, const int32_t *row_begin,
+                                          const int32_t *row_end, const double *const *X, double *const *Y,
+                                          mpk_stream stream) {
+    MPK_GUARD_BEGIN
+    if (count < 0 || count > MPK_MAX_ROW_SEGMENTS) fail(MPK_ERR_INVALID, "count must be in [0, %d]", MPK_MAX_ROW_SEGMENTS);
+    if (count == 0) return MPK_OK;
+    if (!plans || !row_begin || !row_end || !X || !Y) fail(MPK_ERR_INVALID, "NULL argument array");
+    const Plan *pp[MPK_MAX_ROW_SEGMENTS];
+    int vt = -1, m = 0;
+    for (int32_t i = 0; i < count; ++i) {
+        if (!plans[i] || !plans[i]->impl) fail(MPK_ERR_INVALID, "plan %d is NULL", i);
+        const Plan &P = *plans[i]->impl;
+        pp[i] = &P;
+        if (row_begin[i] < 0 || row_end[i] > P.n || row_begin[i] > row_end[i])
+            fail(MPK_ERR_INVALID, "bad row range in segment %d", i);
+        if (row_end[i] == row_begin[i]) continue;
+        if (!X[i] || !Y[i]) fail(MPK_ERR_INVALID, "NULL X or Y in segment %d", i);
+        if (vt < 0) {
+            vt = P.val_type;
+            m = P.m;
+        } else if (vt != P.val_type || m != P.m) {
+            fail(MPK_ERR_INVALID, "segments need one value type and one nrhs");
+        }
+    }
+    launch_spmv_rows(pp, row_begin, row_end, X, Y, count, as_stream(stream));
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
+extern "C" mpk_status mpk_copy_rows(const double *src, const int64_t *src_idx, double *dst, const int64_t *dst_idx,
+                                    int64_t n, int32_t m, mpk_stream stream) {
+    MPK_GUARD_BEGIN
+    if (n < 0 || m < 1) fail(MPK_ERR_INVALID, "bad sizes");
+    if (n > 0 && (!src || !src_idx || !dst || !dst_idx)) fail(MPK_ERR_INVALID, "NULL argument");
+    launch_copy_rows(src, src_idx, dst, dst_idx, n, m, as_stream(stream));
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
+extern "C" mpk_status mpk_gather_rows(const double *src, const int32_t *idx, int32_t n, int32_t m, double *dst,
+                                      mpk_stream stream) {
+    MPK_GUARD_BEGIN
+    if (n < 0 || m < 1) fail(MPK_ERR_INVALID, "bad sizes");
+    if (n > 0 && (!src || !idx || !dst)) fail(MPK_ERR_INVALID, "NULL argument");
+    launch_gather_rows(src, idx, dst, n, m, as_stream(stream));
     return MPK_OK;
     MPK_GUARD_END
 }

@@ -148,6 +148,17 @@ constexpr int kMaxP = 31;
 #define MPK_STAGE_ENTRIES 4096
 #endif
 constexpr int kStageEntries = MPK_STAGE_ENTRIES;
+// 1: chunks whose entries fit a buffer are copied to shared memory by the bulk-copy engine;
+// 0: every unit reads its entries from global memory (L2) directly
+#ifndef MPK_STAGE
+#define MPK_STAGE 1
+#endif
+constexpr bool kStageChunks = MPK_STAGE != 0;
+// entries whose x loads a lane issues together on the global-memory (unstaged) path
+#ifndef MPK_UNSTAGED_BATCH
+#define MPK_UNSTAGED_BATCH 1
+#endif
+constexpr int kUnstagedBatch = MPK_UNSTAGED_BATCH;
 // dependency ranges kept per chunk (exact sets compressed to this many index ranges)
 constexpr int kDepRanges = 4;
 // trace counters accumulated in shared memory (the last one, SM cycles, is added directly)
@@ -239,6 +250,9 @@ struct Plan {
     // batch plans (direct sum of several matrices, mpk_batch_plan): instance i owns rows
     // [inst_row[i], inst_row[i+1]) in both numberings and takes powers 1..inst_p[i]
     std::vector<int32_t> inst_row, inst_p;
+    std::vector<int32_t> h_chunk_row;  // chunk row offsets on the host (num_chunks + 1)
+    bool level_capped = false;        // rows of level L take powers up to min(L, p) (DLB local phase)
+    int32_t level0_rows = 0;          // level-capped plans: rows of level 0 (no unit copies their x)
     int32_t drop_unit = -1;  // armed by mpk_debug_drop_release for the next launch
     unsigned long long *trace = nullptr;  // counters when built with opts.trace
     int grid_mpk[4] = {0, 0, 0, 0};  // persistent grid size per mode
@@ -248,6 +262,28 @@ struct Plan {
 // kernels (mpk_kernel.cu)
 void launch_mpk(const Plan &P, KArgs &a, int mode, cudaStream_t s);
 void launch_spmv(const Plan &P, const double *x, double *y, cudaStream_t s);
+// one SpMV on the plan-order rows [lo, hi) only
+// One launch over row ranges of up to kMaxRowSegs plans (same value type and nrhs).
+constexpr int kMaxRowSegs = 32;
+struct RowSeg {
+    const void *val;
+    const int32_t *col;
+    const int64_t *slice_ptr;
+    const int32_t *chunk_row;
+    const int32_t *chunk_slice;
+    const double *x;
+    double *y;
+    int32_t c0, lo, hi;
+};
+struct RowSegs {
+    int32_t count;
+    int32_t first[kMaxRowSegs + 1];
+    RowSeg seg[kMaxRowSegs];
+};
+void launch_spmv_rows(const Plan *const *plans, const int32_t *lo, const int32_t *hi, const double *const *x,
+                      double *const *y, int count, cudaStream_t s);
+void launch_copy_rows(const double *src, const int64_t *src_idx, double *dst, const int64_t *dst_idx, int64_t n,
+                      int32_t m, cudaStream_t s);
 // Y[k][i] = W[k][iperm[i]] (iperm NULL: W[k][base + i]) for k = 1..p, i < n; W's powers are
 // w_pstride doubles apart (< 0: n * m), Y's n * m
 void launch_scatter_powers(const double *W, const int32_t *iperm, double *Y, int32_t n, int32_t m, int32_t p,
@@ -264,7 +300,8 @@ int occupancy_grid(int mode, int m, bool trace, int vtype);
 void widen_values(int vtype, const void *src, int64_t n, double *dst, cudaStream_t s);
 
 // level builder (mpk_levels.cu)
-Levels *build_levels(const mpk_csr *A, int32_t root, cudaStream_t s);
+// BFS levels from `root`, or from every vertex of `roots` (ascending) as level 0
+Levels *build_levels(const mpk_csr *A, int32_t root, cudaStream_t s, const std::vector<int32_t> *roots = nullptr);
 void validate_csr(const mpk_csr *A, cudaStream_t s);
 
 // planner (mpk_plan.cu)

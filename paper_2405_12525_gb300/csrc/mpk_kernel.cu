@@ -13,6 +13,8 @@
 // bit for bit.
 #include "mpk_internal.h"
 
+#include <algorithm>
+
 namespace mpk {
 
 constexpr int kBS = 32 * (1 + kCompWarps);  // level-blocked kernel: 1 control warp + compute warps
@@ -366,8 +368,9 @@ __device__ __forceinline__ void phase_b(const KArgs &a, int32_t epoch, const Pre
             if (r >= u.row1) continue;
             const int64_t s0 = __ldg(a.slice_ptr + u.slice0 + sl), s1 = __ldg(a.slice_ptr + u.slice0 + sl + 1);
             double w[M];
-            row_sum<M, 1>(GVal<VT>{static_cast<const typename VT::T *>(a.val) + u.ebase}, GCol{a.col + u.ebase}, s0 - u.ebase + lane, (int)((s1 - s0) >> 5),
-                          xin, w);
+            constexpr int BU = kUnstagedBatch < Batch<M>::B ? kUnstagedBatch : Batch<M>::B;
+            row_sum<M, BU>(GVal<VT>{static_cast<const typename VT::T *>(a.val) + u.ebase}, GCol{a.col + u.ebase},
+                           s0 - u.ebase + lane, (int)((s1 - s0) >> 5), xin, w);
             row_epilogue<M, MODE>(a, k, r, w, xin);
             if (k == 1 && a.y0copy) {
 #pragma unroll
@@ -700,30 +703,101 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
 }
 
 // ----------------------------------------------------------------------------- K-SpMV
-// One plain SpMV over the plan's sliced copy: y = A x (plan order), same row body with
-// direct (read-only cached) loads of the entries.  Blocks walk chunks, warps walk the
-// chunk's slices.
+// SpMV restricted to row ranges of one or several plans (plan order), one launch: segment
+// q covers the plan-order rows [lo, hi) of its plan, whose chunks c0 .. c0+nch-1 overlap
+// them; virtual block v belongs to the segment q with first[q] <= v < first[q+1].
 template <int M, class VT>
-__global__ void __launch_bounds__(kSpmvBS) k_spmv(const typename VT::T *__restrict__ val, const int32_t *__restrict__ col,
-                                                  const int64_t *__restrict__ slice_ptr,
-                                                  const int32_t *__restrict__ chunk_row,
-                                                  const int32_t *__restrict__ chunk_slice, int32_t nchunks,
-                                                  const double *x, double *y) {
+__global__ void __launch_bounds__(kSpmvBS) k_spmv_rows(const RowSegs segs) {
     const int lane = threadIdx.x & 31;
-    for (int c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        const int r0 = chunk_row[c], r1 = chunk_row[c + 1], sl0 = chunk_slice[c];
+    for (int v = blockIdx.x; v < segs.first[segs.count]; v += gridDim.x) {
+        int q = 0;
+        while (v >= segs.first[q + 1]) ++q;
+        const RowSeg &g = segs.seg[q];
+        const auto *val = static_cast<const typename VT::T *>(g.val);
+        const int c = g.c0 + (v - segs.first[q]);
+        const int r0 = g.chunk_row[c], r1 = g.chunk_row[c + 1], sl0 = g.chunk_slice[c];
         const int nsl = (r1 - r0 + 31) >> 5;
         for (int sl = threadIdx.x >> 5; sl < nsl; sl += kSpmvBS / 32) {
             const int64_t r = (int64_t)r0 + 32 * sl + lane;
-            if (r < r1) {
-                const int64_t s0 = slice_ptr[sl0 + sl], s1 = slice_ptr[sl0 + sl + 1];
+            if (r < r1 && r >= g.lo && r < g.hi) {
+                const int64_t s0 = g.slice_ptr[sl0 + sl], s1 = g.slice_ptr[sl0 + sl + 1];
                 double w[M];
-                row_sum<M, Batch<M>::B>(GVal<VT>{val}, GCol{col}, s0 + lane, (int)((s1 - s0) >> 5), x, w);
+                row_sum<M, Batch<M>::B>(GVal<VT>{val}, GCol{g.col}, s0 + lane, (int)((s1 - s0) >> 5), g.x, w);
 #pragma unroll
-                for (int i = 0; i < M; ++i) y[r * M + i] = w[i];
+                for (int i = 0; i < M; ++i) g.y[r * M + i] = w[i];
             }
         }
     }
+}
+
+template <class VT>
+static void launch_spmv_rows_vt(const RowSegs &segs, int m, cudaStream_t s) {
+    const int grid = std::min(segs.first[segs.count], 64 * device_sms());
+#define L(MM)                                                 \
+    case MM:                                                  \
+        k_spmv_rows<MM, VT><<<grid, kSpmvBS, 0, s>>>(segs);   \
+        break;
+    switch (m) {
+        L(1) L(2) L(4) L(8) default : fail(MPK_ERR_UNSUPPORTED, "nrhs %d", m);
+    }
+#undef L
+    MPK_LAUNCHED();
+}
+
+void launch_spmv_rows(const Plan *const *plans, const int32_t *lo, const int32_t *hi, const double *const *x,
+                      double *const *y, int count, cudaStream_t s) {
+    RowSegs segs{};
+    segs.first[0] = 0;
+    int vt = -1, m = 0;
+    for (int i = 0; i < count; ++i) {
+        const Plan &P = *plans[i];
+        if (hi[i] <= lo[i]) continue;
+        if (vt < 0) {
+            vt = P.val_type;
+            m = P.m;
+        }
+        // chunks overlapping [lo, hi): h_chunk_row is ascending, from 0 to n
+        const auto &cr = P.h_chunk_row;
+        const int32_t c0 = (int32_t)(std::upper_bound(cr.begin(), cr.end(), lo[i]) - cr.begin()) - 1;
+        const int32_t c1 = (int32_t)(std::lower_bound(cr.begin(), cr.end(), hi[i]) - cr.begin());
+        RowSeg &g = segs.seg[segs.count];
+        g.val = P.val;
+        g.col = P.col;
+        g.slice_ptr = P.slice_ptr;
+        g.chunk_row = P.chunk_row;
+        g.chunk_slice = P.chunk_slice;
+        g.x = x[i];
+        g.y = y[i];
+        g.c0 = c0;
+        g.lo = lo[i];
+        g.hi = hi[i];
+        segs.first[segs.count + 1] = segs.first[segs.count] + (c1 - c0);
+        ++segs.count;
+    }
+    if (segs.count == 0) return;
+    if (vt == MPK_F64) return launch_spmv_rows_vt<ValF64>(segs, m, s);
+    if (vt == MPK_F32) return launch_spmv_rows_vt<ValF32>(segs, m, s);
+    return launch_spmv_rows_vt<ValBF16>(segs, m, s);
+}
+
+// dst[dst_idx[t]] = src[src_idx[t]], m doubles a row (the halo exchange between partitions
+// held on one device)
+__global__ void k_copy_rows(const double *src, const int64_t *src_idx, double *dst, const int64_t *dst_idx, int64_t n,
+                            int32_t m) {
+    const int64_t total = n * m, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += stride) {
+        const int64_t r = t / m, i = t - r * m;
+        dst[dst_idx[r] * m + i] = src[src_idx[r] * m + i];
+    }
+}
+
+void launch_copy_rows(const double *src, const int64_t *src_idx, double *dst, const int64_t *dst_idx, int64_t n,
+                      int32_t m, cudaStream_t s) {
+    if (n <= 0) return;
+    const int64_t total = n * m;
+    const int grid = (int)std::min<int64_t>((total + 255) / 256, 16LL * device_sms());
+    k_copy_rows<<<grid, 256, 0, s>>>(src, src_idx, dst, dst_idx, n, m);
+    MPK_LAUNCHED();
 }
 
 // ----------------------------------------------------------------------------- row moves
@@ -876,26 +950,13 @@ void launch_mpk(const Plan &P, KArgs &a, int mode, cudaStream_t s) {
     MPK_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(kBS), args, mpk_smem_bytes(P.val_type), s));
 }
 
-template <class VT> static void launch_spmv_vt(const Plan &P, const double *x, double *y, cudaStream_t s) {
-    const int grid = P.num_chunks;
-    const auto *val = static_cast<const typename VT::T *>(P.val);
-#define L(MM)                                                                                                 \
-    case MM:                                                                                                  \
-        k_spmv<MM, VT><<<grid, kSpmvBS, 0, s>>>(val, P.col, P.slice_ptr, P.chunk_row, P.chunk_slice, P.num_chunks, \
-                                                x, y);                                                       \
-        break;
-    switch (P.m) {
-        L(1) L(2) L(4) L(8) default : fail(MPK_ERR_UNSUPPORTED, "nrhs %d", P.m);
-    }
-#undef L
-    MPK_LAUNCHED();
-}
-
+// One plain SpMV over the plan's sliced copy, y = A x (plan order): the row-range kernel
+// over all rows.
 void launch_spmv(const Plan &P, const double *x, double *y, cudaStream_t s) {
-    if (P.num_chunks <= 0) return;
-    if (P.val_type == MPK_F64) return launch_spmv_vt<ValF64>(P, x, y, s);
-    if (P.val_type == MPK_F32) return launch_spmv_vt<ValF32>(P, x, y, s);
-    return launch_spmv_vt<ValBF16>(P, x, y, s);
+    if (P.num_chunks <= 0 || P.n <= 0) return;
+    const Plan *pp = &P;
+    const int32_t lo = 0, hi = P.n;
+    launch_spmv_rows(&pp, &lo, &hi, &x, &y, 1, s);
 }
 
 // ----------------------------------------------------------------------------- probes

@@ -99,6 +99,14 @@ __global__ void k_set_root(int32_t *level_of, int32_t *queue_slot, int32_t v, in
     *queue_slot = v;
 }
 
+// level 0 = every root (roots distinct)
+__global__ void k_set_roots(int32_t *level_of, int32_t *queue, const int32_t *roots, int32_t nroots) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nroots; i += gridDim.x * blockDim.x) {
+        level_of[roots[i]] = 0;
+        queue[i] = roots[i];
+    }
+}
+
 __global__ void k_inverse(const uint32_t *perm, int32_t *iperm, int32_t *perm_out, int64_t n) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
@@ -126,10 +134,17 @@ static int grid_n(int64_t n) {
     return (int)(g < 1 ? 1 : g);
 }
 
-Levels *build_levels(const mpk_csr *A, int32_t root, cudaStream_t s) {
+Levels *build_levels(const mpk_csr *A, int32_t root, cudaStream_t s, const std::vector<int32_t> *roots) {
     validate_csr(A, s);
     const int32_t n = A->n;
-    if (n > 0 && (root < 0 || root >= n)) fail(MPK_ERR_INVALID, "root %d outside [0, %d)", root, n);
+    if (roots) {  // level 0 is the whole root set: a BFS distance from the set
+        if (n > 0 && roots->empty()) fail(MPK_ERR_INVALID, "empty root set");
+        for (size_t i = 0; i < roots->size(); ++i)
+            if ((*roots)[i] < 0 || (*roots)[i] >= n || (i > 0 && (*roots)[i] <= (*roots)[i - 1]))
+                fail(MPK_ERR_INVALID, "roots must be ascending, distinct and in [0, %d)", n);
+    } else if (n > 0 && (root < 0 || root >= n)) {
+        fail(MPK_ERR_INVALID, "root %d outside [0, %d)", root, n);
+    }
     Levels *L = new Levels();
     try {
         L->n = n;
@@ -167,9 +182,19 @@ Levels *build_levels(const mpk_csr *A, int32_t root, cudaStream_t s) {
             ~HostFree() { cudaFreeHost(p); }
         } hf{h};
         MPK_CUDA(cudaMemsetAsync(L->level_of, 0xff, sizeof(int32_t) * (size_t)n, s));
-        k_set_root<<<1, 1, 0, s>>>(L->level_of, queue.p, root, 0);
-        MPK_LAUNCHED();
         int64_t head = 0, tail = 1, cursor = 0;
+        if (roots) {
+            const int32_t nr = (int32_t)roots->size();
+            Tmp<int32_t> d_roots(nr);
+            MPK_CUDA(cudaMemcpyAsync(d_roots.p, roots->data(), sizeof(int32_t) * (size_t)nr, cudaMemcpyHostToDevice, s));
+            k_set_roots<<<grid_n(nr), 256, 0, s>>>(L->level_of, queue.p, d_roots.p, nr);
+            MPK_LAUNCHED();
+            MPK_CUDA(cudaStreamSynchronize(s));  // the host root list and d_roots go out of scope
+            tail = nr;
+        } else {
+            k_set_root<<<1, 1, 0, s>>>(L->level_of, queue.p, root, 0);
+            MPK_LAUNCHED();
+        }
         int32_t lev = 0;
         while (true) {
             if (tail > head) {

@@ -99,6 +99,9 @@ extern "C" mpk_status mpk_apply_noalloc(const mpk_plan_t *Ph, const double *X, i
             a.ystride = (int64_t)P.n * P.m;
             a.ring = p + 1;
             a.y0copy = (Y != X) ? Y : nullptr;
+            if (a.y0copy && P.level0_rows > 0)  // level 0 of a level-capped plan has no units
+                MPK_CUDA(cudaMemcpyAsync(Y, X, sizeof(double) * (size_t)P.level0_rows * P.m,
+                                         cudaMemcpyDeviceToDevice, s));
             launch_mpk(P, a, 0, s);
         }
         if (status) {

@@ -177,7 +177,7 @@ __global__ void k_chunk_records(int32_t nchunks, const int32_t *chunk_row, const
         const int32_t sl0 = chunk_slice[c], sl1 = chunk_slice[c + 1], nsl = sl1 - sl0;
         const int64_t e0 = slice_ptr[sl0], e1 = slice_ptr[sl1];
         const int32_t cnt = (int32_t)(e1 - e0);
-        const int staged = cnt > 0 && cnt <= kStageEntries && nsl <= kRecSlices;
+        const int staged = kStageChunks && cnt > 0 && cnt <= kStageEntries && nsl <= kRecSlices;
         int32_t *o = rec + (int64_t)kRecInts * c;
         o[0] = chunk_row[c];
         o[1] = chunk_row[c + 1];
@@ -289,6 +289,9 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         P->wait_ns = o->wait_limit_ns ? o->wait_limit_ns : 2000000000LL;
         P->num_levels = L ? L->num_levels : 0;
         const bool batch = inst_row != nullptr;
+        P->level_capped = o->level_capped != 0;
+        if (P->level_capped && (!L || batch || o->order != MPK_ORDER_PLAN))
+            fail(MPK_ERR_INVALID, "level_capped needs levels, plan order and no batch");
         if (batch) {
             if (!L || !inst_p || inst_row->size() != inst_p->size() + 1 || inst_row->back() != n)
                 fail(MPK_ERR_INVALID, "inconsistent batch description");
@@ -350,7 +353,9 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
                 const int64_t rows = lp[l + 1] - lp[l];
                 const int64_t nz = (int64_t)h_nz[l + 1] - h_nz[l];
                 const int64_t b = (vb + 4) * nz + 4 * rows + 16 * (int64_t)m * rows;
-                if (l > 0 && !inst_start[l] && cur + b <= Bl) {
+                // level-capped plans: every level below p_max is a group of its own
+                const bool cut = P->level_capped && l <= pmax;
+                if (l > 0 && !inst_start[l] && !cut && cur + b <= Bl) {
                     cur += b;
                 } else {
                     if (l > 0) g_level.push_back(l);
@@ -358,6 +363,7 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
                 }
             }
             g_level.push_back(NL);
+            if (P->level_capped && NL > 0) P->level0_rows = lp[1];
             for (int32_t gl : g_level) g_row.push_back(lp[gl]);
         } else {
             g_row = {0, 0};
@@ -411,6 +417,7 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         }
         g_chunk.push_back((int32_t)c_row.size() - 1);
         const int32_t NC = (int32_t)c_row.size() - 1;
+        P->h_chunk_row = c_row;
         if (NC >= (1 << 26)) fail(MPK_ERR_TOO_LARGE, "too many chunks (%d)", NC);
         P->num_chunks = NC;
         P->chunk_row = P->arena.alloc_n<int32_t>(NC + 1);
@@ -529,12 +536,17 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
                     }
             P->unit_off[pmax + 1] = (int64_t)units.size();  // the table of p = p_max is the batch table
         }
+        // level-capped plans: group g (a single level below p_max, or levels >= p_max) takes
+        // powers up to its first level
+        std::vector<int32_t> g_cap((size_t)G, pmax);
+        if (P->level_capped)
+            for (int32_t g = 0; g < G; ++g) g_cap[g] = std::min(pmax, g_level[g]);
         for (int32_t p = 1; p <= pmax && !batch; ++p) {
             P->unit_off[p] = (int64_t)units.size();
             for (int32_t d = kSlotSkew; d <= G - 1 + kSlotSkew * p; ++d)
                 for (int32_t k = 1; k <= p; ++k) {
                     const int32_t g = d - kSlotSkew * k;
-                    if (g < 0 || g >= G) continue;
+                    if (g < 0 || g >= G || k > g_cap[g]) continue;
                     for (int32_t c = g_chunk[g]; c < g_chunk[g + 1]; ++c) units.push_back((c << 5) | k);
                 }
         }
