@@ -766,6 +766,31 @@ def main():
     ms_plain_nat = timed(lambda: P0.spmv_powers(Xd, p, Y=Y2), max(3, args.steps // 4), 2)
     ms_plain_bfs = timed(lambda: P.spmv_powers(Xp, p, Y=Y2), max(3, args.steps // 4), 2)
     identical = bool(torch.equal(Y, Y2))   # level-blocked == back-to-back SpMV, bit for bit
+    # ---- comparator: plain p x CSR SpMV of the vendor library (cuSPARSE through torch's sparse
+    #      CSR matmul), natural order, on the unpermuted CSR arrays
+    csr = None
+    try:
+        import warnings
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore")
+            Acsr = torch.sparse_csr_tensor(torch.as_tensor(A.row_ptr).cuda(), torch.as_tensor(A.col).cuda(),
+                                           torch.as_tensor(A.val, dtype=torch.float64).cuda(), size=(A.n, A.n))
+
+            def csr_powers():
+                v = Xd
+                for _ in range(p):
+                    v = Acsr @ v
+                return v
+
+            ms_csr = timed(csr_powers, max(3, args.steps // 4), 2)
+            v = csr_powers()
+            rel = float(torch.linalg.norm(v[:, 0] - Y2[p, :, 0].index_select(0, L.iperm.long())) /
+                        torch.linalg.norm(v[:, 0]))
+            csr = {"ms": ms_csr, "gflops": flops / (ms_csr * 1e-3) / 1e9, "speedup": ms_csr / ms,
+                   "rel_diff_power_p": rel, "library": "cuSPARSE (torch sparse CSR matmul)"}
+            del Acsr, v
+    except Exception as e:  # the comparator is optional; the headline does not depend on it
+        csr = {"unavailable": f"{type(e).__name__}: {e}"}
 
     # ---- end to end through the C ABI with host buffers (pinned), plan-order vectors
     e2e = None
@@ -819,7 +844,9 @@ def main():
                            "speedup_vs_best_plain": best_plain / ms,
                            "speedup_original_order_vs_best_plain": best_plain / ms_orig,
                            "plain_hbm_gbs": p * (a_bytes + 2 * v_bytes) / (best_plain * 1e-3) / 1e9,
-                           "bit_identical_to_plain": identical},
+                           "bit_identical_to_plain": identical,
+                           "plain_spmv_note": "plain_* use this library's sliced (SELL-32) copy, grid-stride kernel",
+                           "vendor_csr": csr},
             "preprocess": {"levels_ms": t_levels * 1e3, "plan_ms": t_plan * 1e3,
                            "spmv_equivalents": (t_levels + t_plan) * 1e3 / (best_plain / p)},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,

@@ -124,9 +124,9 @@ void mpk_levels_destroy(mpk_levels *L);
 typedef struct {
     int32_t p_max;          /* largest power mpk_apply may request (1..31)                 */
     int32_t nrhs;           /* m: 1, 2, 4 or 8 right-hand sides per call                    */
-    int64_t cache_bytes;    /* C in bytes; 0 = half of the device L2                       */
+    int64_t cache_bytes;    /* C in bytes; 0 = the device L2 size                          */
     int32_t order;          /* mpk_order of X, Y and the Chebyshev input/output             */
-    int32_t chunk_rows;     /* rows per work unit (multiple of 32); 0 = 480                 */
+    int32_t chunk_rows;     /* rows per work unit (multiple of 32); 0 = 416 (13 slices)     */
     int64_t wait_limit_ns;  /* bound on every device-side wait; 0 = 2 s                     */
     int64_t mem_budget;     /* bytes the plan may allocate on the device; 0 = no limit     */
     int32_t trace;          /* 1: the level-blocked kernel accumulates timing counters      */
@@ -136,7 +136,19 @@ typedef struct {
                                up to p_max; powers above a row's cap are left untouched.
                                Needs levels and MPK_ORDER_PLAN (else MPK_ERR_INVALID);
                                mpk_cheb_filter rejects such a plan                           */
+    int32_t engine;         /* MPK_ENGINE_STAGED (0, default) or MPK_ENGINE_WARP (1), below  */
 } mpk_plan_opts;
+
+/* Engines of the level-blocked kernel (same results bit for bit, same Lp-diagram order):
+ *  MPK_ENGINE_STAGED  blocks of one control warp and compute warps; the control warp claims
+ *                     chunk units, copies their entries to shared memory with bulk copies and
+ *                     polls chunk-level dependency flags.
+ *  MPK_ENGINE_WARP    every warp claims items of kWarpSlices 32-row slices on its own, reads
+ *                     the entries from global memory (L2) and waits for whole cells (group,
+ *                     power k-1) of the three neighbouring groups; no shared memory, full
+ *                     occupancy.  Not for batch plans (MPK_ERR_INVALID); mpk_apply_noalloc
+ *                     runs such a plan with the staged engine. */
+enum { MPK_ENGINE_STAGED = 0, MPK_ENGINE_WARP = 1 };
 
 /* Fills the defaults described above (p_max = 8, nrhs = 1, order = ORIGINAL). */
 void mpk_plan_opts_default(mpk_plan_opts *o);

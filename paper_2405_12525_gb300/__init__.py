@@ -29,6 +29,7 @@ MPK_OK, MPK_ERR_INVALID, MPK_ERR_TOO_LARGE, MPK_ERR_OOM, MPK_ERR_TIMEOUT = 0, 1,
 MPK_ERR_CUDA, MPK_ERR_BUDGET, MPK_ERR_UNSUPPORTED = 5, 6, 7
 MPK_F64, MPK_F32, MPK_BF16 = 0, 1, 2
 ORDER_ORIGINAL, ORDER_PLAN = 0, 1
+ENGINE_STAGED, ENGINE_WARP = 0, 1
 
 EXPORTED_SYMBOLS = [
     "mpk_build_levels", "mpk_levels_get", "mpk_levels_destroy", "mpk_plan_opts_default", "mpk_plan",
@@ -55,7 +56,7 @@ class _Csr(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("p_max", C.c_int32), ("nrhs", C.c_int32), ("cache_bytes", C.c_int64), ("order", C.c_int32),
                 ("chunk_rows", C.c_int32), ("wait_limit_ns", C.c_int64), ("mem_budget", C.c_int64),
-                ("trace", C.c_int32), ("level_capped", C.c_int32)]
+                ("trace", C.c_int32), ("level_capped", C.c_int32), ("engine", C.c_int32)]
 
 
 class _Desc(C.Structure):
@@ -431,7 +432,7 @@ class Plan:
 
 def plan(A: CsrMatrix, levels: Levels | None = None, p_max: int = 8, nrhs: int = 1, cache_bytes: int = 0,
          order: int = ORDER_ORIGINAL, chunk_rows: int = 0, wait_limit_ns: int = 0, mem_budget: int = 0,
-         trace: bool = False, level_capped: bool = False, stream=None) -> Plan:
+         trace: bool = False, level_capped: bool = False, engine: int = ENGINE_STAGED, stream=None) -> Plan:
     lib = load()
     o = _Opts()
     lib.mpk_plan_opts_default(C.byref(o))
@@ -439,6 +440,7 @@ def plan(A: CsrMatrix, levels: Levels | None = None, p_max: int = 8, nrhs: int =
     o.chunk_rows, o.wait_limit_ns, o.mem_budget = chunk_rows, wait_limit_ns, mem_budget
     o.trace = 1 if trace else 0
     o.level_capped = 1 if level_capped else 0
+    o.engine = int(engine)
     h = C.c_void_p()
     csr = A._c()
     _check(lib.mpk_plan(C.byref(csr), levels._h if levels is not None else None, C.byref(o), _stream(stream),

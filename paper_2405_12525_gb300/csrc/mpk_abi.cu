@@ -166,6 +166,19 @@ KArgs mpk::base_args(Plan &P, int32_t p) {
     a.trace = P.trace;
     P.drop_unit = -1;
     a.ystride = (int64_t)P.n * P.m;
+    if (P.engine == MPK_ENGINE_WARP) {
+        a.w_item = P.w_item + P.w_cell_off[p];
+        a.w_gk = P.w_gk + P.w_cell_off[p];
+        a.w_ncells = P.w_cell_off[p + 1] - P.w_cell_off[p];
+        a.w_nitems = P.w_items[p];
+        a.w_cnt = P.w_cnt;
+        a.w_q = reinterpret_cast<unsigned int *>(P.w_cnt + (int64_t)(P.p_max + 1) * std::max(P.num_chunks, 1));
+        a.g_row = P.group_row_ptr;
+        a.g_slice = P.g_slice;
+        a.w_slice_chunk = P.w_slice_chunk;
+        a.w_chunk_nsl = P.w_chunk_nsl;
+        a.ngroups = P.num_groups;
+    }
     return a;
 }
 

@@ -145,7 +145,7 @@ struct Levels {
 constexpr int kMaxP = 31;
 // padded entries of one chunk that the kernel stages in shared memory (per buffer)
 #ifndef MPK_STAGE_ENTRIES
-#define MPK_STAGE_ENTRIES 4096
+#define MPK_STAGE_ENTRIES 3072
 #endif
 constexpr int kStageEntries = MPK_STAGE_ENTRIES;
 // 1: chunks whose entries fit a buffer are copied to shared memory by the bulk-copy engine;
@@ -165,7 +165,7 @@ constexpr int kDepRanges = 4;
 constexpr int kTraceShared = MPK_TRACE_COUNTERS - 1;
 // compute warps of the level-blocked kernel; the default chunk is one 32-row slice per warp
 #ifndef MPK_COMP_WARPS
-#define MPK_COMP_WARPS 15
+#define MPK_COMP_WARPS 13
 #endif
 constexpr int kCompWarps = MPK_COMP_WARPS;
 constexpr int kDefaultChunkRows = 32 * kCompWarps;
@@ -216,7 +216,24 @@ struct KArgs {
     int32_t complex_coeff;
     double cre[kMaxP + 1];
     double cim[kMaxP + 1];
+    // warp-ticketed engine (MPK_ENGINE_WARP): the cells (group g, power k) of this launch in
+    // ticket order, each split into items of kWarpSlices slices, and per-cell counters of
+    // finished items
+    const int64_t *w_item;   // first item of each cell (strictly ascending), w_ncells entries
+    const int32_t *w_gk;     // g << 5 | k of each cell
+    int64_t w_ncells;
+    int64_t w_nitems;
+    int32_t *w_cnt;          // (p+1) x nchunks finished slices per (power, chunk); zero at launch start
+    unsigned int *w_q;       // kWarpQueues claim counters; zero when the launch starts
+    const int32_t *g_row;    // G+1 group row offsets
+    const int32_t *g_slice;  // G+1 group slice offsets
+    const int32_t *w_slice_chunk;  // chunk of every slice
+    const int32_t *w_chunk_nsl;    // slices of every chunk
+    int32_t ngroups;
 };
+// warp-ticketed engine: slices per item, claim queues (one per warp of a block)
+constexpr int kWarpSlices = 1;
+constexpr int kWarpQueues = 16;
 
 struct Plan {
     int32_t n = 0, nnz = 0, m = 1, p_max = 8, order = MPK_ORDER_ORIGINAL;
@@ -253,6 +270,16 @@ struct Plan {
     std::vector<int32_t> h_chunk_row;  // chunk row offsets on the host (num_chunks + 1)
     bool level_capped = false;        // rows of level L take powers up to min(L, p) (DLB local phase)
     int32_t level0_rows = 0;          // level-capped plans: rows of level 0 (no unit copies their x)
+    // warp-ticketed engine (plans built with engine = MPK_ENGINE_WARP)
+    int32_t engine = MPK_ENGINE_STAGED;
+    int32_t *g_slice = nullptr;         // G+1 group slice offsets (device)
+    int64_t *w_item = nullptr;          // cells of every p, concatenated (device)
+    int32_t *w_gk = nullptr;
+    std::vector<int64_t> w_cell_off;    // p_max + 2: the cells of p start at w_cell_off[p]
+    std::vector<int64_t> w_items;       // p_max + 1: items of a launch with p powers
+    int32_t *w_cnt = nullptr;           // (p_max+1) x nchunks counters, then kWarpQueues claim counters
+    int32_t *w_slice_chunk = nullptr;   // chunk of every slice (device)
+    int32_t *w_chunk_nsl = nullptr;     // slices of every chunk (device)
     int32_t drop_unit = -1;  // armed by mpk_debug_drop_release for the next launch
     unsigned long long *trace = nullptr;  // counters when built with opts.trace
     int grid_mpk[4] = {0, 0, 0, 0};  // persistent grid size per mode

@@ -18,12 +18,30 @@
 namespace mpk {
 
 constexpr int kBS = 32 * (1 + kCompWarps);  // level-blocked kernel: 1 control warp + compute warps
-constexpr int kBlocksPerSM = 1024 / kBS;     // register budget: 64 per thread at 2048 threads per SM
+// blocks per SM the register budget is set for (65536 registers per SM): three blocks of
+// 14 warps (40 registers a thread), whose 2 x 3072-entry slots (72 KB) fit three times in
+// an SM's shared memory
+#ifndef MPK_MIN_BLOCKS
+#define MPK_MIN_BLOCKS 3
+#endif
+// (the single-vector power kernel; wider blocks, the Chebyshev recurrence and the traced
+// kernel keep 64 registers a thread at two blocks)
+template <int M, int MODE, bool TRACE> struct MpkOcc {
+    static constexpr int blocks = (M == 1 && MODE == 0 && !TRACE) ? MPK_MIN_BLOCKS : 2;
+};
 constexpr int kSpmvBS = 256;        // threads per block of the plain SpMV kernel
 // Staging slots: the control warp fills one while the compute warps work on the other.
 constexpr int kSlots = 2;
+// column indices of staged chunks: copied to shared memory beside the values (1), or read
+// from global memory (L2) by the compute warps (0), which halves the slot size for FP64
+#ifndef MPK_STAGE_COL
+#define MPK_STAGE_COL 1
+#endif
+constexpr bool kStageCol = MPK_STAGE_COL != 0;
 // one slot: kStageEntries values of the matrix's value type, then as many column indices
-template <class VT> constexpr int smem_bytes() { return kSlots * kStageEntries * (int)(sizeof(typename VT::T) + 4); }
+template <class VT> constexpr int smem_bytes() {
+    return kSlots * kStageEntries * (int)(sizeof(typename VT::T) + (kStageCol ? 4 : 0));
+}
 
 enum Mode { MODE_POWERS = 0, MODE_CHEB = 1 };
 
@@ -327,7 +345,7 @@ __device__ __forceinline__ void phase_b(const KArgs &a, int32_t epoch, const Pre
     const int k = pf.unit & 31;
     const double *xin = input_block<M>(a, k);
     const SVal<VT> sval{sval0 + pf.slot * kStageEntries};
-    const int32_t *scol = scol0 + pf.slot * kStageEntries;
+    const int32_t *scol = kStageCol ? scol0 + pf.slot * kStageEntries : a.col + u.ebase;
     if (u.staged) {
         if (pf.r >= 0) {  // first slice: prefetched first batch, then the rest of the row
             double w[M];
@@ -438,7 +456,7 @@ __device__ __forceinline__ int dep_ranges_of(int rec, int (&lo)[kDepRanges], int
 }
 
 template <int M, int MODE, bool TRACE, class VT>
-__global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
+__global__ void __launch_bounds__(kBS, (MpkOcc<M, MODE, TRACE>::blocks)) k_mpk(const KArgs a) {
     using T = typename VT::T;
     const bool tr = TRACE && a.trace != nullptr;  // timing counters (instantiated separately)
     extern __shared__ __align__(128) unsigned char smem[];
@@ -549,10 +567,11 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
                 s_u[b] = u;
                 if (u.staged) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    mbar_expect_tx_only(&s_full[b], (uint32_t)u.ecount * (uint32_t)(sizeof(T) + 4));
+                    mbar_expect_tx_only(&s_full[b], (uint32_t)u.ecount * (uint32_t)(sizeof(T) + (kStageCol ? 4 : 0)));
                     bulk_g2s(sval0 + b * kStageEntries, static_cast<const T *>(a.val) + u.ebase,
                              (uint32_t)(u.ecount * sizeof(T)), &s_full[b]);
-                    bulk_g2s(scol0 + b * kStageEntries, a.col + u.ebase, (uint32_t)u.ecount * 4u, &s_full[b]);
+                    if (kStageCol)
+                        bulk_g2s(scol0 + b * kStageEntries, a.col + u.ebase, (uint32_t)u.ecount * 4u, &s_full[b]);
                 }
             }
             if (tr && lane == 0) tr_add(8, clock64() - c2);
@@ -660,7 +679,7 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
             }
             {
                 const long long c0 = tr ? clock64() : 0;
-                phase_a<M>(a, s_u[b], b, scol0 + b * kStageEntries, cw, lane, pf);
+                phase_a<M>(a, s_u[b], b, kStageCol ? scol0 + b * kStageEntries : a.col + s_u[b].ebase, cw, lane, pf);
                 if (tr) {  // wait for the gathers (integer ops only) to split the unit time
                     int h = 0;
 #pragma unroll
@@ -695,6 +714,136 @@ __global__ void __launch_bounds__(kBS, kBlocksPerSM) k_mpk(const KArgs a) {
         const unsigned int done = atomicAdd(a.exit_count, 1u);
         if (done == gridDim.x - 1) {
             *a.ticket = 0u;
+            *a.exit_count = 0u;
+            *a.epoch_word = (unsigned int)epoch;
+            __threadfence();
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------- K-MPK, warp engine
+// The same cells (group g, local power k) in the same order as k_mpk (lines g + kSlotSkew*k
+// ascending, k ascending inside a line), split into items of kWarpSlices 32-row slices and
+// numbered in that order.  Every warp works alone: warp q of each block claims the items
+// q, q + Q, q + 2Q, ... (Q = kWarpQueues) through the claim counter of queue q, so that any
+// resident block serves every queue; it waits until the cells (g-1, k-1), (g, k-1) and
+// (g+1, k-1) have all their items finished (acquire), computes its slices with the entries
+// read from global memory (L2, where the line order keeps the working set), and adds one
+// to its cell's counter (release).
+// No deadlock: take the smallest claimed, unfinished item m.  Each of its dependencies x < m
+// is finished: a claimed x would be held by a warp with an unfinished item below m, and an
+// unclaimed x of queue q would lie above every item claimed from q, although the queue-q warp
+// of m's block holds an unfinished item of q, which is at least m.  Claims run one item
+// ahead; the argument holds for the items being computed.  Every wait is bounded by
+// a.wait_ns; on expiry the warp records the epoch and MPK_ERR_TIMEOUT in a.err and leaves,
+// and the others leave when they see the error.
+// blocks of kWarpBS threads per SM the register budget is set for (no spills)
+template <int M, int MODE, class VT> struct WarpOcc {
+    static constexpr bool f64 = sizeof(typename VT::T) == 8;
+    static constexpr int blocks = !f64 || M > 2 ? 2 : (M == 1 && MODE == 0 ? 4 : 3);
+};
+constexpr int kWarpBS = 32 * kWarpQueues;
+
+template <int M, int MODE, class VT>
+__global__ void __launch_bounds__(kWarpBS, (WarpOcc<M, MODE, VT>::blocks)) k_mpkw(const KArgs a) {
+    constexpr int B = Batch<M>::B;
+    const int lane = threadIdx.x & 31, q = threadIdx.x >> 5;
+    __shared__ int32_t s_epoch;
+    if (threadIdx.x == 0) s_epoch = ld_relaxed(reinterpret_cast<const int32_t *>(a.epoch_word)) + 1;
+    __syncthreads();
+    const int32_t epoch = s_epoch;
+    const auto *val = static_cast<const typename VT::T *>(a.val);
+    // lane 0 holds the pending claims (queue positions) of the current and the next item
+    unsigned int c_now = 0, c_next = 0;
+    if (lane == 0) {
+        c_now = atomicAdd(a.w_q + q, 1u);
+        c_next = atomicAdd(a.w_q + q, 1u);
+    }
+    int64_t cell = 0;
+    bool failed = false;
+    for (;;) {
+        const int64_t it = (int64_t)__shfl_sync(0xffffffffu, c_now, 0) * kWarpQueues + q;
+        if (it >= a.w_nitems) break;
+        // the item's cell: the last one whose first item is <= it (the warp's items ascend)
+        for (;;) {
+            const int64_t cc = cell + 1 + lane;
+            const bool le = cc < a.w_ncells && __ldg(a.w_item + cc) <= it;
+            const unsigned int bal = __ballot_sync(0xffffffffu, le);
+            cell += __popc(bal);
+            if (bal != 0xffffffffu) break;
+        }
+        const int gk = __ldg(a.w_gk + cell);
+        const int g = gk >> 5, k = gk & 31;
+        const int j = (int)(it - __ldg(a.w_item + cell));
+        const int gs0 = __ldg(a.g_slice + g), gs1 = __ldg(a.g_slice + g + 1);
+        const int gr0 = __ldg(a.g_row + g), gr1 = __ldg(a.g_row + g + 1);
+        const int s_first = gs0 + j * kWarpSlices, s_end = min(s_first + kWarpSlices, gs1);
+        const int c = __ldg(a.w_slice_chunk + s_first);  // items never leave a chunk (one slice)
+        if (k > 1) {
+            // the chunks this chunk's rows read (its dependency ranges) must have all their
+            // slices finished at power k-1
+            const int rv = lane < kRecInts ? __ldg(reinterpret_cast<const int32_t *>(a.chunk_rec) +
+                                                   (int64_t)kRecInts * c + lane)
+                                           : 0;
+            int dlo[kDepRanges], dlen[kDepRanges];
+            const int total = dep_ranges_of(rv, dlo, dlen);
+            const int32_t *cnt = a.w_cnt + (int64_t)(k - 1) * a.nchunks;
+            const uint64_t t0 = globaltimer();
+            for (int v0 = 0; v0 < total && !failed; v0 += 32) {
+                int v = v0 + lane, idx = -1;
+                if (v < total) {
+#pragma unroll
+                    for (int r = 0; r < kDepRanges; ++r) {
+                        if (idx < 0 && v < dlen[r]) idx = dlo[r] + v;
+                        if (idx < 0) v -= dlen[r];
+                    }
+                }
+                const int ns = idx >= 0 ? __ldg(a.w_chunk_nsl + idx) : 0;
+                const int need = (ns >> 24) >= k - 1 ? (ns & 0xffffff) : 0;
+                for (;;) {
+                    const bool ok = idx < 0 || ld_relaxed(cnt + idx) >= need;
+                    if (__all_sync(0xffffffffu, ok)) break;
+                    const bool stop = ld_relaxed(a.err) == epoch || timed_out(t0, a.wait_ns);
+                    if (__any_sync(0xffffffffu, stop)) {
+                        failed = true;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+            }
+            if (failed) break;
+            fence_acq_rel_gpu();  // acquire: the neighbours' rows before this warp's reads
+            __syncwarp();
+        }
+        const double *xin = input_block<M>(a, k);
+        for (int sl = s_first; sl < s_end; ++sl) {
+            const int64_t r = (int64_t)gr0 + 32 * (sl - gs0) + lane;
+            if (r < gr1) {
+                const int64_t e0 = __ldg(a.slice_ptr + sl), e1 = __ldg(a.slice_ptr + sl + 1);
+                double w[M];
+                row_sum<M, B>(GVal<VT>{val}, GCol{a.col}, e0 + lane, (int)((e1 - e0) >> 5), xin, w);
+                row_epilogue<M, MODE>(a, k, r, w, xin);
+                if (k == 1 && a.y0copy) {
+#pragma unroll
+                    for (int i = 0; i < M; ++i) a.y0copy[r * M + i] = a.x0[r * M + i];
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            fence_acq_rel_gpu();  // release: this warp's rows before the count
+            atomicAdd(a.w_cnt + (int64_t)k * a.nchunks + c, 1);
+        }
+        c_now = c_next;
+        if (lane == 0) c_next = atomicAdd(a.w_q + q, 1u);
+    }
+    if (failed && lane == 0 && atomicExch(a.err, epoch) != epoch) st_relaxed(a.err + 1, (int)MPK_ERR_TIMEOUT);
+    // ---- exit: the last block stores the epoch for the next launch
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        const unsigned int done = atomicAdd(a.exit_count, 1u);
+        if (done == gridDim.x - 1) {
             *a.exit_count = 0u;
             *a.epoch_word = (unsigned int)epoch;
             __threadfence();
@@ -940,7 +1089,46 @@ int occupancy_grid(int mode, int m, bool trace, int vtype) {
     return c;
 }
 
+template <class VT> static void *select_mpkw_vt(int mode, int m) {
+#define SEL(MM)                                                                              \
+    if (m == MM) return mode == MODE_POWERS ? (void *)k_mpkw<MM, MODE_POWERS, VT> : (void *)k_mpkw<MM, MODE_CHEB, VT>;
+    SEL(1) SEL(2) SEL(4) SEL(8)
+#undef SEL
+    fail(MPK_ERR_UNSUPPORTED, "nrhs %d", m);
+}
+
+static void *select_mpkw(int mode, int m, int vtype) {
+    if (vtype == MPK_F64) return select_mpkw_vt<ValF64>(mode, m);
+    if (vtype == MPK_F32) return select_mpkw_vt<ValF32>(mode, m);
+    if (vtype == MPK_BF16) return select_mpkw_vt<ValBF16>(mode, m);
+    fail(MPK_ERR_UNSUPPORTED, "value type %d", vtype);
+}
+
+static int occupancy_grid_w(int mode, int m, int vtype) {
+    static int cache[3][2][9] = {};
+    if (vtype < 0 || vtype > 2 || m < 1 || m > 8) fail(MPK_ERR_UNSUPPORTED, "value type %d, nrhs %d", vtype, m);
+    int &c = cache[vtype][mode][m];
+    if (c) return c;
+    int per_sm = 0;
+    MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, select_mpkw(mode, m, vtype), kWarpBS, 0));
+    if (per_sm < 1) fail(MPK_ERR_CUDA, "warp-engine kernel cannot be resident (occupancy 0)");
+    c = per_sm * device_sms();
+    return c;
+}
+
 void launch_mpk(const Plan &P, KArgs &a, int mode, cudaStream_t s) {
+    if (a.w_item != nullptr && a.trace == nullptr && a.drop_unit < 0) {  // warp engine
+        if (a.w_nitems <= 0) return;
+        MPK_CUDA(cudaMemsetAsync(a.w_cnt, 0,
+                                 sizeof(int32_t) * ((size_t)(P.p_max + 1) * std::max(P.num_chunks, 1) + kWarpQueues),
+                                 s));
+        int grid = occupancy_grid_w(mode, P.m, P.val_type);
+        const int64_t warps_needed = (a.w_nitems + kWarpQueues - 1) / kWarpQueues;
+        if ((int64_t)grid > warps_needed) grid = (int)warps_needed;
+        void *args[] = {&a};
+        MPK_CUDA(cudaLaunchKernel(select_mpkw(mode, P.m, P.val_type), dim3(grid), dim3(kWarpBS), args, 0, s));
+        return;
+    }
     if (a.nunits <= 0) return;
     const bool trace = a.trace != nullptr;
     int grid = occupancy_grid(mode, P.m, trace, P.val_type);

@@ -283,7 +283,7 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         P->order = o->order;
         P->identity = (L == nullptr);
         P->chunk_rows = chunk_rows;
-        P->cache_bytes = o->cache_bytes ? o->cache_bytes : device_l2_bytes() / 2;
+        P->cache_bytes = o->cache_bytes ? o->cache_bytes : device_l2_bytes();
         P->window = kSlotSkew * pmax + 1;
         P->group_budget = P->cache_bytes / P->window;
         P->wait_ns = o->wait_limit_ns ? o->wait_limit_ns : 2000000000LL;
@@ -551,6 +551,64 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
                 }
         }
         if (!batch) P->unit_off[pmax + 1] = (int64_t)units.size();
+
+        // ---- warp-ticketed engine: the same cells in the same order, split into items of
+        //      kWarpSlices slices; counters of finished items per cell
+        if (o->engine != MPK_ENGINE_STAGED && o->engine != MPK_ENGINE_WARP)
+            fail(MPK_ERR_INVALID, "engine must be MPK_ENGINE_STAGED or MPK_ENGINE_WARP");
+        if (o->engine == MPK_ENGINE_WARP) {
+            if (batch) fail(MPK_ERR_INVALID, "batch plans run on the staged engine");
+            P->engine = MPK_ENGINE_WARP;
+            std::vector<int64_t> w_item;
+            std::vector<int32_t> w_gk;
+            P->w_cell_off.assign((size_t)pmax + 2, 0);
+            P->w_items.assign((size_t)pmax + 1, 0);
+            for (int32_t p = 1; p <= pmax; ++p) {
+                P->w_cell_off[p] = (int64_t)w_item.size();
+                int64_t items = 0;
+                for (int32_t d = kSlotSkew; d <= G - 1 + kSlotSkew * p; ++d)
+                    for (int32_t k = 1; k <= p; ++k) {
+                        const int32_t g = d - kSlotSkew * k;
+                        if (g < 0 || g >= G || k > g_cap[g]) continue;
+                        const int32_t ns = g_slice[g + 1] - g_slice[g];
+                        if (ns <= 0) continue;
+                        w_item.push_back(items);
+                        w_gk.push_back((g << 5) | k);
+                        items += (ns + kWarpSlices - 1) / kWarpSlices;
+                    }
+                P->w_items[p] = items;
+                if (items >= ((int64_t)1 << 31) * kWarpQueues) fail(MPK_ERR_TOO_LARGE, "too many items");
+            }
+            P->w_cell_off[pmax + 1] = (int64_t)w_item.size();
+            if (G >= (1 << 26)) fail(MPK_ERR_TOO_LARGE, "too many groups for the warp engine");
+            P->g_slice = P->arena.alloc_n<int32_t>((int64_t)G + 1);
+            MPK_CUDA(cudaMemcpyAsync(P->g_slice, g_slice.data(), sizeof(int32_t) * ((size_t)G + 1),
+                                     cudaMemcpyHostToDevice, s));
+            P->w_item = P->arena.alloc_n<int64_t>((int64_t)w_item.size() + 1);
+            P->w_gk = P->arena.alloc_n<int32_t>((int64_t)w_gk.size() + 1);
+            if (!w_item.empty()) {
+                MPK_CUDA(cudaMemcpyAsync(P->w_item, w_item.data(), sizeof(int64_t) * w_item.size(),
+                                         cudaMemcpyHostToDevice, s));
+                MPK_CUDA(cudaMemcpyAsync(P->w_gk, w_gk.data(), sizeof(int32_t) * w_gk.size(), cudaMemcpyHostToDevice,
+                                         s));
+            }
+            // per chunk: its slices, and in bits 24.. the highest power it computes (a power
+            // above it never completes, so a dependency on it is void: level-capped plans)
+            std::vector<int32_t> s_chunk((size_t)NS + 1, 0), c_nsl((size_t)NC + 1, 0);
+            for (int32_t g = 0; g < G; ++g)
+                for (int32_t c = g_chunk[g]; c < g_chunk[g + 1]; ++c) {
+                    c_nsl[c] = (c_slice[c + 1] - c_slice[c]) | (g_cap[g] << 24);
+                    for (int32_t q = c_slice[c]; q < c_slice[c + 1]; ++q) s_chunk[q] = c;
+                }
+            P->w_slice_chunk = P->arena.alloc_n<int32_t>((int64_t)NS + 1);
+            P->w_chunk_nsl = P->arena.alloc_n<int32_t>((int64_t)NC + 1);
+            MPK_CUDA(cudaMemcpyAsync(P->w_slice_chunk, s_chunk.data(), sizeof(int32_t) * ((size_t)NS + 1),
+                                     cudaMemcpyHostToDevice, s));
+            MPK_CUDA(cudaMemcpyAsync(P->w_chunk_nsl, c_nsl.data(), sizeof(int32_t) * ((size_t)NC + 1),
+                                     cudaMemcpyHostToDevice, s));
+            P->w_cnt = P->arena.alloc_n<int32_t>((int64_t)(pmax + 1) * std::max(NC, 1) + kWarpQueues);
+            MPK_CUDA(cudaStreamSynchronize(s));  // host tables go out of scope
+        }
         P->units = P->arena.alloc_n<int32_t>((int64_t)units.size() + 1);
         if (!units.empty())
             MPK_CUDA(cudaMemcpyAsync(P->units, units.data(), sizeof(int32_t) * units.size(), cudaMemcpyHostToDevice, s));

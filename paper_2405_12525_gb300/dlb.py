@@ -129,7 +129,7 @@ class DlbMpk:
     vectors and the gather of the powers into A's own numbering."""
 
     def __init__(self, A, parts: int, p_m: int, nrhs: int = 1, cache_bytes: int = 0, value_type=None,
-                 balance: str = "nnz"):
+                 balance: str = "nnz", engine: int = 0):
         import torch
         from . import MAX_ROW_SEGMENTS, MPK_F64, ORDER_PLAN, CsrMatrix, build_levels, build_levels_from, plan
         if parts > MAX_ROW_SEGMENTS:
@@ -153,7 +153,7 @@ class DlbMpk:
             else:
                 L = build_levels(dA, 0)
             P = plan(dA, L, p_max=p_m, nrhs=nrhs, order=ORDER_PLAN, cache_bytes=cache_bytes,
-                     level_capped=bool(pb["nh"]))
+                     level_capped=bool(pb["nh"]), engine=engine)
             lp = L.level_ptr.cpu().numpy().astype(np.int64)
             perm = L.perm.cpu().numpy().astype(np.int64)
             iperm = L.iperm.cpu().numpy().astype(np.int64)
