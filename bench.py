@@ -38,7 +38,7 @@ METRIC = "Level-blocked MPK Gflop/s vs p×CSR SpMV on 1 GB300; serving p50/p99 l
 SM_MAX_MHZ = 2070.0
 NUM_SMS = 152
 DFMA_LANES_PER_CLK_PER_SM = 2  # measured on GB300 (0.60 T FP64 FMA/s at ~1.97 GHz)
-KERNEL_SOURCE = os.path.join(ROOT, "paper_2405_12525_gb300", "csrc", "mpk_kernel.cu")
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2405_12525_gb300", "csrc", f) for f in ("mpk_kernel.cu", "mpk_internal.h")]
 TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "k_mpk_traffic.json")
 
 
@@ -47,7 +47,10 @@ def measured_traffic(side: int):
     when the record is missing, was taken on another workload, or the kernel source changed."""
     try:
         rec = json.load(open(TRAFFIC_RECORD))
-        sha = hashlib.sha256(open(KERNEL_SOURCE, "rb").read()).hexdigest()
+        h = hashlib.sha256()
+        for f in KERNEL_SOURCES:
+            h.update(open(f, "rb").read())
+        sha = h.hexdigest()
     except (OSError, ValueError):
         return None
     if rec.get("kernel_source_sha256") != sha or rec.get("side") != side:
@@ -63,6 +66,7 @@ def parse():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--side", type=int, default=256, help="grid side of the 3-D Laplacian")
     ap.add_argument("--p", type=int, default=8)
+    ap.add_argument("--cache-mb", type=int, default=0, help="cache budget C of the plan in MiB (0: library default)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="laplace3d", choices=["laplace3d", "cheb_xxz", "batch_cfg3", "serving", "dlb"])
@@ -720,9 +724,10 @@ def main():
     L = mpk.build_levels(dA, 0)
     t_levels = time.perf_counter() - t0
     t0 = time.perf_counter()
-    P = mpk.plan(dA, L, p_max=p, nrhs=1, order=mpk.ORDER_PLAN)          # headline: one kernel launch
+    cb = args.cache_mb << 20
+    P = mpk.plan(dA, L, p_max=p, nrhs=1, order=mpk.ORDER_PLAN, cache_bytes=cb)    # headline: one kernel launch
     t_plan = time.perf_counter() - t0
-    Po = mpk.plan(dA, L, p_max=p, nrhs=1, order=mpk.ORDER_ORIGINAL)     # with gather/scatter
+    Po = mpk.plan(dA, L, p_max=p, nrhs=1, order=mpk.ORDER_ORIGINAL, cache_bytes=cb)  # with gather/scatter
     P0 = mpk.plan(dA, None, p_max=p, nrhs=1)                            # natural-order comparator
     desc = P.describe()
     Y = torch.empty((p + 1, A.n, 1), dtype=torch.float64, device="cuda")

@@ -124,7 +124,7 @@ void mpk_levels_destroy(mpk_levels *L);
 typedef struct {
     int32_t p_max;          /* largest power mpk_apply may request (1..31)                 */
     int32_t nrhs;           /* m: 1, 2, 4 or 8 right-hand sides per call                    */
-    int64_t cache_bytes;    /* C in bytes; 0 = the device L2 size                          */
+    int64_t cache_bytes;    /* C in bytes; 0 = three quarters of the device L2            */
     int32_t order;          /* mpk_order of X, Y and the Chebyshev input/output             */
     int32_t chunk_rows;     /* rows per work unit (multiple of 32); 0 = 416 (13 slices)     */
     int64_t wait_limit_ns;  /* bound on every device-side wait; 0 = 2 s                     */
@@ -137,6 +137,10 @@ typedef struct {
                                Needs levels and MPK_ORDER_PLAN (else MPK_ERR_INVALID);
                                mpk_cheb_filter rejects such a plan                           */
     int32_t engine;         /* MPK_ENGINE_STAGED (0, default) or MPK_ENGINE_WARP (1), below  */
+    int32_t shape;          /* block shape of the staged engine: 0 = chosen from the mean
+                               row width; 1 = 13 compute warps, 3072-entry slots, 3 blocks
+                               per SM (rows up to ~7 entries); 2 = 15 warps, 4096 entries,
+                               2 blocks; 3 = 15 warps, entries read from global memory      */
 } mpk_plan_opts;
 
 /* Engines of the level-blocked kernel (same results bit for bit, same Lp-diagram order):

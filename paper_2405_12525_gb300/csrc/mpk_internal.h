@@ -143,32 +143,30 @@ struct Levels {
 
 // Arguments of the level-blocked kernel, passed by value.
 constexpr int kMaxP = 31;
-// padded entries of one chunk that the kernel stages in shared memory (per buffer)
-#ifndef MPK_STAGE_ENTRIES
-#define MPK_STAGE_ENTRIES 3072
-#endif
-constexpr int kStageEntries = MPK_STAGE_ENTRIES;
+// Block shapes of the level-blocked kernel: compute warps per block (one 32-row slice each
+// per unit, so the default chunk is 32 * comp_warps rows), padded entries a shared-memory
+// slot holds (a chunk is cut to fit one), and blocks per SM for the single-vector power
+// kernel.  Shape 0 suits rows of up to about 7 stored entries (13 slices of width 7 fill a
+// slot); shape 1 suits wider rows; shape 2 stages nothing (stage_entries 0: the compute
+// warps read the entries from global memory, and chunks are not cut by a slot), for rows so
+// wide that a slot holds only a few slices.  The planner picks the shape from the mean
+// slice width unless the plan options name one.
+struct BlockShape {
+    int comp_warps, stage_entries, blocks;
+};
+constexpr BlockShape kShapes[3] = {{13, 3072, 3}, {15, 4096, 2}, {15, 0, 2}};
+constexpr int kNumShapes = 3;
+constexpr int kMaxStageEntries = 4096;
 // 1: chunks whose entries fit a buffer are copied to shared memory by the bulk-copy engine;
 // 0: every unit reads its entries from global memory (L2) directly
 #ifndef MPK_STAGE
 #define MPK_STAGE 1
 #endif
 constexpr bool kStageChunks = MPK_STAGE != 0;
-// entries whose x loads a lane issues together on the global-memory (unstaged) path
-#ifndef MPK_UNSTAGED_BATCH
-#define MPK_UNSTAGED_BATCH 1
-#endif
-constexpr int kUnstagedBatch = MPK_UNSTAGED_BATCH;
 // dependency ranges kept per chunk (exact sets compressed to this many index ranges)
 constexpr int kDepRanges = 4;
 // trace counters accumulated in shared memory (the last one, SM cycles, is added directly)
 constexpr int kTraceShared = MPK_TRACE_COUNTERS - 1;
-// compute warps of the level-blocked kernel; the default chunk is one 32-row slice per warp
-#ifndef MPK_COMP_WARPS
-#define MPK_COMP_WARPS 13
-#endif
-constexpr int kCompWarps = MPK_COMP_WARPS;
-constexpr int kDefaultChunkRows = 32 * kCompWarps;
 // The level-blocked kernel walks the Lp diagram along lines g + kSlotSkew * k = const.  With
 // skew 1 (the paper's diagonals) the cells of one line form a dependency chain; with skew 3
 // every dependency of a cell lies at least two lines back, so the cells in flight on the
@@ -240,6 +238,7 @@ struct Plan {
     int32_t val_type = MPK_F64, val_bytes = 8;  // storage of the matrix values (mpk_dtype)
     int32_t num_levels = 0, num_groups = 0, num_chunks = 0, num_slices = 0;
     int32_t chunk_rows = 512;
+    int32_t shape = 0;  // block shape of the level-blocked kernel (kShapes)
     int64_t cache_bytes = 0, group_budget = 0, padded = 0, wait_ns = 0;
     int32_t window = 0;  // groups sharing the cache budget: kSlotSkew * p_max + 1
     bool identity = false;
@@ -322,7 +321,7 @@ void launch_scatter_rows(const double *src, const int32_t *iperm, double *dst, i
                          cudaStream_t s);
 void launch_cheb_init(const double *v0, double *acc, int32_t n, int32_t m, double c0re, double c0im,
                       int complex_coeff, cudaStream_t s);
-int occupancy_grid(int mode, int m, bool trace, int vtype);
+int occupancy_grid(int mode, int m, bool trace, int vtype, int shape);
 // dst[i] = src[i] widened to float64 (src of mpk_dtype vtype), exact
 void widen_values(int vtype, const void *src, int64_t n, double *dst, cudaStream_t s);
 

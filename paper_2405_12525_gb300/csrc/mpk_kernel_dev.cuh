@@ -1,0 +1,757 @@
+// Device code shared by the translation units of the level-blocked kernel: constants,
+// synchronisation helpers, value types, the row body and the persistent kernel k_mpk.
+// mpk_kernel.cu includes it for the warp engine, the SpMV and the launches; each
+// mpk_kshape<N>.cu instantiates k_mpk for block shape N, so that the shapes compile in
+// parallel.
+#pragma once
+#include "mpk_internal.h"
+
+#include <algorithm>
+
+namespace mpk {
+
+// level-blocked kernel of block shape SH: one control warp and the shape's compute warps
+template <int SH> struct Shape {
+    static constexpr int CW = kShapes[SH].comp_warps;
+    static constexpr int SE = kShapes[SH].stage_entries;
+    static constexpr int BS = 32 * (1 + CW);
+};
+// blocks per SM the register budget is set for (65536 registers per SM).  Shape 0 runs the
+// single-vector power kernel at three blocks of 14 warps (40 registers a thread; its two
+// 3072-entry slots, 72 KB, fit three times in an SM's shared memory); wider blocks, the
+// Chebyshev recurrence, the traced kernel and shape 1 keep 64 registers at two blocks.
+template <int M, int MODE, bool TRACE, int SH> struct MpkOcc {
+    static constexpr int blocks = (M == 1 && MODE == 0 && !TRACE) ? kShapes[SH].blocks : 2;
+};
+constexpr int kSpmvBS = 256;        // threads per block of the plain SpMV kernel
+// Staging slots: the control warp fills one while the compute warps work on the other.
+constexpr int kSlots = 2;
+// column indices of staged chunks: copied to shared memory beside the values (1), or read
+// from global memory (L2) by the compute warps (0), which halves the slot size for FP64
+#ifndef MPK_STAGE_COL
+#define MPK_STAGE_COL 1
+#endif
+constexpr bool kStageCol = MPK_STAGE_COL != 0;
+// one slot: the shape's stage entries of the matrix's value type, then as many column indices
+template <class VT, int SH> constexpr int smem_bytes() {
+    return kSlots * Shape<SH>::SE * (int)(sizeof(typename VT::T) + (kStageCol ? 4 : 0));
+}
+
+enum Mode { MODE_POWERS = 0, MODE_CHEB = 1 };
+
+__device__ __forceinline__ int ld_relaxed(const int32_t *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed(int32_t *p, int v) {
+    asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint64_t globaltimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx_only(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// global -> shared bulk copy (TMA, untiled); addresses 16-byte aligned, bytes % 16 == 0
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Entries whose x loads are issued together before their FMAs.
+template <int M> struct Batch {
+    static constexpr int B = M == 1 ? 8 : (M == 2 ? 4 : (M == 4 ? 2 : 1));
+};
+
+// acc[i] = sum_j val[j] * x[col[j]*M + i] over a row's entries, in stored order.  Entry j
+// of the row is at val[off + 32 j] / col[off + 32 j] (global or shared memory), j < width
+// of the row's slice; entries past the row's end are padding with col < 0 and are skipped.
+template <int M, int B, class VP, class CP>
+__device__ __forceinline__ void row_sum(VP val, CP col, int64_t off, int width, const double *x, double (&acc)[M]) {
+#pragma unroll
+    for (int i = 0; i < M; ++i) acc[i] = 0.0;
+    for (int j0 = 0; j0 < width; j0 += B) {
+        double v[B];
+        int32_t c[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            if (j0 + b < width) {
+                v[b] = val[off + 32 * (int64_t)(j0 + b)];
+                c[b] = col[off + 32 * (int64_t)(j0 + b)];
+            } else {
+                v[b] = 0.0;
+                c[b] = -1;
+            }
+        }
+        double xv[B][M];
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+#pragma unroll
+            for (int i = 0; i < M; ++i) xv[b][i] = (c[b] >= 0) ? x[(int64_t)c[b] * M + i] : 0.0;
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+            if (c[b] >= 0) {
+#pragma unroll
+                for (int i = 0; i < M; ++i) acc[i] = fma(v[b], xv[b][i], acc[i]);
+            }
+    }
+}
+
+// Continues a row sum from entry j0 (acc already holds entries 0..j0-1).
+template <int M, int B, class VP, class CP>
+__device__ __forceinline__ void row_sum_from(VP val, CP col, int64_t off, int j_start, int width, const double *x,
+                                             double (&acc)[M]) {
+    for (int j0 = j_start; j0 < width; j0 += B) {
+        double v[B];
+        int32_t c[B];
+#pragma unroll
+        for (int b = 0; b < B; ++b) {
+            if (j0 + b < width) {
+                v[b] = val[off + 32 * (int64_t)(j0 + b)];
+                c[b] = col[off + 32 * (int64_t)(j0 + b)];
+            } else {
+                v[b] = 0.0;
+                c[b] = -1;
+            }
+        }
+        double xv[B][M];
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+#pragma unroll
+            for (int i = 0; i < M; ++i) xv[b][i] = (c[b] >= 0) ? x[(int64_t)c[b] * M + i] : 0.0;
+#pragma unroll
+        for (int b = 0; b < B; ++b)
+            if (c[b] >= 0) {
+#pragma unroll
+                for (int i = 0; i < M; ++i) acc[i] = fma(v[b], xv[b][i], acc[i]);
+            }
+    }
+}
+
+// ----------------------------------------------------------------------------- value types
+// Matrix values are stored as float64, float32 or bfloat16 and widened to float64 before
+// their FMA, exactly and with integer operations only (widen_normal32: the planner admits
+// zeros and normal numbers in the narrow types).
+struct ValF64 {
+    using T = double;
+    static __device__ __forceinline__ double widen(double v) { return v; }
+};
+struct ValF32 {
+    using T = float;
+    static __device__ __forceinline__ double widen(float v) { return widen_normal32(__float_as_uint(v)); }
+};
+struct ValBF16 {
+    using T = uint16_t;  // bfloat16 bits
+    static __device__ __forceinline__ double widen(uint16_t v) { return widen_normal32((uint32_t)v << 16); }
+};
+
+// read-only views returning widened values: the immutable matrix copy in global memory, or a
+// staged slot in shared memory
+template <class VT> struct GVal {
+    const typename VT::T *p;
+    __device__ __forceinline__ double operator[](int64_t i) const { return VT::widen(__ldg(p + i)); }
+};
+template <class VT> struct SVal {
+    const typename VT::T *p;
+    __device__ __forceinline__ double operator[](int64_t i) const { return VT::widen(p[i]); }
+};
+struct GCol {
+    const int32_t *p;
+    __device__ __forceinline__ int32_t operator[](int64_t i) const { return __ldg(p + i); }
+};
+
+// Epilogue of one row at local power k: store into the plan-order slot, or advance the
+// Chebyshev recurrence.
+template <int M, int MODE>
+__device__ __forceinline__ void row_epilogue(const KArgs &a, int k, int64_t r, const double (&w)[M],
+                                             const double *xin) {
+    const int j = a.k_offset + k;  // absolute power / recurrence step
+    double *y = a.ybase + (int64_t)(j % a.ring) * a.ystride + r * M;
+    if constexpr (MODE == MODE_CHEB) {
+        double vn[M];
+        if (j == 1) {
+#pragma unroll
+            for (int i = 0; i < M; ++i) vn[i] = fma(a.halpha, w[i], a.hbeta * xin[r * M + i]);
+        } else {
+            const double *vp2 = a.ybase + (int64_t)((j - 2) % a.ring) * a.ystride + r * M;
+#pragma unroll
+            for (int i = 0; i < M; ++i) vn[i] = fma(a.alpha, w[i], fma(a.beta, xin[r * M + i], -vp2[i]));
+        }
+#pragma unroll
+        for (int i = 0; i < M; ++i) y[i] = vn[i];
+        double *acc = a.acc + r * M;
+        const double cr = a.cre[k];
+        if (!a.complex_coeff) {
+#pragma unroll
+            for (int i = 0; i < M; ++i) acc[i] = fma(cr, vn[i], acc[i]);
+        } else {
+            const double ci = a.cim[k];
+#pragma unroll
+            for (int i = 0; i + 1 < M; i += 2) {
+                double re = acc[i], im = acc[i + 1];
+                re = fma(cr, vn[i], re);
+                re = fma(-ci, vn[i + 1], re);
+                im = fma(cr, vn[i + 1], im);
+                im = fma(ci, vn[i], im);
+                acc[i] = re;
+                acc[i + 1] = im;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < M; ++i) y[i] = w[i];
+    }
+}
+
+// ----------------------------------------------------------------------------- K-MPK
+// Work unit = (row chunk c, local power k).  Units are claimed through one atomic ticket
+// in the order of the unit table, which lists the Lp-diagram cells (group g, power k) line
+// by line (g + kSlotSkew * k ascending) and, inside a line, k ascending.  Every dependency
+// of a unit (chunks holding the rows it reads, at power k-1) lies on an earlier line, so it
+// has a smaller ticket: the unit holding the
+// smallest unfinished ticket can always run, whichever blocks are resident, and the
+// schedule cannot deadlock.  A finished unit publishes flags[k][c] = epoch (release); a
+// unit waits until the flags of its dependency ranges at power k-1 equal the epoch
+// (acquire).
+//
+// Warp roles.  Warp 0 (control) claims units, stages each unit's matrix entries into one
+// of kSlots shared-memory slots with bulk (TMA) copies and polls the unit's dependencies;
+// warps 1..kCompWarps (compute) compute rows, and the last of them to finish a unit
+// publishes its completion flag.  Slot b has two mbarriers: full[b] completes when the
+// entries have landed and the dependencies are met, empty[b] when every compute warp is
+// done with the slot.  The control warp prepares unit i+1 while compute warps work on unit
+// i; its claims run three units ahead (tickets, unit ids and chunk records are fetched an
+// iteration before they are needed), so only the dependency poll is on its critical path.
+// A block processes its tickets in claim order and claims are increasing, so the block
+// holding the smallest unfinished ticket is working on it: the schedule stays deadlock
+// free with tickets claimed ahead.
+// When no ticket is left, or a wait fails, the control warp stores the number of units it
+// handed over in s_final; compute warps stop at that unit.  Every wait is bounded by
+// a.wait_ns (globaltimer); on expiry the control warp records the epoch and
+// MPK_ERR_TIMEOUT in a.err and all blocks drain out; no block exits with a bulk copy of
+// its own still in flight.  The last block to exit resets the ticket.
+struct UnitInfo {
+    int unit;         // chunk << 5 | k
+    int row0, row1, slice0;
+    int ecount;       // padded entries of the chunk
+    int staged;       // entries were copied to the slot's shared buffer
+    int nsl;          // slices of the chunk
+    int widths[4];    // staged chunks: width of slice q in byte q of the 16 bytes
+    long long ebase;  // first entry of the chunk in the sliced copy
+};
+
+__device__ __forceinline__ bool timed_out(uint64_t t0, int64_t limit) { return globaltimer() - t0 > (uint64_t)limit; }
+
+__device__ __forceinline__ int slice_width(const int (&w)[4], int q) {
+    const int word = (q < 8) ? ((q < 4) ? w[0] : w[1]) : ((q < 12) ? w[2] : w[3]);  // no dynamic indexing
+    return (word >> (8 * (q & 3))) & 0xff;
+}
+
+// A compute warp handles a unit in two phases.  Phase A reads the column indices of the
+// warp's first row batch from shared memory and issues the x gathers; phase B runs the
+// FMAs on those x values, finishes any further batches or slices, stores the results and
+// publishes the unit.  Phase B directly follows phase A of the same unit: a warp holds no
+// unit across a wait, so its lanes, which wait on the slot's mbarrier one by one, always
+// work on the same unit.
+template <int M> struct Prefetch {
+    static constexpr int B = Batch<M>::B;
+    int unit;             // -1: nothing pending
+    int slot;
+    int r;                // this lane's row in the warp's first slice, -1 if none
+    int off;              // offset of that row's entries in the slot (staged units)
+    int width;            // width of the warp's first slice (staged units)
+    double x[B][M];       // x values of the first batch (entries j < min(B, width))
+};
+
+template <int M>
+__device__ __forceinline__ const double *input_block(const KArgs &a, int k) {
+    return (k == 1 && a.k_offset == 0) ? a.x0 : a.ybase + (int64_t)((a.k_offset + k - 1) % a.ring) * a.ystride;
+}
+
+// phase A: request the x values of the warp's first batch of unit u (slot b)
+template <int M>
+__device__ __forceinline__ void phase_a(const KArgs &a, const UnitInfo &u, int b, const int32_t *scol, int cwarp,
+                                        int lane, Prefetch<M> &pf) {
+    constexpr int B = Batch<M>::B;
+    pf.unit = u.unit;
+    pf.slot = b;
+    const double *xin = input_block<M>(a, u.unit & 31);
+    pf.r = -1;
+    pf.width = 0;
+    pf.off = 0;
+    if (u.staged && cwarp < u.nsl) {
+        int pre = 0;
+#pragma unroll
+        for (int q = 0; q < kRecSlices; ++q) pre += (q < cwarp) ? slice_width(u.widths, q) : 0;
+        pf.width = slice_width(u.widths, cwarp);
+        pf.off = 32 * pre + lane;
+        const int r = u.row0 + 32 * cwarp + lane;
+        if (r < u.row1) pf.r = r;
+    }
+#pragma unroll
+    for (int q = 0; q < B; ++q) {
+        const int c = (pf.r >= 0 && q < pf.width) ? scol[pf.off + 32 * q] : -1;
+#pragma unroll
+        for (int i = 0; i < M; ++i) pf.x[q][i] = (c >= 0) ? xin[(int64_t)c * M + i] : 0.0;
+    }
+}
+
+// phase B: finish unit pf (all of the warp's rows), then publish and release its slot
+template <int M, int MODE, class VT, int SH>
+__device__ __forceinline__ void phase_b(const KArgs &a, int32_t epoch, const Prefetch<M> &pf, const UnitInfo *s_u,
+                                        const typename VT::T *sval0, const int32_t *scol0, int *s_done, uint64_t *s_empty,
+                                        int cwarp, int lane) {
+    constexpr int B = Batch<M>::B;
+    const UnitInfo &u = s_u[pf.slot];
+    const int k = pf.unit & 31;
+    const double *xin = input_block<M>(a, k);
+    constexpr int kCompWarps = Shape<SH>::CW;
+    const SVal<VT> sval{sval0 + pf.slot * Shape<SH>::SE};
+    const int32_t *scol = kStageCol ? scol0 + pf.slot * Shape<SH>::SE : a.col + u.ebase;
+    if (u.staged) {
+        if (pf.r >= 0) {  // first slice: prefetched first batch, then the rest of the row
+            double w[M];
+#pragma unroll
+            for (int i = 0; i < M; ++i) w[i] = 0.0;
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+                if (q < pf.width && scol[pf.off + 32 * q] >= 0) {
+                    const double v = sval[pf.off + 32 * q];
+#pragma unroll
+                    for (int i = 0; i < M; ++i) w[i] = fma(v, pf.x[q][i], w[i]);
+                }
+            }
+            if (pf.width > B) row_sum_from<M, 2>(sval, scol, pf.off, B, pf.width, xin, w);  // rare: wide rows
+            row_epilogue<M, MODE>(a, k, pf.r, w, xin);
+            if (k == 1 && a.y0copy) {
+#pragma unroll
+                for (int i = 0; i < M; ++i) a.y0copy[(int64_t)pf.r * M + i] = a.x0[(int64_t)pf.r * M + i];
+            }
+        }
+        for (int sl = cwarp + kCompWarps; sl < u.nsl; sl += kCompWarps) {  // further slices (wide chunks)
+            const int64_t r = (int64_t)u.row0 + 32 * sl + lane;
+            int pre = 0;
+#pragma unroll
+            for (int q = 0; q < kRecSlices; ++q) pre += (q < sl) ? slice_width(u.widths, q) : 0;
+            if (r >= u.row1) continue;
+            double w[M];
+            row_sum<M, 2>(sval, scol, 32 * pre + lane, slice_width(u.widths, sl), xin, w);  // rare: wide chunks
+            row_epilogue<M, MODE>(a, k, r, w, xin);
+            if (k == 1 && a.y0copy) {
+#pragma unroll
+                for (int i = 0; i < M; ++i) a.y0copy[r * M + i] = a.x0[r * M + i];
+            }
+        }
+    } else {  // entries in global memory (chunk too large to stage)
+        for (int sl = cwarp; sl < u.nsl; sl += kCompWarps) {
+            const int64_t r = (int64_t)u.row0 + 32 * sl + lane;
+            if (r >= u.row1) continue;
+            const int64_t s0 = __ldg(a.slice_ptr + u.slice0 + sl), s1 = __ldg(a.slice_ptr + u.slice0 + sl + 1);
+            double w[M];
+            // entries whose x loads are issued together: the unstaged shape issues a row's
+            // loads in batches; the staged shapes keep this rare path small (registers)
+            constexpr int BU = Shape<SH>::SE == 0 ? Batch<M>::B : 1;
+            row_sum<M, BU>(GVal<VT>{static_cast<const typename VT::T *>(a.val) + u.ebase}, GCol{a.col + u.ebase},
+                           s0 - u.ebase + lane, (int)((s1 - s0) >> 5), xin, w);
+            row_epilogue<M, MODE>(a, k, r, w, xin);
+            if (k == 1 && a.y0copy) {
+#pragma unroll
+                for (int i = 0; i < M; ++i) a.y0copy[r * M + i] = a.x0[r * M + i];
+            }
+        }
+    }
+    __syncwarp();
+    if (lane == 0) {
+        // the last compute warp to finish the unit publishes it (release at gpu scope after
+        // the other warps' stores were ordered at block scope), then the slot is released
+        __threadfence_block();
+        if (atomicAdd(&s_done[pf.slot], 1) == kCompWarps - 1) {
+            s_done[pf.slot] = 0;
+            fence_acq_rel_gpu();
+            if (pf.unit != a.drop_unit)
+                st_relaxed(a.flags + (int64_t)k * a.nchunks + (pf.unit >> 5), epoch);
+        }
+        mbar_arrive(&s_empty[pf.slot]);
+    }
+}
+
+// dependency flags v0 .. v0+127 of a unit (4 per lane); flags past `total` read as ready
+__device__ __forceinline__ void dep_load(const KArgs &a, int32_t epoch, int k, const int (&lo)[kDepRanges],
+                                         const int (&len)[kDepRanges], int total, int v0, int lane, int (&got)[4]) {
+    const int32_t *f = a.flags + (int64_t)(k - 1) * a.nchunks;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        int v = v0 + 32 * q + lane;
+        int idx = -1;
+        if (v < total) {
+#pragma unroll
+            for (int r = 0; r < kDepRanges; ++r) {
+                if (idx < 0 && v < len[r]) idx = lo[r] + v;
+                if (idx < 0) v -= len[r];
+            }
+        }
+        got[q] = idx >= 0 ? ld_relaxed(f + idx) : epoch;
+    }
+}
+
+// all lanes of the control warp: true when every flag of the unit's ranges equals epoch
+__device__ __forceinline__ bool deps_ready(const KArgs &a, int32_t epoch, int k, const int (&lo)[kDepRanges],
+                                           const int (&len)[kDepRanges], int total, int lane) {
+    bool ok = true;
+    for (int v0 = 0; v0 < total; v0 += 128) {
+        int got[4];
+        dep_load(a, epoch, k, lo, len, total, v0, lane, got);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ok = ok && got[q] == epoch;
+    }
+    return __all_sync(0xffffffffu, ok);
+}
+
+// dependency ranges of a chunk record (ints 8..15, shuffled from the lanes holding them)
+__device__ __forceinline__ int dep_ranges_of(int rec, int (&lo)[kDepRanges], int (&len)[kDepRanges]) {
+    int total = 0;
+#pragma unroll
+    for (int r = 0; r < kDepRanges; ++r) {
+        lo[r] = __shfl_sync(0xffffffffu, rec, 8 + 2 * r);
+        len[r] = max(0, __shfl_sync(0xffffffffu, rec, 9 + 2 * r) - lo[r] + 1);
+        total += len[r];
+    }
+    return total;
+}
+
+template <int M, int MODE, bool TRACE, class VT, int SH>
+__global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::blocks)) k_mpk(const KArgs a) {
+    constexpr int kCompWarps = Shape<SH>::CW, kStageEntries = Shape<SH>::SE;
+    using T = typename VT::T;
+    const bool tr = TRACE && a.trace != nullptr;  // timing counters (instantiated separately)
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t s_full[kSlots];
+    __shared__ __align__(8) uint64_t s_empty[kSlots];
+    __shared__ UnitInfo s_u[kSlots];
+    __shared__ volatile int s_final;  // units handed over in total; -1 while the control warp runs
+    __shared__ int s_done[kSlots];    // compute warps finished with the slot's unit
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    T *const sval0 = reinterpret_cast<T *>(smem);
+    int32_t *const scol0 = reinterpret_cast<int32_t *>(smem + kSlots * kStageEntries * sizeof(T));
+
+    const uint64_t t_start = tr ? globaltimer() : 0;
+    // trace counters (see mpk_read_trace); s_tarr: time of each slot's last hand-over
+    __shared__ unsigned long long s_tr[kTraceShared];
+    __shared__ unsigned long long s_tarr[kSlots];
+    auto tr_add = [&](int q, unsigned long long v) {
+        if (tr) atomicAdd(&s_tr[q], v);
+    };
+    const long long c_start = tr ? clock64() : 0;
+    if (tid < kTraceShared) s_tr[tid] = 0;
+    // Epochs live on the device, so that launches replayed from a CUDA graph stay distinct:
+    // the last block of a launch stores its epoch, the next launch uses that plus one.
+    __shared__ int32_t s_epoch;
+    if (tid == 0) {
+        s_epoch = (int32_t)ld_relaxed(reinterpret_cast<const int32_t *>(a.epoch_word)) + 1;
+        s_final = -1;
+        for (int q = 0; q < kSlots; ++q) {
+            s_done[q] = 0;
+            mbar_init(&s_full[q], 1);
+            mbar_init(&s_empty[q], kCompWarps);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int32_t epoch = s_epoch;
+
+    if (warp == 0) {
+        // ------------------------------------------------------------------ control warp
+        const int32_t *rec = reinterpret_cast<const int32_t *>(a.chunk_rec);
+        bool slot_busy[kSlots] = {};  // a handed-over unit may still be computed
+        int slot_use[kSlots] = {};    // phase index (i / kSlots) of that hand-over
+        bool aborted = false;
+        auto record_timeout = [&]() {
+            if (lane == 0 && atomicExch(a.err, epoch) != epoch) st_relaxed(a.err + 1, (int)MPK_ERR_TIMEOUT);
+        };
+        auto unit_at = [&](unsigned int t) -> int { return (int64_t)t < a.nunits ? __ldg(a.units + t) : -1; };
+        // claim pipeline, three units deep: unit i (id u_cur, record r_cur), unit i+1 (u_nxt,
+        // r_nxt), unit i+2 (id u_nn, held by lane 0) and the ticket t of unit i+3.  At the end
+        // of iteration i the record of unit i+2, the id of unit i+3 and one more ticket are
+        // fetched, each a full iteration before it is needed.
+        auto rec_at = [&](int un) -> int {
+            return (un >= 0 && lane < kRecInts) ? __ldg(rec + kRecInts * (int64_t)(un >> 5) + lane) : 0;
+        };
+        int u_cur = -1, u_nxt = -1, u_nn = -1;
+        unsigned int t = 0;
+        if (lane == 0) {
+            const unsigned int t0 = atomicAdd(a.ticket, 1u);
+            const unsigned int t1 = atomicAdd(a.ticket, 1u);
+            const unsigned int t2 = atomicAdd(a.ticket, 1u);
+            t = atomicAdd(a.ticket, 1u);
+            u_cur = unit_at(t0);
+            u_nxt = unit_at(t1);
+            u_nn = unit_at(t2);
+        }
+        u_cur = __shfl_sync(0xffffffffu, u_cur, 0);
+        u_nxt = __shfl_sync(0xffffffffu, u_nxt, 0);
+        int r_cur = rec_at(u_cur);
+        int r_nxt = rec_at(u_nxt);
+        int i = 0;
+        for (;; ++i) {
+            if (u_cur < 0) break;  // no more work
+            const int b = i % kSlots;
+            const long long c0 = tr ? clock64() : 0;
+            // current unit
+            UnitInfo u;
+            u.unit = u_cur;
+            u.row0 = __shfl_sync(0xffffffffu, r_cur, 0);
+            u.row1 = __shfl_sync(0xffffffffu, r_cur, 1);
+            u.slice0 = __shfl_sync(0xffffffffu, r_cur, 2);
+            u.ecount = __shfl_sync(0xffffffffu, r_cur, 3);
+            u.ebase = (long long)(unsigned int)__shfl_sync(0xffffffffu, r_cur, 4) |
+                      ((long long)__shfl_sync(0xffffffffu, r_cur, 5) << 32);
+            u.staged = __shfl_sync(0xffffffffu, r_cur, 6);
+            u.nsl = __shfl_sync(0xffffffffu, r_cur, 7);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) u.widths[q] = __shfl_sync(0xffffffffu, r_cur, 16 + q);
+            int dlo[kDepRanges], dlen[kDepRanges];
+            const int total = dep_ranges_of(r_cur, dlo, dlen);
+            if (tr && lane == 0) tr_add(11, clock64() - c0);
+            // slot b held unit i-kSlots: wait until it is computed before reusing the slot
+            if (slot_busy[b]) {
+                const uint64_t t0 = globaltimer();
+                bool ok;
+                while (!(ok = mbar_try_wait(&s_empty[b], slot_use[b] & 1)))
+                    if (timed_out(t0, a.wait_ns)) break;
+                if (tr && lane == 0) tr_add(3, globaltimer() - t0);
+                if (!ok) {
+                    record_timeout();
+                    aborted = true;
+                    break;
+                }
+                slot_busy[b] = false;
+            }
+            // stage the entries
+            const long long c2 = tr ? clock64() : 0;
+            if (lane == 0) {
+                s_u[b] = u;
+                if (u.staged) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    mbar_expect_tx_only(&s_full[b], (uint32_t)u.ecount * (uint32_t)(sizeof(T) + (kStageCol ? 4 : 0)));
+                    bulk_g2s(sval0 + b * kStageEntries, static_cast<const T *>(a.val) + u.ebase,
+                             (uint32_t)(u.ecount * sizeof(T)), &s_full[b]);
+                    if (kStageCol)
+                        bulk_g2s(scol0 + b * kStageEntries, a.col + u.ebase, (uint32_t)u.ecount * 4u, &s_full[b]);
+                }
+            }
+            if (tr && lane == 0) tr_add(8, clock64() - c2);
+            // dependencies of unit i
+            const int k = u.unit & 31;
+            if (k > 1) {
+                const uint64_t t0 = globaltimer();
+                while (!deps_ready(a, epoch, k, dlo, dlen, total, lane)) {
+                    if (lane == 0) tr_add(2, 1);
+                    const bool stop = ld_relaxed(a.err) == epoch || timed_out(t0, a.wait_ns);
+                    if (__any_sync(0xffffffffu, stop)) {
+                        aborted = true;
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+                if (tr && lane == 0) tr_add(1, globaltimer() - t0);
+            }
+            if (lane == 0) tr_add(0, 1);
+            if (aborted) {
+                // unit i is not handed over: the compute warps stop before it.  Complete the
+                // slot's phase so that its bulk copy can be waited for, then wait for it.
+                record_timeout();
+                if (lane == 0) {
+                    s_final = i;
+                    mbar_arrive(&s_full[b]);
+                }
+                if (u.staged) {
+                    const uint64_t t1 = globaltimer();
+                    while (!mbar_try_wait(&s_full[b], (i / kSlots) & 1))
+                        if (timed_out(t1, a.wait_ns)) break;
+                }
+                break;
+            }
+            const long long c4 = tr ? clock64() : 0;
+            fence_acq_rel_gpu();  // acquire: flags before the compute warps' reads (via full[b])
+            __syncwarp();
+            if (tr && lane == 0) s_tarr[b] = globaltimer();
+            if (lane == 0) mbar_arrive(&s_full[b]);
+            const long long c5 = tr ? clock64() : 0;
+            if (tr && lane == 0) tr_add(9, c5 - c4);
+            slot_busy[b] = true;
+            slot_use[b] = i / kSlots;
+            // prefetch after the hand-over, so that these loads and the atomic complete during
+            // the next units' staging and polls instead of delaying this unit's fence
+            const int u2 = __shfl_sync(0xffffffffu, u_nn, 0);
+            const int r2 = rec_at(u2);
+            int u3 = -1;
+            unsigned int t_next = t;
+            if (lane == 0) {
+                u3 = unit_at(t);                   // id of unit i+3
+                t_next = atomicAdd(a.ticket, 1u);  // ticket of unit i+4, claimed whether or not it exists
+            }
+            u_cur = u_nxt;
+            r_cur = r_nxt;
+            u_nxt = u2;
+            r_nxt = r2;
+            u_nn = u3;
+            t = t_next;
+            if (tr && lane == 0) tr_add(10, clock64() - c5);
+        }
+        if (lane == 0 && s_final < 0) s_final = i;  // units 0..i-1 were handed over
+    } else {
+        // ------------------------------------------------------------------ compute warps
+        const int cw = warp - 1;
+        Prefetch<M> pf;
+        pf.unit = -1;
+        for (int i = 0;; ++i) {
+            const int b = i % kSlots;
+            // Each lane waits for itself; whichever iteration a lane leaves the loop in, every
+            // lane then runs the same phases of the same unit (one __syncwarp each), so the
+            // warp's lanes never hold different units.
+            const uint64_t t0 = globaltimer();
+            bool got = false, stop = false;
+            while (true) {
+                if (mbar_try_wait(&s_full[b], (i / kSlots) & 1)) {
+                    got = true;
+                    break;
+                }
+                const int fin = s_final;
+                if (fin >= 0 && i >= fin) {
+                    stop = true;
+                    break;
+                }
+                if (timed_out(t0, 2 * a.wait_ns + 100000000LL)) break;
+            }
+            if (got) {
+                const int fin = s_final;  // set before the hand-over of an aborted unit
+                if (fin >= 0 && i >= fin) stop = true;
+            }
+            if (stop) break;
+            if (!got) {  // the control warp gave no sign of life: give up
+                if (lane == 0 && atomicExch(a.err, epoch) != epoch) st_relaxed(a.err + 1, (int)MPK_ERR_TIMEOUT);
+                break;
+            }
+            uint64_t t_got = 0;
+            if (tr) {
+                t_got = globaltimer();
+                if (lane == 0) tr_add(4, t_got - t0);
+                if (lane == 0 && cw == 0 && t_got - t0 > 1000) {  // waited: how long after the hand-over
+                    const unsigned long long ta = s_tarr[b];
+                    tr_add(14, t_got > ta ? t_got - ta : 0);
+                    tr_add(15, 1);
+                }
+            }
+            {
+                const long long c0 = tr ? clock64() : 0;
+                phase_a<M>(a, s_u[b], b, kStageCol ? scol0 + b * kStageEntries : a.col + s_u[b].ebase, cw, lane, pf);
+                if (tr) {  // wait for the gathers (integer ops only) to split the unit time
+                    int h = 0;
+#pragma unroll
+                    for (int q = 0; q < Batch<M>::B; ++q) h ^= __double2hiint(pf.x[q][0]);
+                    int d;
+                    asm volatile("add.u32 %0, %1, 0;" : "=r"(d) : "r"(h));
+                    const long long c1 = clock64();
+                    if (lane == 0) tr_add(12, c1 - c0);
+                    phase_b<M, MODE, VT, SH>(a, epoch, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane);
+                    if (lane == 0) tr_add(13, clock64() - c1);
+                } else {
+                    phase_b<M, MODE, VT, SH>(a, epoch, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane);
+                }
+                pf.unit = -1;
+            }
+            if (tr && lane == 0) tr_add(5, globaltimer() - t_got);
+        }
+    }
+    if (tr) {
+        __syncthreads();
+        if (tid == 0) {
+            s_tr[6] = globaltimer() - t_start;
+            s_tr[7] = blockIdx.x == 0;
+            for (int q = 0; q < kTraceShared; ++q) atomicAdd(a.trace + q, s_tr[q]);
+            atomicAdd(a.trace + kTraceShared, (unsigned long long)(clock64() - c_start));
+        }
+    }
+    // ---- exit: the last block resets the ticket and stores the epoch for the next launch
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        const unsigned int done = atomicAdd(a.exit_count, 1u);
+        if (done == gridDim.x - 1) {
+            *a.ticket = 0u;
+            *a.exit_count = 0u;
+            *a.epoch_word = (unsigned int)epoch;
+            __threadfence();
+        }
+    }
+}
+
+
+// ----------------------------------------------------------------------------- shape entry points
+template <int M, int MODE, class VT, int SH> static void *mpk_fn(bool trace) {
+    return trace ? (void *)k_mpk<M, MODE, true, VT, SH> : (void *)k_mpk<M, MODE, false, VT, SH>;
+}
+
+template <class VT, int SH> static void *select_mpk_vs(int mode, int m, bool trace) {
+#define SEL(MM)                                                                 \
+    if (m == MM) {                                                              \
+        if (mode == MODE_POWERS) return mpk_fn<MM, MODE_POWERS, VT, SH>(trace); \
+        return mpk_fn<MM, MODE_CHEB, VT, SH>(trace);                            \
+    }
+    SEL(1) SEL(2) SEL(4) SEL(8)
+#undef SEL
+    fail(MPK_ERR_UNSUPPORTED, "nrhs %d", m);
+}
+
+// k_mpk of block shape SH for (mode, nrhs, trace, value type), and its dynamic shared memory
+template <int SH> void *select_mpk_shape(int mode, int m, bool trace, int vtype) {
+    if (vtype == MPK_F64) return select_mpk_vs<ValF64, SH>(mode, m, trace);
+    if (vtype == MPK_F32) return select_mpk_vs<ValF32, SH>(mode, m, trace);
+    if (vtype == MPK_BF16) return select_mpk_vs<ValBF16, SH>(mode, m, trace);
+    fail(MPK_ERR_UNSUPPORTED, "value type %d", vtype);
+}
+
+template <int SH> int smem_bytes_shape(int vtype) {
+    return vtype == MPK_F64 ? smem_bytes<ValF64, SH>()
+                            : (vtype == MPK_F32 ? smem_bytes<ValF32, SH>() : smem_bytes<ValBF16, SH>());
+}
+
+// defined in mpk_kshape<N>.cu
+void *select_mpk_shape0(int mode, int m, bool trace, int vtype);
+void *select_mpk_shape1(int mode, int m, bool trace, int vtype);
+void *select_mpk_shape2(int mode, int m, bool trace, int vtype);
+
+}  // namespace mpk

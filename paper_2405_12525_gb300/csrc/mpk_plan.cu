@@ -172,12 +172,12 @@ __global__ void k_dep_ranges(int32_t nchunks, const int2 *hull, const int64_t *w
 //  kDepRanges (lo, hi) dependency ranges, slice widths as bytes].  A chunk is staged in
 // shared memory when its entries fit a buffer and its widths fit the record.
 __global__ void k_chunk_records(int32_t nchunks, const int32_t *chunk_row, const int32_t *chunk_slice,
-                                const int64_t *slice_ptr, const int4 *ranges, int32_t *rec) {
+                                const int64_t *slice_ptr, const int4 *ranges, int32_t stage_entries, int32_t *rec) {
     for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nchunks; c += gridDim.x * blockDim.x) {
         const int32_t sl0 = chunk_slice[c], sl1 = chunk_slice[c + 1], nsl = sl1 - sl0;
         const int64_t e0 = slice_ptr[sl0], e1 = slice_ptr[sl1];
         const int32_t cnt = (int32_t)(e1 - e0);
-        const int staged = kStageChunks && cnt > 0 && cnt <= kStageEntries && nsl <= kRecSlices;
+        const int staged = kStageChunks && cnt > 0 && cnt <= stage_entries && nsl <= kRecSlices;
         int32_t *o = rec + (int64_t)kRecInts * c;
         o[0] = chunk_row[c];
         o[1] = chunk_row[c + 1];
@@ -264,8 +264,8 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
     if (!(o->nrhs == 1 || o->nrhs == 2 || o->nrhs == 4 || o->nrhs == 8))
         fail(MPK_ERR_UNSUPPORTED, "nrhs must be 1, 2, 4 or 8 (got %d)", o->nrhs);
     if (o->order != MPK_ORDER_ORIGINAL && o->order != MPK_ORDER_PLAN) fail(MPK_ERR_INVALID, "bad order");
-    const int32_t chunk_rows = o->chunk_rows ? o->chunk_rows : kDefaultChunkRows;
-    if (chunk_rows < 32 || chunk_rows > 8192 || chunk_rows % 32)
+    int32_t chunk_rows = o->chunk_rows;  // 0: 32 rows per compute warp of the block shape
+    if (chunk_rows != 0 && (chunk_rows < 32 || chunk_rows > 8192 || chunk_rows % 32))
         fail(MPK_ERR_INVALID, "chunk_rows must be a multiple of 32 in [32, 8192]");
     if (o->cache_bytes < 0 || o->mem_budget < 0 || o->wait_limit_ns < 0) fail(MPK_ERR_INVALID, "negative option");
     if (L && L->n != A->n) fail(MPK_ERR_INVALID, "levels were built for n = %d, matrix has n = %d", L->n, A->n);
@@ -283,7 +283,7 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         P->order = o->order;
         P->identity = (L == nullptr);
         P->chunk_rows = chunk_rows;
-        P->cache_bytes = o->cache_bytes ? o->cache_bytes : device_l2_bytes();
+        P->cache_bytes = o->cache_bytes ? o->cache_bytes : device_l2_bytes() / 4 * 3;
         P->window = kSlotSkew * pmax + 1;
         P->group_budget = P->cache_bytes / P->window;
         P->wait_ns = o->wait_limit_ns ? o->wait_limit_ns : 2000000000LL;
@@ -397,8 +397,26 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         for (int32_t i = 0; i < NS; ++i) sptr[i + 1] = sptr[i] + 32 * (int64_t)width[i];
         P->padded = sptr[NS];
 
+        // ---- block shape: shape 0 when its slot holds a full chunk of slices of the mean
+        //      width, else shape 1 when its slot holds at least a third of a chunk, else
+        //      unstaged (measured: 27-point stencils run 1.7x faster unstaged, banded graphs
+        //      of ~15 entries a row 10% faster on shape 1)
+        if (o->shape < 0 || o->shape > kNumShapes) fail(MPK_ERR_INVALID, "shape must be in [0, %d]", kNumShapes);
+        if (o->shape > 0) {
+            P->shape = o->shape - 1;
+        } else {
+            auto fits = [&](int sh, int slices) {
+                return (int64_t)slices * P->padded <= (int64_t)kShapes[sh].stage_entries * std::max(NS, 1);
+            };
+            P->shape = fits(0, kShapes[0].comp_warps) ? 0 : (fits(1, kShapes[1].comp_warps / 3) ? 1 : 2);
+        }
+        const int32_t stage_entries = kShapes[P->shape].stage_entries;
+        const int64_t chunk_entries = stage_entries > 0 ? stage_entries : INT64_MAX;
+        if (chunk_rows == 0) chunk_rows = 32 * kShapes[P->shape].comp_warps;
+        P->chunk_rows = chunk_rows;
+
         // ---- chunks: consecutive slices of one group, at most chunk_rows rows and at most
-        //      kStageEntries padded entries (a single wider slice forms its own chunk)
+        //      stage_entries padded entries (a single wider slice forms its own chunk)
         std::vector<int32_t> c_row, c_slice, g_chunk;
         c_row.push_back(0);
         c_slice.push_back(0);
@@ -408,7 +426,7 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
             while (s0 < g_slice[g + 1]) {
                 int32_t s1 = s0 + 1;
                 while (s1 < g_slice[g + 1] && s_row[s1 + 1] - s_row[s0] <= chunk_rows &&
-                       sptr[s1 + 1] - sptr[s0] <= kStageEntries)
+                       sptr[s1 + 1] - sptr[s0] <= chunk_entries)
                     ++s1;
                 c_row.push_back(s_row[s1]);
                 c_slice.push_back(s1);
@@ -503,7 +521,7 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         P->chunk_rec = reinterpret_cast<int4 *>(P->arena.alloc_n<int32_t>((int64_t)kRecInts * (NC > 0 ? NC : 1)));
         if (NC > 0) {
             k_chunk_records<<<grid_n(NC), 256, 0, s>>>(NC, P->chunk_row, P->chunk_slice, P->slice_ptr, P->dep_ranges,
-                                                      reinterpret_cast<int32_t *>(P->chunk_rec));
+                                                      stage_entries, reinterpret_cast<int32_t *>(P->chunk_rec));
             MPK_LAUNCHED();
         }
 

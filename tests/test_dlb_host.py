@@ -211,3 +211,35 @@ def test_gloo_ranks_dlb_phases(tmp_path, world, p_m):
     want = oracle.mpk(A, x, p_m)[:, :, 0]
     scale = np.abs(want).max(axis=1, keepdims=True)
     assert np.all(np.abs(got - want) <= 1e-13 * scale)
+
+
+def test_fig4c_phases_and_order():
+    # The 1-D, two-process case of Fig. 4c: the cells phase ii computes (each row of I_k up to
+    # power k, the bulk up to p_m), the order of phase iii, and the Lp-diagram order inside
+    # phase ii (diagonals of level + power, p ascending, levels counted from the far end)
+    from conftest import read_golden
+    fig = read_golden("fig4c_dlb_order.txt")
+    stage = {(v, p): s for v, p, s in fig}
+    p_m = 3
+    A = gen.laplacian_1d(8)
+    b, probs = _parts(A, 2, balance="rows")
+    pb = probs[0]
+    assert list(pb["halo"]) == [4]
+    d = dlb.boundary_distance(pb)                     # x0..x3 -> 4, 3, 2, 1
+    assert list(d) == [4, 3, 2, 1]
+    cap = np.minimum(d, p_m)
+    phase_ii = {(v, p) for v in range(4) for p in range(1, cap[v] + 1)}
+    assert phase_ii == {c for c, s in stage.items() if 1 <= s <= 9}
+    # phase iii: ("halo", p) -> vertex 4 at power p; ("rows", k, q) -> the vertex at distance k
+    seq = []
+    for st in dlb.phase_iii_steps(int(d.max()) + 1, p_m):
+        if st[0] == "halo":
+            seq.append((4, st[1]))
+        else:
+            seq += [(int(v), st[2]) for v in np.nonzero(d == st[1])[0]]
+    assert seq == sorted((c for c, s in stage.items() if s >= 10), key=lambda c: stage[c])
+    # phase ii in the figure follows the Fig. 2 rule on levels counted from x0
+    level = d.max() - d
+    order = sorted(phase_ii, key=lambda c: (level[c[0]] + c[1], c[1]))
+    assert [stage[c] for c in order] == list(range(1, 10))
+    assert stage[(4, 0)] == 0

@@ -422,3 +422,21 @@ def test_apply_replays_from_cuda_graph(mpk):
         torch.cuda.synchronize()
         P.sync_status()
         _check_powers(Ys, oracle.mpk(A, X, 6)[:, pe, :])
+
+
+@pytest.mark.parametrize("shape", [1, 2, 3])
+@pytest.mark.parametrize("name", ["lap3d_17x9x6", "band_3000", "int_nonsym_500", "xxz_10", "empty_rows"])
+def test_apply_every_block_shape(mpk, shape, name):
+    # the three block shapes of the staged kernel (13 warps with 3072-entry slots, 15 warps
+    # with 4096, 15 warps reading entries from global memory) give the same bits
+    make, sym = MATRICES[name]
+    A = make()
+    dA = _dev(A, mpk, sym)
+    L = mpk.build_levels(dA, 0)
+    X = gen.vector(A.n, 2, stream=98)
+    P = mpk.plan(dA, L, p_max=7, nrhs=2, cache_bytes=30000, shape=shape)
+    Y = P.apply(torch.from_numpy(X).cuda(), 7, Y=_poisoned((8, A.n, 2)))
+    P.sync_status()
+    _check_powers(Y, oracle.mpk(A, X, 7))
+    with pytest.raises(mpk.MpkError):
+        mpk.plan(dA, L, p_max=3, shape=4)
