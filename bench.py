@@ -38,7 +38,9 @@ METRIC = "Level-blocked MPK Gflop/s vs p×CSR SpMV on 1 GB300; serving p50/p99 l
 SM_MAX_MHZ = 2070.0
 NUM_SMS = 152
 DFMA_LANES_PER_CLK_PER_SM = 2  # measured on GB300 (0.60 T FP64 FMA/s at ~1.97 GHz)
-KERNEL_SOURCES = [os.path.join(ROOT, "paper_2405_12525_gb300", "csrc", f) for f in ("mpk_kernel.cu", "mpk_internal.h")]
+# the level-blocked kernel, its tunables and the planner that cuts its chunks
+KERNEL_SOURCES = [os.path.join(ROOT, "paper_2405_12525_gb300", "csrc", f)
+                  for f in ("mpk_kernel_dev.cuh", "mpk_internal.h", "mpk_plan.cu")]
 TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "k_mpk_traffic.json")
 
 

@@ -175,6 +175,9 @@ typedef struct {
     const int32_t *group_row_ptr_dev;   /* num_groups+1 row offsets                        */
     const int32_t *chunk_row_ptr_dev;   /* num_chunks+1 row offsets                        */
     const int32_t *perm_dev;            /* new -> old (NULL: identity)                     */
+    int32_t shape;                /* block shape of the staged engine (0..2, opts.shape - 1) */
+    int32_t engine;               /* MPK_ENGINE_STAGED or MPK_ENGINE_WARP                 */
+    int32_t chunk_rows;           /* rows per chunk limit in effect                      */
 } mpk_plan_desc;
 
 mpk_status mpk_plan_describe(const mpk_plan_t *P, mpk_plan_desc *out);

@@ -67,7 +67,8 @@ class _Desc(C.Structure):
                 ("cache_bytes", C.c_int64),
                 ("device_bytes", C.c_int64), ("padded_entries", C.c_int64),
                 ("group_level_ptr_dev", C.c_void_p), ("group_row_ptr_dev", C.c_void_p),
-                ("chunk_row_ptr_dev", C.c_void_p), ("perm_dev", C.c_void_p)]
+                ("chunk_row_ptr_dev", C.c_void_p), ("perm_dev", C.c_void_p), ("shape", C.c_int32),
+                ("engine", C.c_int32), ("chunk_rows", C.c_int32)]
 
 
 _lib = None

@@ -107,6 +107,9 @@ extern "C" mpk_status mpk_plan_describe(const mpk_plan_t *P, mpk_plan_desc *d) {
     d->group_row_ptr_dev = p.group_row_ptr;
     d->chunk_row_ptr_dev = p.chunk_row;
     d->perm_dev = p.perm;
+    d->shape = p.shape;
+    d->engine = p.engine;
+    d->chunk_rows = p.chunk_rows;
     return MPK_OK;
 }
 

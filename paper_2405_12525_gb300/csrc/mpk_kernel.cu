@@ -20,10 +20,10 @@ namespace mpk {
 // ascending, k ascending inside a line), split into items of kWarpSlices 32-row slices and
 // numbered in that order.  Every warp works alone: warp q of each block claims the items
 // q, q + Q, q + 2Q, ... (Q = kWarpQueues) through the claim counter of queue q, so that any
-// resident block serves every queue; it waits until the cells (g-1, k-1), (g, k-1) and
-// (g+1, k-1) have all their items finished (acquire), computes its slices with the entries
-// read from global memory (L2, where the line order keeps the working set), and adds one
-// to its cell's counter (release).
+// resident block serves every queue; it waits until every chunk its rows read (the chunk's
+// dependency ranges) has all its slices finished at power k-1 (acquire), computes its slice
+// with the entries read from global memory (L2, where the line order keeps the working
+// set), and adds one to its chunk's counter at power k (release).
 // No deadlock: take the smallest claimed, unfinished item m.  Each of its dependencies x < m
 // is finished: a claimed x would be held by a warp with an unfinished item below m, and an
 // unclaimed x of queue q would lie above every item claimed from q, although the queue-q warp

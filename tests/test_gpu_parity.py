@@ -435,8 +435,19 @@ def test_apply_every_block_shape(mpk, shape, name):
     L = mpk.build_levels(dA, 0)
     X = gen.vector(A.n, 2, stream=98)
     P = mpk.plan(dA, L, p_max=7, nrhs=2, cache_bytes=30000, shape=shape)
+    assert P.describe()["shape"] == shape - 1
     Y = P.apply(torch.from_numpy(X).cuda(), 7, Y=_poisoned((8, A.n, 2)))
     P.sync_status()
     _check_powers(Y, oracle.mpk(A, X, 7))
     with pytest.raises(mpk.MpkError):
         mpk.plan(dA, L, p_max=3, shape=4)
+
+
+def test_automatic_block_shape(mpk):
+    # rows of 7 entries fill a 3072-entry slot with 13 slices (shape 0); 13-15 entries a row
+    # fill a 4096-entry slot with at least 5 (shape 1); 27-point rows go unstaged (shape 2)
+    for A, want in ((gen.laplacian_3d(30, 30, 30), 0), (gen.xxz_chain(12, stream=99), 1), (gen.stencil27(40), 2)):
+        dA = _dev(A, mpk, True)
+        P = mpk.plan(dA, mpk.build_levels(dA, 0), p_max=4)
+        d = P.describe()
+        assert d["shape"] == want and d["engine"] == 0 and d["chunk_rows"] == 32 * (13 if want == 0 else 15)
