@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kWarpBS, (WarpOcc<M, MODE, VT>::blocks)) k_mpk
             }
         }
         __syncwarp();
-        if (lane == 0) {
+        if (lane == 0 && ((c << 5) | k) != a.drop_unit) {  // test hook: a chunk that never completes
             fence_acq_rel_gpu();  // release: this warp's rows before the count
             atomicAdd(a.w_cnt + (int64_t)k * a.nchunks + c, 1);
         }
@@ -398,7 +398,7 @@ static int occupancy_grid_w(int mode, int m, int vtype) {
 }
 
 void launch_mpk(const Plan &P, KArgs &a, int mode, cudaStream_t s) {
-    if (a.w_item != nullptr && a.trace == nullptr && a.drop_unit < 0) {  // warp engine
+    if (a.w_item != nullptr && a.trace == nullptr) {  // warp engine
         if (a.w_nitems <= 0) return;
         MPK_CUDA(cudaMemsetAsync(a.w_cnt, 0,
                                  sizeof(int32_t) * ((size_t)(P.p_max + 1) * std::max(P.num_chunks, 1) + kWarpQueues),

@@ -160,3 +160,21 @@ def test_warp_engine_rejected_for_batch_and_bad_value(mpk):
     o = mpk._Opts()
     lib.mpk_plan_opts_default(C.byref(o))
     assert o.engine == mpk.ENGINE_STAGED
+
+
+def test_warp_timeout_is_reported_and_plan_recovers(mpk):
+    # one chunk never counts its slices at power 1: every warp waiting on it gives up after the
+    # plan's wait limit, the launch ends with MPK_ERR_TIMEOUT, and the next launch is unaffected
+    A = gen.laplacian_3d(16, 16, 16)
+    dA = _dev(A, mpk, True)
+    P = mpk.plan(dA, mpk.build_levels(dA, 0), p_max=4, cache_bytes=20000, wait_limit_ns=20_000_000,
+                 engine=mpk.ENGINE_WARP)
+    X = torch.from_numpy(gen.vector(A.n, 1, stream=86)).cuda()
+    P.debug_drop_release(chunk=3, k=1)
+    P.apply(X, 4)
+    with pytest.raises(mpk.MpkError) as e:
+        P.sync_status()
+    assert e.value.status == 4
+    Y = P.apply(X, 4)
+    P.sync_status()
+    _check_powers(Y, oracle.mpk(A, X.cpu().numpy(), 4))
