@@ -287,11 +287,30 @@ def main_cheb(args):
     t0 = time.perf_counter()
     P = mpk.plan(dA, L, p_max=p, nrhs=m, order=mpk.ORDER_PLAN)
     t_plan = time.perf_counter() - t0
-    desc = P.describe()
     perm = L.perm.long()
     psi_p = torch.from_numpy(psi).cuda()[perm].contiguous()   # state in the plan's numbering
     out = torch.empty_like(psi_p)
     cr, ci = coef.real.copy(), coef.imag.copy()
+    # engine choice by timing (the autotuner's rule): level-blocked staged kernel or the
+    # unblocked sweep, whose results are the same bits
+    tune = {}
+    plans = {"staged": P, "sweep": mpk.plan(dA, L, p_max=p, nrhs=m, order=mpk.ORDER_PLAN, engine=mpk.ENGINE_SWEEP)}
+    for name, Pc in plans.items():
+        for _ in range(2):
+            Pc.cheb_filter(psi_p, deg, cr, ci, scale=a, shift=c, out=out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(3):
+            Pc.cheb_filter(psi_p, deg, cr, ci, scale=a, shift=c, out=out)
+        e1.record(stream)
+        e1.synchronize()
+        Pc.sync_status()
+        tune[name + "_ms"] = e0.elapsed_time(e1) / 3
+    chosen = min(plans, key=lambda k: tune[k + "_ms"])
+    tune["chosen"] = chosen
+    P = plans[chosen]
+    desc = P.describe()
 
     def step():
         P.cheb_filter(psi_p, deg, cr, ci, scale=a, shift=c, out=out)
@@ -364,15 +383,17 @@ def main_cheb(args):
                        "levels": desc["num_levels"], "groups": desc["num_groups"], "chunks": desc["num_chunks"]},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
                          "frac": achieved / peak_alu, "traffic": None,
-                         "kernel": "k_mpk<2,1> (recurrence mode), 8 launches per step",
+                         "kernel": ("k_mpk<2,1> (recurrence mode), 8 launches per step" if chosen == "staged" else
+                                    "k_sweep<2,1> (recurrence mode, unblocked), 64 launches per step"),
                          "algorithmic": "per recurrence step 2 nnz m (SpMV) + 8 n m (update, complex accumulate)"},
             "comparator": {"plain_spmv_same_count_ms": ms_spmv,
                            "note": f"{deg} plain SpMVs of the 2 RHS without the recurrence (lower bound of an unblocked "
                                    f"step)", "speedup_vs_plain_spmv": ms_spmv / ms},
             "unitarity": {"norm_ratio": norm_ratio},
+            "engine_choice": tune,
             "preprocess": {"levels_ms": t_levels * 1e3, "plan_ms": t_plan * 1e3},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
-            "gpu_launches": args.steps * (1 + (deg + p - 1) // p),
+            "gpu_launches": args.steps * (1 + ((deg + p - 1) // p if chosen == "staged" else deg)),
         }
         print(json.dumps(line), flush=True)
     if dist:
@@ -773,6 +794,11 @@ def main():
     ms_plain_nat = timed(lambda: P0.spmv_powers(Xd, p, Y=Y2), max(3, args.steps // 4), 2)
     ms_plain_bfs = timed(lambda: P.spmv_powers(Xp, p, Y=Y2), max(3, args.steps // 4), 2)
     identical = bool(torch.equal(Y, Y2))   # level-blocked == back-to-back SpMV, bit for bit
+    # ---- comparator: the unblocked sweep engine (one grid-stride launch per power, same row body)
+    Ps = mpk.plan(dA, L, p_max=p, nrhs=1, order=mpk.ORDER_PLAN, engine=mpk.ENGINE_SWEEP)
+    ms_sweep = timed(lambda: Ps.apply(Xp, p, Y=Y2), max(3, args.steps // 4), 2)
+    identical = identical and bool(torch.equal(Y, Y2))
+    del Ps
     # ---- comparator: plain p x CSR SpMV of the vendor library (cuSPARSE through torch's sparse
     #      CSR matmul), natural order, on the unpermuted CSR arrays
     csr = None
@@ -822,7 +848,7 @@ def main():
 
     peak_alu = NUM_SMS * DFMA_LANES_PER_CLK_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s
     achieved = flops / (ms * 1e-3) / 1e12
-    best_plain = min(ms_plain_nat, ms_plain_bfs)
+    best_plain = min(ms_plain_nat, ms_plain_bfs, ms_sweep)
     clocks = clk.summary()
     if rank == 0:
         line = {
@@ -848,11 +874,14 @@ def main():
                                "bit_identical_to_plan_order": orig_identical},
             "comparator": {"plain_spmv_natural_gflops": flops / (ms_plain_nat * 1e-3) / 1e9,
                            "plain_spmv_bfs_gflops": flops / (ms_plain_bfs * 1e-3) / 1e9,
+                           "unblocked_sweep_gflops": flops / (ms_sweep * 1e-3) / 1e9,
                            "speedup_vs_best_plain": best_plain / ms,
                            "speedup_original_order_vs_best_plain": best_plain / ms_orig,
                            "plain_hbm_gbs": p * (a_bytes + 2 * v_bytes) / (best_plain * 1e-3) / 1e9,
                            "bit_identical_to_plain": identical,
-                           "plain_spmv_note": "plain_* use this library's sliced (SELL-32) copy, grid-stride kernel",
+                           "plain_spmv_note": "plain_* and unblocked_sweep use this library's sliced (SELL-32) copy; "
+                                              "the sweep is the plan's unblocked engine (one launch per power, "
+                                              "the level-blocked kernel's row body); best_plain is the fastest",
                            "vendor_csr": csr},
             "preprocess": {"levels_ms": t_levels * 1e3, "plan_ms": t_plan * 1e3,
                            "spmv_equivalents": (t_levels + t_plan) * 1e3 / (best_plain / p)},

@@ -29,7 +29,7 @@ MPK_OK, MPK_ERR_INVALID, MPK_ERR_TOO_LARGE, MPK_ERR_OOM, MPK_ERR_TIMEOUT = 0, 1,
 MPK_ERR_CUDA, MPK_ERR_BUDGET, MPK_ERR_UNSUPPORTED = 5, 6, 7
 MPK_F64, MPK_F32, MPK_BF16 = 0, 1, 2
 ORDER_ORIGINAL, ORDER_PLAN = 0, 1
-ENGINE_STAGED, ENGINE_WARP = 0, 1
+ENGINE_STAGED, ENGINE_WARP, ENGINE_SWEEP = 0, 1, 2
 
 EXPORTED_SYMBOLS = [
     "mpk_build_levels", "mpk_levels_get", "mpk_levels_destroy", "mpk_plan_opts_default", "mpk_plan",

@@ -1,4 +1,5 @@
-"""Autotuner for plan parameters: the group budget C (cache_bytes) and the rows per chunk.
+"""Autotuner for plan parameters: the group budget C (cache_bytes), the rows per chunk and,
+for single plans, the unblocked sweep engine as one more candidate.
 
 The paper studies p and C by hand (Sec. 6, the p x C parameter scan); here each candidate
 plan is built, timed on the device with CUDA events over a few applies of the caller's
@@ -8,7 +9,7 @@ from __future__ import annotations
 
 import itertools
 
-from . import ORDER_PLAN, batch_plan, device_info, plan
+from . import ENGINE_SWEEP, ORDER_PLAN, batch_plan, device_info, plan
 
 
 def _time(fn, reps: int):
@@ -45,6 +46,13 @@ def tune_plan(dA, levels, p: int, X, nrhs: int = 1, order: int = ORDER_PLAN, can
             best = (ms, P)
         else:
             del P
+    if cands.get("sweep", True):  # no level blocking: pays when the levels are too bulky
+        P = plan(dA, levels, p_max=p, nrhs=nrhs, order=order, engine=ENGINE_SWEEP)
+        ms = _time(lambda: P.apply(X, p, Y=Y), reps)
+        P.sync_status()
+        report.append((ms, {"engine": "sweep"}))
+        if ms < best[0]:
+            best = (ms, P)
     return best[1], sorted(report, key=lambda t: t[0])
 
 

@@ -169,6 +169,7 @@ KArgs mpk::base_args(Plan &P, int32_t p) {
     a.trace = P.trace;
     P.drop_unit = -1;
     a.ystride = (int64_t)P.n * P.m;
+    a.p_launch = p;
     if (P.engine == MPK_ENGINE_WARP) {
         a.w_item = P.w_item + P.w_cell_off[p];
         a.w_gk = P.w_gk + P.w_cell_off[p];

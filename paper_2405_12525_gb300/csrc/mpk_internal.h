@@ -228,6 +228,7 @@ struct KArgs {
     const int32_t *w_slice_chunk;  // chunk of every slice
     const int32_t *w_chunk_nsl;    // slices of every chunk
     int32_t ngroups;
+    int32_t p_launch;              // powers of this launch (local 1..p_launch)
 };
 // warp-ticketed engine: slices per item, claim queues (one per warp of a block)
 constexpr int kWarpSlices = 1;

@@ -145,17 +145,64 @@ __global__ void __launch_bounds__(kWarpBS, (WarpOcc<M, MODE, VT>::blocks)) k_mpk
     }
 }
 
+// ----------------------------------------------------------------------------- sweep engine
+// One power k of the whole matrix, unblocked: blocks walk the plan's chunks, warps their
+// slices, with the level-blocked kernel's row body and epilogue (plain powers or the
+// Chebyshev recurrence), so the results are the same bits.  One launch per power; stream
+// order supplies every dependency.
+template <int M, int MODE, class VT>
+__global__ void __launch_bounds__(kSpmvBS) k_sweep(const KArgs a, int k) {
+    const int lane = threadIdx.x & 31;
+    const auto *val = static_cast<const typename VT::T *>(a.val);
+    const double *xin = input_block<M>(a, k);
+    for (int c = blockIdx.x; c < a.nchunks; c += gridDim.x) {
+        const int r0 = a.chunk_row[c], r1 = a.chunk_row[c + 1], sl0 = a.chunk_slice[c];
+        const int nsl = (r1 - r0 + 31) >> 5;
+        for (int sl = threadIdx.x >> 5; sl < nsl; sl += kSpmvBS / 32) {
+            const int64_t r = (int64_t)r0 + 32 * sl + lane;
+            if (r < r1) {
+                const int64_t e0 = a.slice_ptr[sl0 + sl], e1 = a.slice_ptr[sl0 + sl + 1];
+                double w[M];
+                row_sum<M, Batch<M>::B>(GVal<VT>{val}, GCol{a.col}, e0 + lane, (int)((e1 - e0) >> 5), xin, w);
+                row_epilogue<M, MODE>(a, k, r, w, xin);
+                if (k == 1 && a.y0copy) {
+#pragma unroll
+                    for (int i = 0; i < M; ++i) a.y0copy[r * M + i] = a.x0[r * M + i];
+                }
+            }
+        }
+    }
+}
+
+template <class VT> static void *select_sweep_vt(int mode, int m) {
+#define SEL(MM)                                                                                \
+    if (m == MM) return mode == MODE_POWERS ? (void *)k_sweep<MM, MODE_POWERS, VT> : (void *)k_sweep<MM, MODE_CHEB, VT>;
+    SEL(1) SEL(2) SEL(4) SEL(8)
+#undef SEL
+    fail(MPK_ERR_UNSUPPORTED, "nrhs %d", m);
+}
+
+static void *select_sweep(int mode, int m, int vtype) {
+    if (vtype == MPK_F64) return select_sweep_vt<ValF64>(mode, m);
+    if (vtype == MPK_F32) return select_sweep_vt<ValF32>(mode, m);
+    if (vtype == MPK_BF16) return select_sweep_vt<ValBF16>(mode, m);
+    fail(MPK_ERR_UNSUPPORTED, "value type %d", vtype);
+}
+
 // ----------------------------------------------------------------------------- K-SpMV
 // SpMV restricted to row ranges of one or several plans (plan order), one launch: segment
 // q covers the plan-order rows [lo, hi) of its plan, whose chunks c0 .. c0+nch-1 overlap
 // them; virtual block v belongs to the segment q with first[q] <= v < first[q+1].
-template <int M, class VT>
+// SINGLE: one segment, read with constant offsets (a parameter indexed by a run-time value
+// is copied to local memory first).
+template <int M, class VT, bool SINGLE>
 __global__ void __launch_bounds__(kSpmvBS) k_spmv_rows(const RowSegs segs) {
     const int lane = threadIdx.x & 31;
-    for (int v = blockIdx.x; v < segs.first[segs.count]; v += gridDim.x) {
+    for (int v = blockIdx.x; v < segs.first[SINGLE ? 1 : segs.count]; v += gridDim.x) {
         int q = 0;
-        while (v >= segs.first[q + 1]) ++q;
-        const RowSeg &g = segs.seg[q];
+        if (!SINGLE)
+            while (v >= segs.first[q + 1]) ++q;
+        const RowSeg &g = segs.seg[SINGLE ? 0 : q];
         const auto *val = static_cast<const typename VT::T *>(g.val);
         const int c = g.c0 + (v - segs.first[q]);
         const int r0 = g.chunk_row[c], r1 = g.chunk_row[c + 1], sl0 = g.chunk_slice[c];
@@ -176,9 +223,12 @@ __global__ void __launch_bounds__(kSpmvBS) k_spmv_rows(const RowSegs segs) {
 template <class VT>
 static void launch_spmv_rows_vt(const RowSegs &segs, int m, cudaStream_t s) {
     const int grid = std::min(segs.first[segs.count], 64 * device_sms());
-#define L(MM)                                                 \
-    case MM:                                                  \
-        k_spmv_rows<MM, VT><<<grid, kSpmvBS, 0, s>>>(segs);   \
+#define L(MM)                                                                      \
+    case MM:                                                                       \
+        if (segs.count == 1)                                                       \
+            k_spmv_rows<MM, VT, true><<<grid, kSpmvBS, 0, s>>>(segs);              \
+        else                                                                       \
+            k_spmv_rows<MM, VT, false><<<grid, kSpmvBS, 0, s>>>(segs);             \
         break;
     switch (m) {
         L(1) L(2) L(4) L(8) default : fail(MPK_ERR_UNSUPPORTED, "nrhs %d", m);
@@ -398,6 +448,16 @@ static int occupancy_grid_w(int mode, int m, int vtype) {
 }
 
 void launch_mpk(const Plan &P, KArgs &a, int mode, cudaStream_t s) {
+    if (P.engine == MPK_ENGINE_SWEEP && a.trace == nullptr && a.drop_unit < 0 && a.w_item == nullptr) {
+        if (P.num_chunks <= 0) return;
+        void *fn = select_sweep(mode, P.m, P.val_type);
+        const int grid = std::min(P.num_chunks, 64 * device_sms());
+        for (int k = 1; k <= a.p_launch; ++k) {
+            void *args[] = {&a, &k};
+            MPK_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(kSpmvBS), args, 0, s));
+        }
+        return;
+    }
     if (a.w_item != nullptr && a.trace == nullptr) {  // warp engine
         if (a.w_nitems <= 0) return;
         MPK_CUDA(cudaMemsetAsync(a.w_cnt, 0,

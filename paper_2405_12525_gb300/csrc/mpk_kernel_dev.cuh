@@ -318,7 +318,7 @@ __device__ __forceinline__ const double *input_block(const KArgs &a, int k) {
 }
 
 // phase A: request the x values of the warp's first batch of unit u (slot b)
-template <int M>
+template <int M, bool STAGING>
 __device__ __forceinline__ void phase_a(const KArgs &a, const UnitInfo &u, int b, const int32_t *scol, int cwarp,
                                         int lane, Prefetch<M> &pf) {
     constexpr int B = Batch<M>::B;
@@ -328,7 +328,7 @@ __device__ __forceinline__ void phase_a(const KArgs &a, const UnitInfo &u, int b
     pf.r = -1;
     pf.width = 0;
     pf.off = 0;
-    if (u.staged && cwarp < u.nsl) {
+    if (STAGING && u.staged && cwarp < u.nsl) {  // shapes without slots never stage
         int pre = 0;
 #pragma unroll
         for (int q = 0; q < kRecSlices; ++q) pre += (q < cwarp) ? slice_width(u.widths, q) : 0;
@@ -357,7 +357,7 @@ __device__ __forceinline__ void phase_b(const KArgs &a, int32_t epoch, const Pre
     constexpr int kCompWarps = Shape<SH>::CW;
     const SVal<VT> sval{sval0 + pf.slot * Shape<SH>::SE};
     const int32_t *scol = kStageCol ? scol0 + pf.slot * Shape<SH>::SE : a.col + u.ebase;
-    if (u.staged) {
+    if (Shape<SH>::SE > 0 && u.staged) {
         if (pf.r >= 0) {  // first slice: prefetched first batch, then the rest of the row
             double w[M];
 #pragma unroll
@@ -695,7 +695,8 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
             }
             {
                 const long long c0 = tr ? clock64() : 0;
-                phase_a<M>(a, s_u[b], b, kStageCol ? scol0 + b * kStageEntries : a.col + s_u[b].ebase, cw, lane, pf);
+                phase_a<M, (kStageEntries > 0)>(a, s_u[b], b, kStageCol ? scol0 + b * kStageEntries : a.col + s_u[b].ebase,
+                                                 cw, lane, pf);
                 if (tr) {  // wait for the gathers (integer ops only) to split the unit time
                     int h = 0;
 #pragma unroll

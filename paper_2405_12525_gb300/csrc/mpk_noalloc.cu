@@ -98,6 +98,7 @@ extern "C" mpk_status mpk_apply_noalloc(const mpk_plan_t *Ph, const double *X, i
             a.ybase = Y;
             a.ystride = (int64_t)P.n * P.m;
             a.ring = p + 1;
+            a.p_launch = p;
             a.y0copy = (Y != X) ? Y : nullptr;
             if (a.y0copy && P.level0_rows > 0)  // level 0 of a level-capped plan has no units
                 MPK_CUDA(cudaMemcpyAsync(Y, X, sizeof(double) * (size_t)P.level0_rows * P.m,

@@ -572,8 +572,12 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
 
         // ---- warp-ticketed engine: the same cells in the same order, split into items of
         //      kWarpSlices slices; counters of finished items per cell
-        if (o->engine != MPK_ENGINE_STAGED && o->engine != MPK_ENGINE_WARP)
-            fail(MPK_ERR_INVALID, "engine must be MPK_ENGINE_STAGED or MPK_ENGINE_WARP");
+        if (o->engine != MPK_ENGINE_STAGED && o->engine != MPK_ENGINE_WARP && o->engine != MPK_ENGINE_SWEEP)
+            fail(MPK_ERR_INVALID, "engine must be MPK_ENGINE_STAGED, MPK_ENGINE_WARP or MPK_ENGINE_SWEEP");
+        if (o->engine == MPK_ENGINE_SWEEP) {
+            if (batch || P->level_capped) fail(MPK_ERR_INVALID, "batch and level-capped plans need level blocking");
+            P->engine = MPK_ENGINE_SWEEP;
+        }
         if (o->engine == MPK_ENGINE_WARP) {
             if (batch) fail(MPK_ERR_INVALID, "batch plans run on the staged engine");
             P->engine = MPK_ENGINE_WARP;

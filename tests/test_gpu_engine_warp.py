@@ -178,3 +178,74 @@ def test_warp_timeout_is_reported_and_plan_recovers(mpk):
     Y = P.apply(X, 4)
     P.sync_status()
     _check_powers(Y, oracle.mpk(A, X.cpu().numpy(), 4))
+
+
+# ----------------------------------------------------------------------------- sweep engine
+@pytest.mark.parametrize("name", sorted(MATRICES))
+@pytest.mark.parametrize("order", [0, 1])
+def test_sweep_apply_bit_exact(mpk, name, order):
+    make, sym = MATRICES[name]
+    A = make()
+    dA = _dev(A, mpk, sym)
+    L = mpk.build_levels(dA, 0)
+    P = mpk.plan(dA, L, p_max=6, nrhs=2, cache_bytes=20000, order=order, engine=mpk.ENGINE_SWEEP)
+    assert P.describe()["engine"] == mpk.ENGINE_SWEEP
+    X = gen.vector(A.n, 2, stream=81)
+    _, pe, ip, _ = oracle.levels(A, 0)
+    Yo = oracle.mpk(A, X, 6)
+    if order == 1:
+        Yo = Yo[:, pe, :]
+    Xin = torch.from_numpy(np.ascontiguousarray(X if order == 0 else X[pe])).cuda()
+    for p in (1, 4, 6):
+        Y = P.apply(Xin, p, Y=_poisoned((p + 1, A.n, 2)))
+        P.sync_status()
+        _check_powers(Y, Yo[: p + 1])
+    if order == 1:
+        Y = _poisoned((7, A.n, 2))
+        P.apply_noalloc(Xin, 6, Y)
+        _check_powers(Y, Yo)
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_sweep_cheb_bit_exact(mpk, order):
+    A = gen.xxz_chain(12, stream=87)
+    dA = _dev(A, mpk, True)
+    lo, hi = gen.gershgorin_bounds(A)
+    scale, shift = (hi - lo) / 2 * 1.01, (hi + lo) / 2
+    P = mpk.plan(dA, mpk.build_levels(dA, 0), p_max=8, nrhs=2, order=order, engine=mpk.ENGINE_SWEEP)
+    X = gen.vector(A.n, 2, stream=88)
+    _, pe, ip, _ = oracle.levels(A, 0)
+    Xin = torch.from_numpy(np.ascontiguousarray(X if order == 0 else X[pe])).cuda()
+    cr = gen.uniform(gen.derive_seed(96), 21)
+    ci = gen.uniform(gen.derive_seed(95), 21)
+    for im in (None, ci):
+        want = oracle.cheb(A, X, 20, cr, im, scale=scale, shift=shift)
+        got = P.cheb_filter(Xin, 20, cr, im, scale=scale, shift=shift).cpu().numpy()
+        P.sync_status()
+        if order == 1:
+            got = got[ip]
+        assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+
+
+def test_sweep_engine_rejected_for_level_capped(mpk):
+    A = gen.laplacian_2d(20, 20)
+    dA = _dev(A, mpk, True)
+    L = mpk.build_levels_from(dA, [0, 7])
+    with pytest.raises(mpk.MpkError):
+        mpk.plan(dA, L, p_max=3, order=mpk.ORDER_PLAN, level_capped=True, engine=mpk.ENGINE_SWEEP)
+
+
+def test_autotuner_plan_candidates(mpk):
+    from paper_2405_12525_gb300 import autotune
+    A = gen.laplacian_3d(24, 20, 18)
+    dA = _dev(A, mpk, True)
+    L = mpk.build_levels(dA, 0)
+    pe = L.perm.cpu().numpy()
+    X = gen.vector(A.n, 1, stream=97)
+    Xp = torch.from_numpy(np.ascontiguousarray(X[pe])).cuda()
+    P, report = autotune.tune_plan(dA, L, 5, Xp, candidates={"cache_bytes": [100000, 1 << 22], "chunk_rows": [0]})
+    assert len(report) == 3 and any(opts.get("engine") == "sweep" for _, opts in report)
+    assert all(report[i][0] <= report[i + 1][0] for i in range(len(report) - 1))
+    Y = P.apply(Xp, 5, Y=_poisoned((6, A.n, 1)))
+    P.sync_status()
+    _check_powers(Y, oracle.mpk(A, X, 5)[:, pe, :])
