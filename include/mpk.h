@@ -43,7 +43,7 @@ typedef enum {
     MPK_ERR_TIMEOUT = 4,     /* a bounded device wait expired; results of that call are void */
     MPK_ERR_CUDA = 5,        /* a CUDA runtime call failed */
     MPK_ERR_BUDGET = 6,      /* the plan would exceed mpk_plan_opts.mem_budget */
-    MPK_ERR_UNSUPPORTED = 7  /* valid request this build does not implement (e.g. nrhs) */
+    MPK_ERR_UNSUPPORTED = 7  /* valid request the library does not implement (e.g. nrhs 3)  */
 } mpk_status;
 
 typedef enum { MPK_F64 = 0, MPK_F32 = 1, MPK_BF16 = 2 } mpk_dtype;
@@ -151,8 +151,13 @@ typedef struct {
  *                     the entries from global memory (L2) and waits for whole cells (group,
  *                     power k-1) of the three neighbouring groups; no shared memory, full
  *                     occupancy.  Not for batch plans (MPK_ERR_INVALID); mpk_apply_noalloc
- *                     runs such a plan with the staged engine. */
-enum { MPK_ENGINE_STAGED = 0, MPK_ENGINE_WARP = 1 };
+ *                     runs such a plan with the staged engine.
+ *  MPK_ENGINE_SWEEP   no level blocking: one grid-stride launch per power over the plan's
+ *                     sliced copy, with the same row body and the same epilogue (powers or
+ *                     Chebyshev recurrence), for matrices whose levels are too bulky for the
+ *                     cache budget to give any reuse.  Not for batch or level-capped plans
+ *                     (MPK_ERR_INVALID). */
+enum { MPK_ENGINE_STAGED = 0, MPK_ENGINE_WARP = 1, MPK_ENGINE_SWEEP = 2 };
 
 /* Fills the defaults described above (p_max = 8, nrhs = 1, order = ORIGINAL). */
 void mpk_plan_opts_default(mpk_plan_opts *o);
