@@ -141,6 +141,9 @@ typedef struct {
                                row width; 1 = 13 compute warps, 3072-entry slots, 3 blocks
                                per SM (rows up to ~7 entries); 2 = 15 warps, 4096 entries,
                                2 blocks; 3 = 15 warps, entries read from global memory      */
+    int64_t shuffle_seed;   /* race-detection aid: non-zero permutes the staged engine's work
+                               units inside every line of the schedule (a valid order whose
+                               results must be the same bits); 0 = the natural order         */
 } mpk_plan_opts;
 
 /* Engines of the level-blocked kernel (same results bit for bit, same Lp-diagram order):

@@ -559,14 +559,29 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         std::vector<int32_t> g_cap((size_t)G, pmax);
         if (P->level_capped)
             for (int32_t g = 0; g < G; ++g) g_cap[g] = std::min(pmax, g_level[g]);
+        // race-detection aid: shuffle_seed != 0 permutes the units of every line (all their
+        // dependencies lie on earlier lines, so any order inside a line is a valid schedule and
+        // must give the same bits); splitmix64 drives a Fisher-Yates shuffle
+        uint64_t rng = (uint64_t)o->shuffle_seed;
+        auto next_rand = [&rng]() {
+            uint64_t z = (rng += 0x9e3779b97f4a7c15ULL);
+            z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ULL;
+            z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
+            return z ^ (z >> 31);
+        };
         for (int32_t p = 1; p <= pmax && !batch; ++p) {
             P->unit_off[p] = (int64_t)units.size();
-            for (int32_t d = kSlotSkew; d <= G - 1 + kSlotSkew * p; ++d)
+            for (int32_t d = kSlotSkew; d <= G - 1 + kSlotSkew * p; ++d) {
+                const size_t line0 = units.size();
                 for (int32_t k = 1; k <= p; ++k) {
                     const int32_t g = d - kSlotSkew * k;
                     if (g < 0 || g >= G || k > g_cap[g]) continue;
                     for (int32_t c = g_chunk[g]; c < g_chunk[g + 1]; ++c) units.push_back((c << 5) | k);
                 }
+                if (o->shuffle_seed != 0)
+                    for (size_t j = units.size() - 1; j > line0; --j)
+                        std::swap(units[j], units[line0 + next_rand() % (j - line0 + 1)]);
+            }
         }
         if (!batch) P->unit_off[pmax + 1] = (int64_t)units.size();
 

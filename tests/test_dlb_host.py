@@ -243,3 +243,43 @@ def test_fig4c_phases_and_order():
     order = sorted(phase_ii, key=lambda c: (level[c[0]] + c[1], c[1]))
     assert [stage[c] for c in order] == list(range(1, 10))
     assert stage[(4, 0)] == 0
+
+
+def _failing_rank_main(rank, world, port, out):
+    import datetime
+    import torch
+    import torch.distributed as dist
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world,
+                            timeout=datetime.timedelta(seconds=20))
+    A = gen.banded_random(300, stream=36, per_row=5, band_frac=0.02)
+    b = dlb.partition_rows(A.n, world, A.row_ptr)
+    probs = [dlb.local_problem(A.row_ptr, A.col, A.val, int(b[i]), int(b[i + 1]), b) for i in range(world)]
+    pb = probs[rank]
+    sends = dlb.send_lists(probs)
+    peer = 1 - rank
+    n_in = int(np.sum(pb["owner"] == peer))
+    n_out = int(sends[rank][peer].size)
+    # the first exchange completes on both ranks
+    w = dist.isend(torch.zeros(n_out, dtype=torch.float64), dst=peer)
+    dist.recv(torch.empty(n_in, dtype=torch.float64), src=peer)
+    w.wait()
+    if rank == 1:
+        os._exit(0)  # this rank fails between two exchanges: it never sends again
+    # rank 0 learns of it from a bounded wait on the next halo message, not a hang
+    try:
+        r = dist.irecv(torch.empty(n_in, dtype=torch.float64), src=peer)
+        r.wait(timeout=datetime.timedelta(seconds=2))
+        result = "no error"
+    except Exception as e:  # noqa: BLE001 - any error is the detection
+        result = "detected " + type(e).__name__
+    with open(out, "w") as f:
+        f.write(result)
+    os._exit(0)
+
+
+def test_gloo_rank_failure_is_detected(tmp_path):
+    mp = pytest.importorskip("torch.multiprocessing")
+    out = str(tmp_path / "result.txt")
+    mp.start_processes(_failing_rank_main, args=(2, _free_port(), out), nprocs=2, start_method="spawn")
+    with open(out) as f:
+        assert f.read().startswith("detected")

@@ -451,3 +451,27 @@ def test_automatic_block_shape(mpk):
         P = mpk.plan(dA, mpk.build_levels(dA, 0), p_max=4)
         d = P.describe()
         assert d["shape"] == want and d["engine"] == 0 and d["chunk_rows"] == 32 * (13 if want == 0 else 15)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 0x5EED])
+@pytest.mark.parametrize("name", ["lap3d_17x9x6", "band_3000", "int_nonsym_500", "disconnected", "xxz_10"])
+def test_shuffled_schedules_give_the_same_bits(mpk, seed, name):
+    # race-detection aid: the units of every schedule line in a seeded random order; any
+    # dependency that a unit did not wait for would show up as a different bit or a NaN
+    make, sym = MATRICES[name]
+    A = make()
+    dA = _dev(A, mpk, sym)
+    L = mpk.build_levels(dA, 0)
+    X = gen.vector(A.n, 2, stream=99)
+    P = mpk.plan(dA, L, p_max=7, nrhs=2, cache_bytes=20000, chunk_rows=32, shuffle_seed=seed)
+    Y = P.apply(torch.from_numpy(X).cuda(), 7, Y=_poisoned((8, A.n, 2)))
+    P.sync_status()
+    _check_powers(Y, oracle.mpk(A, X, 7))
+    if A.n > 1:
+        lo, hi = gen.gershgorin_bounds(A)
+        c = gen.uniform(gen.derive_seed(100), 12)
+        got = P.cheb_filter(torch.from_numpy(X).cuda(), 11, c, scale=(hi - lo) / 2 * 1.01 + 1e-3,
+                            shift=(hi + lo) / 2).cpu().numpy()
+        P.sync_status()
+        want = oracle.cheb(A, X, 11, c, scale=(hi - lo) / 2 * 1.01 + 1e-3, shift=(hi + lo) / 2)
+        assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
