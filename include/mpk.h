@@ -249,6 +249,27 @@ mpk_status mpk_cheb_filter(const mpk_plan_t *P, const double *X, int32_t degree,
                            const double *coeff_re, const double *coeff_im, double scale,
                            double shift, double *out, mpk_stream stream);
 
+/* The same filter in pieces, with its state in a caller-owned device buffer that can be saved
+ * and restored between pieces (checkpoint/resume at any step; the natural point is a block
+ * boundary of p_max steps): the ring (v_{k-1}, v_k) and the accumulator, 4 x n x nrhs float64
+ * in the plan's row order, mpk_cheb_state_bytes(P) bytes.  Any split of the steps gives the
+ * same bits as one mpk_cheb_filter call.
+ *   mpk_cheb_begin:   state <- v_0 = X, acc = c_0 X (c_0 = c0_re + i c0_im on (re, im) column
+ *                     pairs when complex_coeff is 1); the state holds step 0.
+ *   mpk_cheb_advance: steps k_begin+1 .. k_end with coefficients coeff_re[k] (and coeff_im[k]),
+ *                     k absolute; k_begin must be the step the state holds (the caller tracks
+ *                     it); launches of at most p_max steps.
+ *   mpk_cheb_finish:  out <- acc (in the numbering opts.order selects).
+ * Arguments, errors and streams otherwise as for mpk_cheb_filter.  mpk_cheb_state_bytes returns
+ * 0 for a NULL plan. */
+int64_t mpk_cheb_state_bytes(const mpk_plan_t *P);
+mpk_status mpk_cheb_begin(const mpk_plan_t *P, const double *X, double c0_re, double c0_im, int32_t complex_coeff,
+                          double *state, mpk_stream stream);
+mpk_status mpk_cheb_advance(const mpk_plan_t *P, double *state, int32_t k_begin, int32_t k_end,
+                            const double *coeff_re, const double *coeff_im, double scale, double shift,
+                            mpk_stream stream);
+mpk_status mpk_cheb_finish(const mpk_plan_t *P, const double *state, double *out, mpk_stream stream);
+
 /* Timing counters of a plan built with opts.trace = 1, accumulated over all launches since
  * the plan was created (host array of MPK_TRACE_COUNTERS int64): 0 units, 1 ns the control
  * warps spent polling dependencies, 2 units whose dependencies were not all met at the first

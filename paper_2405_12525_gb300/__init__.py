@@ -38,6 +38,7 @@ EXPORTED_SYMBOLS = [
     "mpk_status_string", "mpk_last_error", "mpk_debug_drop_release", "mpk_read_trace", "mpk_apply_noalloc",
     "mpk_widen_values", "mpk_batch_plan", "mpk_batch_apply", "mpk_batch_describe", "mpk_batch_workspace",
     "mpk_build_levels_from", "mpk_spmv_rows", "mpk_gather_rows", "mpk_spmv_rows_multi", "mpk_copy_rows",
+    "mpk_cheb_state_bytes", "mpk_cheb_begin", "mpk_cheb_advance", "mpk_cheb_finish",
 ]
 MAX_ROW_SEGMENTS = 32
 
@@ -116,11 +117,16 @@ def load():
         "mpk_gather_rows": [vp, vp, i32, i32, vp, vp],
         "mpk_spmv_rows_multi": [i32, vp, vp, vp, vp, vp, vp],
         "mpk_copy_rows": [vp, vp, vp, vp, i64, i32, vp],
+        "mpk_cheb_begin": [vp, vp, dbl, dbl, i32, vp, vp],
+        "mpk_cheb_advance": [vp, vp, i32, i32, vp, vp, dbl, dbl, vp],
+        "mpk_cheb_finish": [vp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = C.c_int
+    lib.mpk_cheb_state_bytes.argtypes = [vp]
+    lib.mpk_cheb_state_bytes.restype = C.c_int64
     lib.mpk_plan_opts_default.argtypes = [C.POINTER(_Opts)]
     lib.mpk_plan_opts_default.restype = None
     lib.mpk_levels_destroy.argtypes = [vp]
@@ -405,6 +411,41 @@ class Plan:
         _check(self._lib.mpk_cheb_filter(self._h, _ptr(X), int(degree), cr.ctypes.data,
                                          ci.ctypes.data if ci is not None else None, float(scale), float(shift),
                                          _ptr(out), _stream(stream)))
+        return out
+
+    def cheb_state(self):
+        """A zeroed device buffer for the resumable Chebyshev filter: (4, n, nrhs) float64."""
+        torch = _torch()
+        nbytes = int(self._lib.mpk_cheb_state_bytes(self._h))
+        assert nbytes == 4 * self.n * self.nrhs * 8
+        return torch.zeros((4, self.n, self.nrhs), dtype=torch.float64, device="cuda")
+
+    def cheb_begin(self, X, state, c0_re: float, c0_im: float | None = None, stream=None):
+        """state <- (v_0 = X, acc = c_0 X); the state then holds step 0."""
+        self._block(X)
+        _check(self._lib.mpk_cheb_begin(self._h, _ptr(X), float(c0_re), float(c0_im or 0.0),
+                                        1 if c0_im is not None else 0, _ptr(state), _stream(stream)))
+        return state
+
+    def cheb_advance(self, state, k_begin: int, k_end: int, coeff_re, coeff_im=None, scale: float = 1.0,
+                     shift: float = 0.0, stream=None):
+        """Steps k_begin+1 .. k_end of the recurrence (absolute coefficient indices)."""
+        import numpy as np
+        cr = np.ascontiguousarray(coeff_re, dtype=np.float64)
+        ci = None if coeff_im is None else np.ascontiguousarray(coeff_im, dtype=np.float64)
+        if cr.size < k_end + 1 or (ci is not None and ci.size < k_end + 1):
+            raise ValueError("need coefficients up to k_end")
+        _check(self._lib.mpk_cheb_advance(self._h, _ptr(state), int(k_begin), int(k_end), cr.ctypes.data,
+                                          ci.ctypes.data if ci is not None else None, float(scale), float(shift),
+                                          _stream(stream)))
+        return state
+
+    def cheb_finish(self, state, out=None, stream=None):
+        """out <- the accumulated filter (numbering as the plan's order option)."""
+        torch = _torch()
+        if out is None:
+            out = torch.empty((self.n, self.nrhs), dtype=torch.float64, device="cuda")
+        _check(self._lib.mpk_cheb_finish(self._h, _ptr(state), _ptr(out), _stream(stream)))
         return out
 
     def debug_drop_release(self, chunk: int, k: int):

@@ -249,6 +249,47 @@ extern "C" mpk_status mpk_spmv_powers(const mpk_plan_t *Ph, const double *X, int
     MPK_GUARD_END
 }
 
+// Chebyshev recurrence state: ring of three vectors (v_j in ring slot j % 3, plan order) and the
+// accumulator.  cheb_start: v_0 = X (gathered into plan order if the plan keeps A's order),
+// acc = c_0 v_0.  cheb_steps: steps k_begin+1 .. k_end, in launches of at most p_max steps; the
+// ring indices follow the absolute step, so any split of the steps gives the same bits.
+static void cheb_start(Plan &P, const double *X, double c0_re, double c0_im, bool cplx, double *ring, double *acc,
+                       cudaStream_t s) {
+    const int64_t nm = (int64_t)P.n * P.m;
+    if (P.identity || P.order == MPK_ORDER_PLAN)
+        MPK_CUDA(cudaMemcpyAsync(ring, X, sizeof(double) * nm, cudaMemcpyDeviceToDevice, s));
+    else
+        launch_gather_rows(X, P.perm, ring, P.n, P.m, s);
+    launch_cheb_init(ring, acc, P.n, P.m, c0_re, cplx ? c0_im : 0.0, cplx ? 1 : 0, s);
+}
+
+static void cheb_steps(Plan &P, double *ring, double *acc, int32_t k_begin, int32_t k_end, const double *coeff_re,
+                       const double *coeff_im, double scale, double shift, cudaStream_t s) {
+    // same expressions as the recurrence's definition: 2A'v = alpha Av + beta v
+    const double alpha = 2.0 / scale, beta = -2.0 * shift / scale;
+    const double halpha = 1.0 / scale, hbeta = -shift / scale;
+    for (int32_t j0 = k_begin; j0 < k_end; j0 += P.p_max) {
+        const int32_t pb = std::min(P.p_max, k_end - j0);
+        next_epoch(P, s);
+        KArgs a = base_args(P, pb);
+        a.x0 = ring;
+        a.ybase = ring;
+        a.ring = 3;
+        a.k_offset = j0;
+        a.alpha = alpha;
+        a.beta = beta;
+        a.halpha = halpha;
+        a.hbeta = hbeta;
+        a.acc = acc;
+        a.complex_coeff = coeff_im ? 1 : 0;
+        for (int k = 1; k <= pb; ++k) {
+            a.cre[k] = coeff_re[j0 + k];
+            a.cim[k] = coeff_im ? coeff_im[j0 + k] : 0.0;
+        }
+        launch_mpk(P, a, 1, s);
+    }
+}
+
 extern "C" mpk_status mpk_cheb_filter(const mpk_plan_t *Ph, const double *X, int32_t degree, const double *coeff_re,
                                       const double *coeff_im, double scale, double shift, double *out,
                                       mpk_stream stream) {
@@ -266,38 +307,70 @@ extern "C" mpk_status mpk_cheb_filter(const mpk_plan_t *Ph, const double *X, int
     cudaStream_t s = as_stream(stream);
     const int64_t nm = (int64_t)P.n * P.m;
     const bool plan_order = P.identity || P.order == MPK_ORDER_PLAN;
-    // same expressions as the recurrence's definition: 2A'v = alpha Av + beta v
-    const double alpha = 2.0 / scale, beta = -2.0 * shift / scale;
-    const double halpha = 1.0 / scale, hbeta = -shift / scale;
-    double *v0 = P.work;
     double *acc = plan_order ? out : P.work + 3 * nm;
-    if (plan_order) {
-        MPK_CUDA(cudaMemcpyAsync(v0, X, sizeof(double) * nm, cudaMemcpyDeviceToDevice, s));
-    } else {
-        launch_gather_rows(X, P.perm, v0, P.n, P.m, s);
-    }
-    launch_cheb_init(v0, acc, P.n, P.m, coeff_re[0], coeff_im ? coeff_im[0] : 0.0, coeff_im ? 1 : 0, s);
-    for (int32_t j0 = 0; j0 < degree; j0 += P.p_max) {
-        const int32_t pb = std::min(P.p_max, degree - j0);
-        next_epoch(P, s);
-        KArgs a = base_args(P, pb);
-        a.x0 = v0;
-        a.ybase = P.work;
-        a.ring = 3;
-        a.k_offset = j0;
-        a.alpha = alpha;
-        a.beta = beta;
-        a.halpha = halpha;
-        a.hbeta = hbeta;
-        a.acc = acc;
-        a.complex_coeff = coeff_im ? 1 : 0;
-        for (int k = 1; k <= pb; ++k) {
-            a.cre[k] = coeff_re[j0 + k];
-            a.cim[k] = coeff_im ? coeff_im[j0 + k] : 0.0;
-        }
-        launch_mpk(P, a, 1, s);
-    }
+    cheb_start(P, X, coeff_re[0], coeff_im ? coeff_im[0] : 0.0, coeff_im != nullptr, P.work, acc, s);
+    cheb_steps(P, P.work, acc, 0, degree, coeff_re, coeff_im, scale, shift, s);
     if (!plan_order) launch_scatter_rows(acc, P.iperm, out, P.n, P.m, s);
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
+static void check_cheb_plan(const mpk_plan_t *Ph) {
+    if (!Ph || !Ph->impl) fail(MPK_ERR_INVALID, "plan is NULL");
+    const Plan &P = *Ph->impl;
+    if (!P.inst_row.empty()) fail(MPK_ERR_INVALID, "a batch plan runs through mpk_batch_apply");
+    if (P.level_capped) fail(MPK_ERR_INVALID, "a level-capped plan computes partial powers only");
+}
+
+extern "C" int64_t mpk_cheb_state_bytes(const mpk_plan_t *Ph) {
+    if (!Ph || !Ph->impl) return 0;
+    return 4 * (int64_t)Ph->impl->n * Ph->impl->m * (int64_t)sizeof(double);
+}
+
+extern "C" mpk_status mpk_cheb_begin(const mpk_plan_t *Ph, const double *X, double c0_re, double c0_im,
+                                     int32_t complex_coeff, double *state, mpk_stream stream) {
+    MPK_GUARD_BEGIN
+    check_cheb_plan(Ph);
+    Plan &P = *const_cast<Plan *>(Ph->impl);
+    if (complex_coeff && (P.m % 2)) fail(MPK_ERR_INVALID, "complex coefficients need an even nrhs");
+    if (P.n > 0 && (!X || !state)) fail(MPK_ERR_INVALID, "NULL X or state");
+    if (P.n == 0) return MPK_OK;
+    const int64_t nm = (int64_t)P.n * P.m;
+    cheb_start(P, X, c0_re, c0_im, complex_coeff != 0, state, state + 3 * nm, as_stream(stream));
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
+extern "C" mpk_status mpk_cheb_advance(const mpk_plan_t *Ph, double *state, int32_t k_begin, int32_t k_end,
+                                       const double *coeff_re, const double *coeff_im, double scale, double shift,
+                                       mpk_stream stream) {
+    MPK_GUARD_BEGIN
+    check_cheb_plan(Ph);
+    Plan &P = *const_cast<Plan *>(Ph->impl);
+    if (k_begin < 0 || k_end < k_begin) fail(MPK_ERR_INVALID, "need 0 <= k_begin <= k_end");
+    if (!coeff_re) fail(MPK_ERR_INVALID, "coeff_re is NULL");
+    if (!(scale != 0.0)) fail(MPK_ERR_INVALID, "scale must be non-zero");
+    if (coeff_im && (P.m % 2)) fail(MPK_ERR_INVALID, "complex coefficients need an even nrhs");
+    if (P.n > 0 && !state) fail(MPK_ERR_INVALID, "NULL state");
+    if (P.n == 0) return MPK_OK;
+    const int64_t nm = (int64_t)P.n * P.m;
+    cheb_steps(P, state, state + 3 * nm, k_begin, k_end, coeff_re, coeff_im, scale, shift, as_stream(stream));
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
+extern "C" mpk_status mpk_cheb_finish(const mpk_plan_t *Ph, const double *state, double *out, mpk_stream stream) {
+    MPK_GUARD_BEGIN
+    check_cheb_plan(Ph);
+    const Plan &P = *Ph->impl;
+    if (P.n > 0 && (!state || !out)) fail(MPK_ERR_INVALID, "NULL state or out");
+    if (P.n == 0) return MPK_OK;
+    const int64_t nm = (int64_t)P.n * P.m;
+    cudaStream_t s = as_stream(stream);
+    if (P.identity || P.order == MPK_ORDER_PLAN)
+        MPK_CUDA(cudaMemcpyAsync(out, state + 3 * nm, sizeof(double) * nm, cudaMemcpyDeviceToDevice, s));
+    else
+        launch_scatter_rows(state + 3 * nm, P.iperm, out, P.n, P.m, s);
     return MPK_OK;
     MPK_GUARD_END
 }

@@ -475,3 +475,39 @@ def test_shuffled_schedules_give_the_same_bits(mpk, seed, name):
         P.sync_status()
         want = oracle.cheb(A, X, 11, c, scale=(hi - lo) / 2 * 1.01 + 1e-3, shift=(hi + lo) / 2)
         assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+
+
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("engine", [0, 2])
+def test_cheb_resume_in_pieces_and_from_a_checkpoint(mpk, order, engine):
+    # the recurrence state (v_{k-1}, v_k, accumulator) at any step is a resume point: pieces
+    # of the degree, and a state saved to the host and restored, give the same bits as one call
+    A = gen.xxz_chain(12, stream=87)
+    dA = _dev(A, mpk, True)
+    lo, hi = gen.gershgorin_bounds(A)
+    scale, shift = (hi - lo) / 2 * 1.01, (hi + lo) / 2
+    P = mpk.plan(dA, mpk.build_levels(dA, 0), p_max=8, nrhs=2, order=order, cache_bytes=30000, engine=engine)
+    X = gen.vector(A.n, 2, stream=101)
+    _, pe, ip, _ = oracle.levels(A, 0)
+    Xin = torch.from_numpy(np.ascontiguousarray(X if order == 0 else X[pe])).cuda()
+    deg = 37
+    cr = gen.uniform(gen.derive_seed(102), deg + 1)
+    ci = gen.uniform(gen.derive_seed(103), deg + 1)
+    whole = P.cheb_filter(Xin, deg, cr, ci, scale=scale, shift=shift).cpu().numpy()
+    st = P.cheb_state()
+    P.cheb_begin(Xin, st, cr[0], ci[0])
+    for k0, k1 in ((0, 5), (5, 16), (16, 24)):
+        P.cheb_advance(st, k0, k1, cr, ci, scale=scale, shift=shift)
+    saved = st.cpu().numpy().copy()                # checkpoint at step 24
+    st.fill_(float("nan"))
+    st.copy_(torch.from_numpy(saved))              # restore
+    P.cheb_advance(st, 24, deg, cr, ci, scale=scale, shift=shift)
+    got = P.cheb_finish(st).cpu().numpy()
+    P.sync_status()
+    assert np.array_equal(got.view(np.uint64), whole.view(np.uint64))
+    want = oracle.cheb(A, X, deg, cr, ci, scale=scale, shift=shift)
+    if order == 1:
+        got = got[ip]
+    assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+    with pytest.raises(mpk.MpkError):
+        P.cheb_advance(st, 5, 4, cr, ci, scale=scale, shift=shift)
