@@ -140,7 +140,12 @@ typedef struct {
     int32_t shape;          /* block shape of the staged engine: 0 = chosen from the mean
                                row width; 1 = 13 compute warps, 3072-entry slots, 3 blocks
                                per SM (rows up to ~7 entries); 2 = 15 warps, 4096 entries,
-                               2 blocks; 3 = 15 warps, entries read from global memory      */
+                               2 blocks; 3 = 15 warps, entries read from global memory;
+                               4 = 10 compute warps, 2304-entry slots that also hold the
+                               input rows the chunk reads (at most 4 row windows, 1664
+                               doubles), 3 blocks per SM: the compute warps read only shared
+                               memory.  Shape 4 is never chosen automatically; mpk_plan fails
+                               with MPK_ERR_UNSUPPORTED when a chunk's windows do not fit    */
     int64_t shuffle_seed;   /* race-detection aid: non-zero permutes the staged engine's work
                                units inside every line of the schedule (a valid order whose
                                results must be the same bits); 0 = the natural order         */
@@ -183,7 +188,7 @@ typedef struct {
     const int32_t *group_row_ptr_dev;   /* num_groups+1 row offsets                        */
     const int32_t *chunk_row_ptr_dev;   /* num_chunks+1 row offsets                        */
     const int32_t *perm_dev;            /* new -> old (NULL: identity)                     */
-    int32_t shape;                /* block shape of the staged engine (0..2, opts.shape - 1) */
+    int32_t shape;                /* block shape of the staged engine (0..3, opts.shape - 1) */
     int32_t engine;               /* MPK_ENGINE_STAGED or MPK_ENGINE_WARP                 */
     int32_t chunk_rows;           /* rows per chunk limit in effect                      */
 } mpk_plan_desc;

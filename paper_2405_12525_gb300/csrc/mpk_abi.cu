@@ -148,6 +148,7 @@ KArgs mpk::base_args(Plan &P, int32_t p) {
     std::memset(&a, 0, sizeof(a));
     a.val = P.val;
     a.col = P.col;
+    a.lcol = P.lcol;
     a.slice_ptr = P.slice_ptr;
     a.rowlen = P.rowlen;
     a.chunk_row = P.chunk_row;

@@ -57,7 +57,9 @@ struct Arena {
     int64_t bytes = 0;
     int64_t budget = 0;  // 0 = unlimited
     std::vector<void *> ptrs;
+    std::vector<int64_t> sizes;
     void *alloc(int64_t nbytes);
+    void free(void *p);  // frees one allocation of this arena (no-op for NULL)
     template <class T> T *alloc_n(int64_t n) { return static_cast<T *>(alloc(n * (int64_t)sizeof(T))); }
     void release();
 };
@@ -145,17 +147,46 @@ struct Levels {
 constexpr int kMaxP = 31;
 // Block shapes of the level-blocked kernel: compute warps per block (one 32-row slice each
 // per unit, so the default chunk is 32 * comp_warps rows), padded entries a shared-memory
-// slot holds (a chunk is cut to fit one), and blocks per SM for the single-vector power
-// kernel.  Shape 0 suits rows of up to about 7 stored entries (13 slices of width 7 fill a
+// slot holds (a chunk is cut to fit one), blocks per SM for the single-vector power
+// kernel, staging slots per block, and the 8-byte words of input rows a slot holds (x_words,
+// 0: none) and the control warps (1, or 2: one polls dependencies, one stages).  Shape 0 suits rows of up to about 7 stored entries (13 slices of width 7 fill a
 // slot); shape 1 suits wider rows; shape 2 stages nothing (stage_entries 0: the compute
 // warps read the entries from global memory, and chunks are not cut by a slot), for rows so
-// wide that a slot holds only a few slices.  The planner picks the shape from the mean
-// slice width unless the plan options name one.
+// wide that a slot holds only a few slices.  Shape 3 also stages the unit's input rows:
+// after the dependency poll the control warp copies the (at most four) row windows of the
+// input vector that the chunk reads into the slot, and the chunk's column indices are
+// staged as 16-bit positions in that window area, so that the compute warps read nothing
+// but shared memory.  The planner picks shape 3 when every chunk's windows fit a slot, else
+// a shape from the mean slice width, unless the plan options name one.
 struct BlockShape {
-    int comp_warps, stage_entries, blocks;
+    int comp_warps, stage_entries, blocks, slots, x_words, ctrl_warps;
 };
-constexpr BlockShape kShapes[3] = {{13, 3072, 3}, {15, 4096, 2}, {15, 0, 2}};
-constexpr int kNumShapes = 3;
+#ifndef MPK_XS_WARPS
+#define MPK_XS_WARPS 10
+#endif
+#ifndef MPK_XS_ENTRIES
+#define MPK_XS_ENTRIES 2304
+#endif
+#ifndef MPK_XS_BLOCKS
+#define MPK_XS_BLOCKS 3
+#endif
+#ifndef MPK_XS_SLOTS
+#define MPK_XS_SLOTS 2
+#endif
+#ifndef MPK_XS_WORDS
+#define MPK_XS_WORDS 1664
+#endif
+#ifndef MPK_XS_CTL
+#define MPK_XS_CTL 1
+#endif
+constexpr BlockShape kShapes[4] = {{13, 3072, 3, 2, 0, 1},
+                                   {15, 4096, 2, 2, 0, 1},
+                                   {15, 0, 2, 2, 0, 1},
+                                   {MPK_XS_WARPS, MPK_XS_ENTRIES, MPK_XS_BLOCKS, MPK_XS_SLOTS, MPK_XS_WORDS, MPK_XS_CTL}};
+constexpr int kNumShapes = 4;
+constexpr int kShapeX = 3;  // the shape that stages input rows
+// input-row windows of a chunk (shape 3): one per dependency range
+constexpr int kXWin = 4;
 constexpr int kMaxStageEntries = 4096;
 // 1: chunks whose entries fit a buffer are copied to shared memory by the bulk-copy engine;
 // 0: every unit reads its entries from global memory (L2) directly
@@ -173,10 +204,13 @@ constexpr int kTraceShared = MPK_TRACE_COUNTERS - 1;
 // GPU do not wait on each other.  A group is then reused kSlotSkew * p lines later, so the
 // cache budget is shared by kSlotSkew * p_max + 1 groups.
 constexpr int kSlotSkew = 3;
-// chunk record: 8 ints of chunk data, 2 * kDepRanges ints of dependency ranges and the
-// widths of up to kRecSlices slices as bytes (only staged chunks use them)
+// chunk record: 8 ints of chunk data, 2 * kDepRanges ints of dependency ranges, the
+// widths of up to kRecSlices slices as bytes (only staged chunks use them) and, for shape 3,
+// kXWin input-row windows as (first row, rows, position in the slot's window area in rows)
 constexpr int kRecSlices = 16;
-constexpr int kRecInts = 8 + 2 * kDepRanges + kRecSlices / 4;
+constexpr int kRecWin = 8 + 2 * kDepRanges + kRecSlices / 4;  // first int of the windows
+constexpr int kRecInts = kRecWin + 3 * kXWin;
+static_assert(kRecInts <= 32, "a chunk record is read by one lane per int");
 struct KArgs {
     // sliced matrix copy (plan order)
     const void *val;  // values of the matrix's value type (Plan::val_type)
@@ -187,7 +221,8 @@ struct KArgs {
     const int32_t *chunk_slice;
     const int2 *dep;
     const int4 *dep_ranges;  // 2 x int4 per chunk: kDepRanges (lo, hi) pairs
-    const int4 *chunk_rec;   // kRecInts ints per chunk: rows, slices, entries, ranges, widths
+    const int4 *chunk_rec;   // kRecInts ints per chunk: rows, slices, entries, ranges, widths, windows
+    const uint16_t *lcol;    // shape 3: window-area position of every entry's column (0xffff: padding)
     int32_t n;
     int32_t nchunks;
     // schedule for this launch
@@ -246,6 +281,7 @@ struct Plan {
     // device data (owned by arena)
     void *val = nullptr;  // val_bytes per padded entry
     int32_t *col = nullptr;
+    uint16_t *lcol = nullptr;  // shape 3: column positions in the chunk's input-row windows
     int64_t *slice_ptr = nullptr;
     int32_t *rowlen = nullptr;
     int32_t *chunk_row = nullptr;

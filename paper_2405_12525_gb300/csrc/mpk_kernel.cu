@@ -395,14 +395,27 @@ void launch_cheb_init(const double *v0, double *acc, int32_t n, int32_t m, doubl
 static void *select_mpk(int mode, int m, bool trace, int vtype, int shape) {
     if (shape == 0) return select_mpk_shape0(mode, m, trace, vtype);
     if (shape == 1) return select_mpk_shape1(mode, m, trace, vtype);
-    return select_mpk_shape2(mode, m, trace, vtype);
+    if (shape == 2) return select_mpk_shape2(mode, m, trace, vtype);
+    return select_mpk_shape3(mode, m, trace, vtype);
 }
 
 static int mpk_smem_bytes(int vtype, int shape) {
-    return shape == 0 ? smem_bytes_shape<0>(vtype) : (shape == 1 ? smem_bytes_shape<1>(vtype) : smem_bytes_shape<2>(vtype));
+    switch (shape) {
+        case 0: return smem_bytes_shape<0>(vtype);
+        case 1: return smem_bytes_shape<1>(vtype);
+        case 2: return smem_bytes_shape<2>(vtype);
+        default: return smem_bytes_shape<3>(vtype);
+    }
 }
 
-static int mpk_block_size(int shape) { return shape == 0 ? Shape<0>::BS : (shape == 1 ? Shape<1>::BS : Shape<2>::BS); }
+static int mpk_block_size(int shape) {
+    switch (shape) {
+        case 0: return Shape<0>::BS;
+        case 1: return Shape<1>::BS;
+        case 2: return Shape<2>::BS;
+        default: return Shape<3>::BS;
+    }
+}
 
 int occupancy_grid(int mode, int m, bool trace, int vtype, int shape) {
     static int cache[3][2][2][9][kNumShapes] = {};

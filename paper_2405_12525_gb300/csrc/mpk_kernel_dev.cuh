@@ -14,27 +14,35 @@ namespace mpk {
 template <int SH> struct Shape {
     static constexpr int CW = kShapes[SH].comp_warps;
     static constexpr int SE = kShapes[SH].stage_entries;
-    static constexpr int BS = 32 * (1 + CW);
+    static constexpr int BS = 32 * (kShapes[SH].ctrl_warps + CW);
+    static constexpr int SL = kShapes[SH].slots;    // staging slots
+    static constexpr int CTL = kShapes[SH].ctrl_warps;  // control warps: 1, or 2 (poll + stage)
+    static constexpr int XW = kShapes[SH].x_words;  // input-row words per slot (0: not staged)
+    static constexpr bool X = XW > 0;
 };
 // blocks per SM the register budget is set for (65536 registers per SM).  Shape 0 runs the
 // single-vector power kernel at three blocks of 14 warps (40 registers a thread; its two
 // 3072-entry slots, 72 KB, fit three times in an SM's shared memory); wider blocks, the
 // Chebyshev recurrence, the traced kernel and shape 1 keep 64 registers at two blocks.
 template <int M, int MODE, bool TRACE, int SH> struct MpkOcc {
-    static constexpr int blocks = (M == 1 && MODE == 0 && !TRACE) ? kShapes[SH].blocks : 2;
+    static constexpr int blocks = Shape<SH>::X ? kShapes[SH].blocks
+                                               : ((M == 1 && MODE == 0 && !TRACE) ? kShapes[SH].blocks : 2);
 };
 constexpr int kSpmvBS = 256;        // threads per block of the plain SpMV kernel
-// Staging slots: the control warp fills one while the compute warps work on the other.
-constexpr int kSlots = 2;
+// Staging slots (Shape::SL): the control warp fills one while the compute warps work on another.
+constexpr int kMaxSlots = 4;
 // column indices of staged chunks: copied to shared memory beside the values (1), or read
 // from global memory (L2) by the compute warps (0), which halves the slot size for FP64
 #ifndef MPK_STAGE_COL
 #define MPK_STAGE_COL 1
 #endif
 constexpr bool kStageCol = MPK_STAGE_COL != 0;
-// one slot: the shape's stage entries of the matrix's value type, then as many column indices
+// dynamic shared memory: per slot the shape's stage entries of the matrix's value type, then
+// as many column indices (int32; shape 3: 16-bit window positions), then shape 3's input-row
+// window area (x_words doubles)
 template <class VT, int SH> constexpr int smem_bytes() {
-    return kSlots * Shape<SH>::SE * (int)(sizeof(typename VT::T) + (kStageCol ? 4 : 0));
+    return Shape<SH>::X ? Shape<SH>::SL * (Shape<SH>::SE * (int)(sizeof(typename VT::T) + 2) + 8 * Shape<SH>::XW)
+                        : Shape<SH>::SL * Shape<SH>::SE * (int)(sizeof(typename VT::T) + (kStageCol ? 4 : 0));
 }
 
 enum Mode { MODE_POWERS = 0, MODE_CHEB = 1 };
@@ -99,12 +107,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     return ok != 0;
 }
 // global -> shared bulk copy (TMA, untiled); addresses 16-byte aligned, bytes % 16 == 0
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+__device__ __forceinline__ void bulk_g2s_addr(uint32_t dst, uint64_t src, uint32_t bytes, uint64_t *bar) {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    bulk_g2s_addr(smem_u32(dst), (uint64_t)src, bytes, bar);
 }
 
 // Entries whose x loads are issued together before their FMAs.
@@ -208,6 +218,76 @@ struct GCol {
     const int32_t *p;
     __device__ __forceinline__ int32_t operator[](int64_t i) const { return __ldg(p + i); }
 };
+
+// Rows of global memory a row's epilogue reads, loaded before its FMAs so that their latency
+// overlaps the row sum: the row's own input (Chebyshev) and the row two steps back (Chebyshev
+// from step 2 on), or the row of x0 copied to Y[0] (powers, power 1).
+template <int M> struct EpiRows {
+    double own[M], back[M];
+};
+template <int M, int MODE>
+__device__ __forceinline__ void epilogue_load(const KArgs &a, int k, int64_t r, const double *xin, EpiRows<M> &e) {
+    const int j = a.k_offset + k;
+    if constexpr (MODE == MODE_CHEB) {
+#pragma unroll
+        for (int i = 0; i < M; ++i) e.own[i] = xin[r * M + i];
+        if (j != 1) {
+            const double *vp2 = a.ybase + (int64_t)((j - 2) % a.ring) * a.ystride + r * M;
+#pragma unroll
+            for (int i = 0; i < M; ++i) e.back[i] = vp2[i];
+        }
+    } else {
+        if (k == 1 && a.y0copy) {
+#pragma unroll
+            for (int i = 0; i < M; ++i) e.own[i] = a.x0[r * M + i];
+        }
+    }
+}
+// Epilogue of one row at local power k with its rows loaded: store into the plan-order slot
+// (and Y[0] for power 1), or advance the Chebyshev recurrence.
+template <int M, int MODE>
+__device__ __forceinline__ void row_epilogue_loaded(const KArgs &a, int k, int64_t r, const double (&w)[M],
+                                                    const EpiRows<M> &e) {
+    const int j = a.k_offset + k;  // absolute power / recurrence step
+    double *y = a.ybase + (int64_t)(j % a.ring) * a.ystride + r * M;
+    if constexpr (MODE == MODE_CHEB) {
+        double vn[M];
+        if (j == 1) {
+#pragma unroll
+            for (int i = 0; i < M; ++i) vn[i] = fma(a.halpha, w[i], a.hbeta * e.own[i]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < M; ++i) vn[i] = fma(a.alpha, w[i], fma(a.beta, e.own[i], -e.back[i]));
+        }
+#pragma unroll
+        for (int i = 0; i < M; ++i) y[i] = vn[i];
+        double *acc = a.acc + r * M;
+        const double cr = a.cre[k];
+        if (!a.complex_coeff) {
+#pragma unroll
+            for (int i = 0; i < M; ++i) acc[i] = fma(cr, vn[i], acc[i]);
+        } else {
+            const double ci = a.cim[k];
+#pragma unroll
+            for (int i = 0; i + 1 < M; i += 2) {
+                double re = acc[i], im = acc[i + 1];
+                re = fma(cr, vn[i], re);
+                re = fma(-ci, vn[i + 1], re);
+                im = fma(cr, vn[i + 1], im);
+                im = fma(ci, vn[i], im);
+                acc[i] = re;
+                acc[i + 1] = im;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < M; ++i) y[i] = w[i];
+        if (k == 1 && a.y0copy) {
+#pragma unroll
+            for (int i = 0; i < M; ++i) a.y0copy[r * M + i] = e.own[i];
+        }
+    }
+}
 
 // Epilogue of one row at local power k: store into the plan-order slot, or advance the
 // Chebyshev recurrence.
@@ -345,19 +425,82 @@ __device__ __forceinline__ void phase_a(const KArgs &a, const UnitInfo &u, int b
     }
 }
 
-// phase B: finish unit pf (all of the warp's rows), then publish and release its slot
+// Completion of a unit by the compute warps.  Each warp releases the unit's slot (empty[b])
+// as soon as it has read everything it needs from the slot into registers, so that the
+// control warp can refill the slot while the warp still runs its FMA chain and stores; the
+// last warp to finish the unit publishes it.  The finish counters are indexed by the unit's
+// sequence number in the block (modulo kDoneRing), not by the slot, since a slot may hold the
+// next unit while warps still finish the previous one: a warp reaches unit seq + kDoneRing
+// only after every warp released unit seq + kDoneRing - slots >= seq + 1, which each warp
+// does after finishing unit seq.
+constexpr int kDoneRing = 2 * kMaxSlots;
+
+// shapes 0-2 release the slot before their FMA chain too (1), or after their unit (0): the
+// early path holds a batch of entries in registers, more than shape 0's 40 a thread allow
+#ifndef MPK_EARLY_RELEASE_B
+#define MPK_EARLY_RELEASE_B 0
+#endif
+constexpr bool kEarlyReleaseB = MPK_EARLY_RELEASE_B != 0;
+template <int CW>
+__device__ __forceinline__ void release_slot(uint64_t *s_empty, int b, int lane) {
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&s_empty[b]);
+}
+template <int CW>
+__device__ __forceinline__ void publish_unit(const KArgs &a, int32_t epoch, int unit, int seq, int *s_done, int lane) {
+    __syncwarp();
+    if (lane == 0) {
+        // the last compute warp to finish the unit publishes it (release at gpu scope after
+        // the other warps' stores were ordered at block scope)
+        __threadfence_block();
+        const int d = seq % kDoneRing;
+        if (atomicAdd(&s_done[d], 1) == CW - 1) {
+            s_done[d] = 0;
+            fence_acq_rel_gpu();
+            if (unit != a.drop_unit) st_relaxed(a.flags + (int64_t)(unit & 31) * a.nchunks + (unit >> 5), epoch);
+        }
+    }
+}
+
+// phase B: finish unit pf (all of the warp's rows), release its slot and publish it
 template <int M, int MODE, class VT, int SH>
 __device__ __forceinline__ void phase_b(const KArgs &a, int32_t epoch, const Prefetch<M> &pf, const UnitInfo *s_u,
                                         const typename VT::T *sval0, const int32_t *scol0, int *s_done, uint64_t *s_empty,
-                                        int cwarp, int lane) {
+                                        int cwarp, int lane, int seq) {
     constexpr int B = Batch<M>::B;
-    const UnitInfo &u = s_u[pf.slot];
+    const UnitInfo u = s_u[pf.slot];  // a copy: the slot is refilled once released
     const int k = pf.unit & 31;
     const double *xin = input_block<M>(a, k);
     constexpr int kCompWarps = Shape<SH>::CW;
     const SVal<VT> sval{sval0 + pf.slot * Shape<SH>::SE};
     const int32_t *scol = kStageCol ? scol0 + pf.slot * Shape<SH>::SE : a.col + u.ebase;
-    if (Shape<SH>::SE > 0 && u.staged) {
+    bool released = false;
+    if (kEarlyReleaseB && Shape<SH>::SE > 0 && u.staged && u.nsl <= kCompWarps && pf.width <= B) {
+        // the warp's one slice fits one batch: read its entries, release the slot, then compute
+        double v[B];
+        bool on[B];
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+            on[q] = pf.r >= 0 && q < pf.width && scol[pf.off + 32 * q] >= 0;
+            v[q] = on[q] ? sval[pf.off + 32 * q] : 0.0;
+        }
+        EpiRows<M> er;
+        if (pf.r >= 0) epilogue_load<M, MODE>(a, k, pf.r, xin, er);
+        release_slot<kCompWarps>(s_empty, pf.slot, lane);
+        released = true;
+        if (pf.r >= 0) {
+            double w[M];
+#pragma unroll
+            for (int i = 0; i < M; ++i) w[i] = 0.0;
+#pragma unroll
+            for (int q = 0; q < B; ++q)
+                if (on[q]) {
+#pragma unroll
+                    for (int i = 0; i < M; ++i) w[i] = fma(v[q], pf.x[q][i], w[i]);
+                }
+            row_epilogue_loaded<M, MODE>(a, k, pf.r, w, er);
+        }
+    } else if (Shape<SH>::SE > 0 && u.staged) {
         if (pf.r >= 0) {  // first slice: prefetched first batch, then the rest of the row
             double w[M];
 #pragma unroll
@@ -391,7 +534,9 @@ __device__ __forceinline__ void phase_b(const KArgs &a, int32_t epoch, const Pre
                 for (int i = 0; i < M; ++i) a.y0copy[r * M + i] = a.x0[r * M + i];
             }
         }
-    } else {  // entries in global memory (chunk too large to stage)
+    } else {  // entries in global memory (chunk too large to stage): the slot holds nothing
+        release_slot<kCompWarps>(s_empty, pf.slot, lane);
+        released = true;
         for (int sl = cwarp; sl < u.nsl; sl += kCompWarps) {
             const int64_t r = (int64_t)u.row0 + 32 * sl + lane;
             if (r >= u.row1) continue;
@@ -409,21 +554,9 @@ __device__ __forceinline__ void phase_b(const KArgs &a, int32_t epoch, const Pre
             }
         }
     }
-    __syncwarp();
-    if (lane == 0) {
-        // the last compute warp to finish the unit publishes it (release at gpu scope after
-        // the other warps' stores were ordered at block scope), then the slot is released
-        __threadfence_block();
-        if (atomicAdd(&s_done[pf.slot], 1) == kCompWarps - 1) {
-            s_done[pf.slot] = 0;
-            fence_acq_rel_gpu();
-            if (pf.unit != a.drop_unit)
-                st_relaxed(a.flags + (int64_t)k * a.nchunks + (pf.unit >> 5), epoch);
-        }
-        mbar_arrive(&s_empty[pf.slot]);
-    }
+    if (!released) release_slot<kCompWarps>(s_empty, pf.slot, lane);
+    publish_unit<kCompWarps>(a, epoch, pf.unit, seq, s_done, lane);
 }
-
 // dependency flags v0 .. v0+127 of a unit (4 per lane); flags past `total` read as ready
 __device__ __forceinline__ void dep_load(const KArgs &a, int32_t epoch, int k, const int (&lo)[kDepRanges],
                                          const int (&len)[kDepRanges], int total, int v0, int lane, int (&got)[4]) {
@@ -468,9 +601,142 @@ __device__ __forceinline__ int dep_ranges_of(int rec, int (&lo)[kDepRanges], int
     return total;
 }
 
+
+// ----------------------------------------------------------------------------- shape 3
+// Input-row windows.  A shape-3 chunk reads its columns from at most kXWin windows of input
+// rows; window q holds rows [lo, lo + len) and sits in the slot's window area from row
+// position pos on: element (row c, column i) is double number shift + M * (pos + c - lo) + i
+// of the area, shift = (address of the input vector / 8) mod 2.  The control warp copies
+// each window with one bulk copy, whose global start is rounded down and end rounded up to
+// 16 bytes; the planner keeps pos = lo (mod 2) for M = 1 and leaves room around each window,
+// so that the rounded copy lands 16-byte aligned, inside the area and clear of the other
+// windows.  Only at the very end of the input vector is the end not rounded up: the last 8
+// bytes are then copied by a plain load (no read past the vector).
+struct XCopy {
+    uint64_t src;    // global start, 16-byte aligned
+    uint32_t dst;    // shared-memory address, 16-byte aligned
+    uint32_t bytes;  // bulk bytes (multiple of 16, may be 0)
+    uint64_t tail;   // global address of an 8-byte word copied by a plain load (0: none)
+    uint32_t tdst;   // its shared-memory address
+};
+template <int M>
+__device__ __forceinline__ XCopy x_copy(const double *xin, int64_t n, int lo, int len, int pos, uint32_t area) {
+    XCopy c{0, 0, 0, 0, 0};
+    if (len <= 0) return c;
+    const uint64_t shift = ((uint64_t)xin >> 3) & 1u;
+    const uint64_t g0 = (uint64_t)(xin + (int64_t)lo * M), g1 = (uint64_t)(xin + (int64_t)(lo + len) * M);
+    const uint64_t vend = (uint64_t)(xin + n * M);
+    const uint64_t a0 = g0 & ~(uint64_t)15;
+    uint64_t a1 = (g1 + 15) & ~(uint64_t)15;
+    if (a1 > vend) {  // only when the window ends the vector at an 8 (mod 16) address
+        a1 = vend & ~(uint64_t)15;
+        c.tail = a1;
+    }
+    c.src = a0;
+    c.dst = area + (uint32_t)(8 * (shift + (uint64_t)M * pos)) - (uint32_t)(g0 - a0);
+    c.bytes = (uint32_t)(a1 - a0);
+    c.tdst = c.dst + c.bytes;
+    return c;
+}
+
+// Compute warps of shape 3: every row of the warp's slices, with entries, column positions
+// and input rows read from the slot; the slot is released once read, then the unit published.
+template <int M, int MODE, class VT, int SH>
+__device__ __forceinline__ void phase_x(const KArgs &a, int32_t epoch, const UnitInfo *s_u, int b,
+                                        const typename VT::T *sval0, const uint16_t *slc0, const double *sx0,
+                                        int *s_done, uint64_t *s_empty, int cwarp, int lane, int seq) {
+    constexpr int CW = Shape<SH>::CW, SE = Shape<SH>::SE;
+    constexpr int B = Batch<M>::B;
+    const UnitInfo u = s_u[b];  // a copy: the slot is refilled once released
+    const int k = u.unit & 31;
+    const double *xin = input_block<M>(a, k);
+    const SVal<VT> sval{sval0 + b * SE};
+    const uint16_t *slc = slc0 + b * SE;
+    const double *sx = sx0 + b * Shape<SH>::XW + (((uint64_t)xin >> 3) & 1u);
+    if (u.nsl <= CW && (cwarp >= u.nsl || slice_width(u.widths, cwarp) <= B)) {
+        // at most one slice of at most one batch: read it, release the slot, then compute
+        int pre = 0;
+#pragma unroll
+        for (int q = 0; q < kRecSlices; ++q) pre += (q < cwarp) ? slice_width(u.widths, q) : 0;
+        const int width = cwarp < u.nsl ? slice_width(u.widths, cwarp) : 0;
+        const int64_t r = (int64_t)u.row0 + 32 * cwarp + lane;
+        const bool row = cwarp < u.nsl && r < u.row1;
+        const int off = 32 * pre + lane;
+        bool on[B];
+        double v[B], xv[B][M];
+#pragma unroll
+        for (int q = 0; q < B; ++q) {
+            const int lc = (row && q < width) ? (int)slc[off + 32 * q] : 0xffff;
+            on[q] = lc != 0xffff;
+            v[q] = on[q] ? sval[off + 32 * q] : 0.0;
+#pragma unroll
+            for (int i = 0; i < M; ++i) xv[q][i] = on[q] ? sx[M * lc + i] : 0.0;
+        }
+        EpiRows<M> er;
+        if (row) epilogue_load<M, MODE>(a, k, r, xin, er);
+        release_slot<CW>(s_empty, b, lane);
+        if (row) {
+            double w[M];
+#pragma unroll
+            for (int i = 0; i < M; ++i) w[i] = 0.0;
+#pragma unroll
+            for (int q = 0; q < B; ++q)
+                if (on[q]) {
+#pragma unroll
+                    for (int i = 0; i < M; ++i) w[i] = fma(v[q], xv[q][i], w[i]);
+                }
+            row_epilogue_loaded<M, MODE>(a, k, r, w, er);
+        }
+        publish_unit<CW>(a, epoch, u.unit, seq, s_done, lane);
+        return;
+    }
+    for (int sl = cwarp; sl < u.nsl; sl += CW) {
+        int pre = 0;
+#pragma unroll
+        for (int q = 0; q < kRecSlices; ++q) pre += (q < sl) ? slice_width(u.widths, q) : 0;
+        const int width = slice_width(u.widths, sl);
+        const int64_t r = (int64_t)u.row0 + 32 * sl + lane;
+        if (r >= u.row1) continue;
+        const int off = 32 * pre + lane;
+        EpiRows<M> er;
+        epilogue_load<M, MODE>(a, k, r, xin, er);
+        double w[M];
+#pragma unroll
+        for (int i = 0; i < M; ++i) w[i] = 0.0;
+        for (int j0 = 0; j0 < width; j0 += B) {
+            int lc[B];
+            double v[B];
+#pragma unroll
+            for (int q = 0; q < B; ++q) {
+                lc[q] = (j0 + q < width) ? (int)slc[off + 32 * (j0 + q)] : 0xffff;
+                v[q] = (lc[q] != 0xffff) ? sval[off + 32 * (j0 + q)] : 0.0;
+            }
+            double xv[B][M];
+#pragma unroll
+            for (int q = 0; q < B; ++q)
+#pragma unroll
+                for (int i = 0; i < M; ++i) xv[q][i] = (lc[q] != 0xffff) ? sx[M * lc[q] + i] : 0.0;
+#pragma unroll
+            for (int q = 0; q < B; ++q)
+                if (lc[q] != 0xffff) {
+#pragma unroll
+                    for (int i = 0; i < M; ++i) w[i] = fma(v[q], xv[q][i], w[i]);
+                }
+        }
+        row_epilogue_loaded<M, MODE>(a, k, r, w, er);
+    }
+    release_slot<CW>(s_empty, b, lane);
+    publish_unit<CW>(a, epoch, u.unit, seq, s_done, lane);
+}
+
 template <int M, int MODE, bool TRACE, class VT, int SH>
 __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::blocks)) k_mpk(const KArgs a) {
     constexpr int kCompWarps = Shape<SH>::CW, kStageEntries = Shape<SH>::SE;
+    constexpr int kSlots = Shape<SH>::SL;
+    constexpr bool XS = Shape<SH>::X;
+    constexpr int kCtl = Shape<SH>::CTL;
+    constexpr int kRing = 4;  // split control: ready units between the poll and the stage warp
+    static_assert(kSlots >= 2 && kSlots <= kMaxSlots, "slots");
     using T = typename VT::T;
     const bool tr = TRACE && a.trace != nullptr;  // timing counters (instantiated separately)
     extern __shared__ __align__(128) unsigned char smem[];
@@ -478,10 +744,19 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
     __shared__ __align__(8) uint64_t s_empty[kSlots];
     __shared__ UnitInfo s_u[kSlots];
     __shared__ volatile int s_final;  // units handed over in total; -1 while the control warp runs
-    __shared__ int s_done[kSlots];    // compute warps finished with the slot's unit
+    __shared__ int s_done[kDoneRing];  // compute warps finished with a unit (by its sequence number)
+    // split control (two control warps): ring of ready units, its mbarriers, stop flag
+    __shared__ __align__(8) uint64_t s_rfull[kCtl == 2 ? kRing : 1];
+    __shared__ __align__(8) uint64_t s_rfree[kCtl == 2 ? kRing : 1];
+    __shared__ int s_ring_unit[kCtl == 2 ? kRing : 1];
+    __shared__ int s_ring_rec[kCtl == 2 ? kRing : 1][kRecInts];
+    __shared__ volatile int s_stop;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     T *const sval0 = reinterpret_cast<T *>(smem);
     int32_t *const scol0 = reinterpret_cast<int32_t *>(smem + kSlots * kStageEntries * sizeof(T));
+    // shape 3: 16-bit column positions after the values, then the input-row window areas
+    uint16_t *const slc0 = reinterpret_cast<uint16_t *>(smem + kSlots * kStageEntries * sizeof(T));
+    double *const sx0 = reinterpret_cast<double *>(smem + kSlots * kStageEntries * (sizeof(T) + 2));
 
     const uint64_t t_start = tr ? globaltimer() : 0;
     // trace counters (see mpk_read_trace); s_tarr: time of each slot's last hand-over
@@ -498,17 +773,212 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
     if (tid == 0) {
         s_epoch = (int32_t)ld_relaxed(reinterpret_cast<const int32_t *>(a.epoch_word)) + 1;
         s_final = -1;
+        s_stop = 0;
+        for (int q = 0; q < kDoneRing; ++q) s_done[q] = 0;
         for (int q = 0; q < kSlots; ++q) {
-            s_done[q] = 0;
             mbar_init(&s_full[q], 1);
             mbar_init(&s_empty[q], kCompWarps);
         }
+        if constexpr (kCtl == 2)
+            for (int q = 0; q < kRing; ++q) {
+                mbar_init(&s_rfull[q], 1);
+                mbar_init(&s_rfree[q], 1);
+            }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     const int32_t epoch = s_epoch;
 
-    if (warp == 0) {
+    if (warp < kCtl) {
+      if constexpr (kCtl == 2) {
+        // ---------------------------------------------------------- split control (shape 3)
+        // Warp 0 claims units in ticket order, polls their dependencies and pushes each ready
+        // unit (its id and chunk record) into a ring of kRing entries; warp 1 takes them in
+        // the same order, waits for a free slot, copies the entries and input rows and hands
+        // the slot over.  Each warp has one round trip per unit on its path, and the two run
+        // side by side.  The poll's acquire reaches the stage warp through the ring's
+        // mbarrier (release / acquire at CTA scope) and the compute warps through full[b].
+        // An end marker (unit -1) closes the ring; a stage warp that gives up sets s_stop.
+        const int32_t *rec = reinterpret_cast<const int32_t *>(a.chunk_rec);
+        auto record_timeout = [&]() {
+            if (lane == 0 && atomicExch(a.err, epoch) != epoch) st_relaxed(a.err + 1, (int)MPK_ERR_TIMEOUT);
+        };
+        if (warp == 0) {
+            // ------------------------------------------------------ poll warp
+            auto unit_at = [&](unsigned int t) -> int { return (int64_t)t < a.nunits ? __ldg(a.units + t) : -1; };
+            auto rec_at = [&](int un) -> int {
+                return (un >= 0 && lane < kRecInts) ? __ldg(rec + kRecInts * (int64_t)(un >> 5) + lane) : 0;
+            };
+            int u_cur = -1, u_nxt = -1, u_nn = -1;
+            unsigned int t = 0;
+            if (lane == 0) {
+                const unsigned int t0 = atomicAdd(a.ticket, 1u);
+                const unsigned int t1 = atomicAdd(a.ticket, 1u);
+                const unsigned int t2 = atomicAdd(a.ticket, 1u);
+                t = atomicAdd(a.ticket, 1u);
+                u_cur = unit_at(t0);
+                u_nxt = unit_at(t1);
+                u_nn = unit_at(t2);
+            }
+            u_cur = __shfl_sync(0xffffffffu, u_cur, 0);
+            u_nxt = __shfl_sync(0xffffffffu, u_nxt, 0);
+            int r_cur = rec_at(u_cur);
+            int r_nxt = rec_at(u_nxt);
+            // waits for ring entry q to be free again (consumed kRing pushes ago)
+            auto ring_free = [&](int i) -> bool {
+                if (i < kRing) return true;
+                const int q = i % kRing;
+                const uint64_t t0 = globaltimer();
+                while (!mbar_try_wait(&s_rfree[q], ((i / kRing) - 1) & 1)) {
+                    if (s_stop) return false;
+                    if (timed_out(t0, a.wait_ns)) {
+                        record_timeout();
+                        return false;
+                    }
+                }
+                return true;
+            };
+            for (int i = 0;; ++i) {
+                const int q = i % kRing;
+                bool aborted = false;
+                if (u_cur >= 0) {
+                    const int k = u_cur & 31;
+                    int dlo[kDepRanges], dlen[kDepRanges];
+                    const int total = dep_ranges_of(r_cur, dlo, dlen);
+                    if (k > 1) {
+                        const uint64_t t0 = globaltimer();
+                        while (!deps_ready(a, epoch, k, dlo, dlen, total, lane)) {
+                            if (lane == 0) tr_add(2, 1);
+                            const bool stop = ld_relaxed(a.err) == epoch || timed_out(t0, a.wait_ns) || s_stop;
+                            if (__any_sync(0xffffffffu, stop)) {
+                                aborted = true;
+                                break;
+                            }
+                            __nanosleep(32);
+                        }
+                        if (tr && lane == 0) tr_add(1, globaltimer() - t0);
+                    }
+                    if (lane == 0) tr_add(0, 1);
+                }
+                if (aborted) record_timeout();
+                const bool last = u_cur < 0 || aborted;
+                if (!ring_free(i)) break;  // the stage warp stopped, or a wait expired
+                if (lane < kRecInts) s_ring_rec[q][lane] = last ? 0 : r_cur;
+                if (lane == 0) s_ring_unit[q] = last ? -1 : u_cur;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&s_rfull[q]);
+                if (last) break;
+                const int u2 = __shfl_sync(0xffffffffu, u_nn, 0);
+                const int r2 = rec_at(u2);
+                int u3 = -1;
+                unsigned int t_next = t;
+                if (lane == 0) {
+                    u3 = unit_at(t);
+                    t_next = atomicAdd(a.ticket, 1u);
+                }
+                u_cur = u_nxt;
+                r_cur = r_nxt;
+                u_nxt = u2;
+                r_nxt = r2;
+                u_nn = u3;
+                t = t_next;
+            }
+        } else {
+            // ------------------------------------------------------ stage warp
+            bool slot_busy[kSlots] = {};
+            int slot_use[kSlots] = {};
+            int i = 0;
+            for (;; ++i) {
+                const int q = i % kRing, b = i % kSlots;
+                {
+                    const uint64_t t0 = globaltimer();
+                    bool ok;
+                    while (!(ok = mbar_try_wait(&s_rfull[q], (i / kRing) & 1)))
+                        if (timed_out(t0, 2 * a.wait_ns + 100000000LL)) break;
+                    if (tr && lane == 0) tr_add(12, globaltimer() - t0);
+                    if (!ok) {  // the poll warp gave no sign of life
+                        record_timeout();
+                        break;
+                    }
+                }
+                const int un = s_ring_unit[q];
+                const int r_cur = lane < kRecInts ? s_ring_rec[q][lane] : 0;
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&s_rfree[q]);
+                if (un < 0) break;  // end of the units
+                UnitInfo u;
+                u.unit = un;
+                u.row0 = __shfl_sync(0xffffffffu, r_cur, 0);
+                u.row1 = __shfl_sync(0xffffffffu, r_cur, 1);
+                u.slice0 = __shfl_sync(0xffffffffu, r_cur, 2);
+                u.ecount = __shfl_sync(0xffffffffu, r_cur, 3);
+                u.ebase = (long long)(unsigned int)__shfl_sync(0xffffffffu, r_cur, 4) |
+                          ((long long)__shfl_sync(0xffffffffu, r_cur, 5) << 32);
+                u.staged = __shfl_sync(0xffffffffu, r_cur, 6);
+                u.nsl = __shfl_sync(0xffffffffu, r_cur, 7);
+#pragma unroll
+                for (int w = 0; w < 4; ++w) u.widths[w] = __shfl_sync(0xffffffffu, r_cur, 16 + w);
+                const int k = un & 31;
+                XCopy xc{0, 0, 0, 0, 0};
+                uint32_t xbytes = 0;
+                if constexpr (XS) {
+                    const int wsrc = kRecWin + 3 * (lane & (kXWin - 1));
+                    const int wlo = __shfl_sync(0xffffffffu, r_cur, wsrc);
+                    const int wlen = __shfl_sync(0xffffffffu, r_cur, wsrc + 1);
+                    const int wpos = __shfl_sync(0xffffffffu, r_cur, wsrc + 2);
+                    if (lane < kXWin)
+                        xc = x_copy<M>(input_block<M>(a, k), a.n, wlo, wlen, wpos, smem_u32(sx0 + b * Shape<SH>::XW));
+                    xbytes = xc.bytes;
+#pragma unroll
+                    for (int o = 1; o < kXWin; o <<= 1) xbytes += __shfl_xor_sync(0xffffffffu, xbytes, o);
+                }
+                if (slot_busy[b]) {
+                    const uint64_t t0 = globaltimer();
+                    bool ok;
+                    while (!(ok = mbar_try_wait(&s_empty[b], slot_use[b] & 1)))
+                        if (timed_out(t0, a.wait_ns)) break;
+                    if (tr && lane == 0) tr_add(3, globaltimer() - t0);
+                    if (!ok) {
+                        record_timeout();
+                        break;
+                    }
+                    slot_busy[b] = false;
+                }
+                if (lane == 0) {
+                    s_u[b] = u;
+                    if (u.staged) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        constexpr uint32_t cb = XS ? 2u : (kStageCol ? 4u : 0u);
+                        mbar_expect_tx_only(&s_full[b], (uint32_t)u.ecount * (uint32_t)(sizeof(T) + cb) + xbytes);
+                        bulk_g2s(sval0 + b * kStageEntries, static_cast<const T *>(a.val) + u.ebase,
+                                 (uint32_t)(u.ecount * sizeof(T)), &s_full[b]);
+                        if constexpr (XS)
+                            bulk_g2s(slc0 + b * kStageEntries, a.lcol + u.ebase, (uint32_t)u.ecount * 2u, &s_full[b]);
+                        else if (kStageCol)
+                            bulk_g2s(scol0 + b * kStageEntries, a.col + u.ebase, (uint32_t)u.ecount * 4u, &s_full[b]);
+                    }
+                }
+                if constexpr (XS) {
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                    __syncwarp();
+                    if (u.staged && xc.bytes) bulk_g2s_addr(xc.dst, xc.src, xc.bytes, &s_full[b]);
+                    if (u.staged && xc.tail) {
+                        const double v = *reinterpret_cast<const double *>(xc.tail);
+                        asm volatile("st.shared.f64 [%0], %1;" ::"r"(xc.tdst), "d"(v) : "memory");
+                    }
+                }
+                __syncwarp();
+                if (tr && lane == 0) s_tarr[b] = globaltimer();
+                if (lane == 0) mbar_arrive(&s_full[b]);
+                slot_busy[b] = true;
+                slot_use[b] = i / kSlots;
+            }
+            if (lane == 0) {
+                s_stop = 1;     // the poll warp pushes nothing more
+                s_final = i;    // units 0..i-1 were handed over
+            }
+        }
+      } else {
         // ------------------------------------------------------------------ control warp
         const int32_t *rec = reinterpret_cast<const int32_t *>(a.chunk_rec);
         bool slot_busy[kSlots] = {};  // a handed-over unit may still be computed
@@ -518,13 +988,13 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
             if (lane == 0 && atomicExch(a.err, epoch) != epoch) st_relaxed(a.err + 1, (int)MPK_ERR_TIMEOUT);
         };
         auto unit_at = [&](unsigned int t) -> int { return (int64_t)t < a.nunits ? __ldg(a.units + t) : -1; };
+        auto rec_at = [&](int un) -> int {
+            return (un >= 0 && lane < kRecInts) ? __ldg(rec + kRecInts * (int64_t)(un >> 5) + lane) : 0;
+        };
         // claim pipeline, three units deep: unit i (id u_cur, record r_cur), unit i+1 (u_nxt,
         // r_nxt), unit i+2 (id u_nn, held by lane 0) and the ticket t of unit i+3.  At the end
         // of iteration i the record of unit i+2, the id of unit i+3 and one more ticket are
         // fetched, each a full iteration before it is needed.
-        auto rec_at = [&](int un) -> int {
-            return (un >= 0 && lane < kRecInts) ? __ldg(rec + kRecInts * (int64_t)(un >> 5) + lane) : 0;
-        };
         int u_cur = -1, u_nxt = -1, u_nn = -1;
         unsigned int t = 0;
         if (lane == 0) {
@@ -560,7 +1030,50 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
             for (int q = 0; q < 4; ++q) u.widths[q] = __shfl_sync(0xffffffffu, r_cur, 16 + q);
             int dlo[kDepRanges], dlen[kDepRanges];
             const int total = dep_ranges_of(r_cur, dlo, dlen);
+            const int k = u.unit & 31;
+            // shape 3: lane q < kXWin prepares the copy of input-row window q
+            XCopy xc{0, 0, 0, 0, 0};
+            uint32_t xbytes = 0;
+            if constexpr (XS) {
+                const int wsrc = kRecWin + 3 * (lane & (kXWin - 1));
+                const int wlo = __shfl_sync(0xffffffffu, r_cur, wsrc);
+                const int wlen = __shfl_sync(0xffffffffu, r_cur, wsrc + 1);
+                const int wpos = __shfl_sync(0xffffffffu, r_cur, wsrc + 2);
+                if (lane < kXWin)
+                    xc = x_copy<M>(input_block<M>(a, k), a.n, wlo, wlen, wpos,
+                                   smem_u32(sx0 + b * Shape<SH>::XW));
+                xbytes = xc.bytes;
+#pragma unroll
+                for (int o = 1; o < kXWin; o <<= 1) xbytes += __shfl_xor_sync(0xffffffffu, xbytes, o);
+            }
             if (tr && lane == 0) tr_add(11, clock64() - c0);
+            // dependencies of unit i: all lanes poll its flags (acquire)
+            auto poll_deps = [&]() {
+                if (k > 1) {
+                    const uint64_t t0 = globaltimer();
+                    while (!deps_ready(a, epoch, k, dlo, dlen, total, lane)) {
+                        if (lane == 0) tr_add(2, 1);
+                        const bool stop = ld_relaxed(a.err) == epoch || timed_out(t0, a.wait_ns);
+                        if (__any_sync(0xffffffffu, stop)) {
+                            aborted = true;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                    if (tr && lane == 0) tr_add(1, globaltimer() - t0);
+                }
+            };
+            // Shape 3 polls first, while slot b may still be in use: its entries and input
+            // rows are then copied together as soon as the slot is free.  Nothing has been
+            // staged for unit i if the poll gives up: the compute warps stop before it.
+            if constexpr (XS) {
+                poll_deps();
+                if (aborted) {
+                    record_timeout();
+                    if (lane == 0) s_final = i;
+                    break;
+                }
+            }
             // slot b held unit i-kSlots: wait until it is computed before reusing the slot
             if (slot_busy[b]) {
                 const uint64_t t0 = globaltimer();
@@ -575,35 +1088,24 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
                 }
                 slot_busy[b] = false;
             }
-            // stage the entries
+            // stage the entries (and announce the window bytes, copied after the poll)
             const long long c2 = tr ? clock64() : 0;
             if (lane == 0) {
                 s_u[b] = u;
                 if (u.staged) {
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    mbar_expect_tx_only(&s_full[b], (uint32_t)u.ecount * (uint32_t)(sizeof(T) + (kStageCol ? 4 : 0)));
+                    constexpr uint32_t cb = XS ? 2u : (kStageCol ? 4u : 0u);
+                    mbar_expect_tx_only(&s_full[b], (uint32_t)u.ecount * (uint32_t)(sizeof(T) + cb) + xbytes);
                     bulk_g2s(sval0 + b * kStageEntries, static_cast<const T *>(a.val) + u.ebase,
                              (uint32_t)(u.ecount * sizeof(T)), &s_full[b]);
-                    if (kStageCol)
+                    if constexpr (XS)
+                        bulk_g2s(slc0 + b * kStageEntries, a.lcol + u.ebase, (uint32_t)u.ecount * 2u, &s_full[b]);
+                    else if (kStageCol)
                         bulk_g2s(scol0 + b * kStageEntries, a.col + u.ebase, (uint32_t)u.ecount * 4u, &s_full[b]);
                 }
             }
             if (tr && lane == 0) tr_add(8, clock64() - c2);
-            // dependencies of unit i
-            const int k = u.unit & 31;
-            if (k > 1) {
-                const uint64_t t0 = globaltimer();
-                while (!deps_ready(a, epoch, k, dlo, dlen, total, lane)) {
-                    if (lane == 0) tr_add(2, 1);
-                    const bool stop = ld_relaxed(a.err) == epoch || timed_out(t0, a.wait_ns);
-                    if (__any_sync(0xffffffffu, stop)) {
-                        aborted = true;
-                        break;
-                    }
-                    __nanosleep(32);
-                }
-                if (tr && lane == 0) tr_add(1, globaltimer() - t0);
-            }
+            if constexpr (!XS) poll_deps();
             if (lane == 0) tr_add(0, 1);
             if (aborted) {
                 // unit i is not handed over: the compute warps stop before it.  Complete the
@@ -624,6 +1126,17 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
             // acquire: the flags before the compute warps' reads (via full[b]); units of power
             // 1 read only x0, written before the launch, and poll nothing
             if (k > 1 && !kAcquirePoll) fence_acq_rel_gpu();
+            if constexpr (XS) {
+                // the input rows were written through the generic proxy and are now read by
+                // bulk copies (async proxy): order the acquired writes before those reads
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+                __syncwarp();
+                if (u.staged && xc.bytes) bulk_g2s_addr(xc.dst, xc.src, xc.bytes, &s_full[b]);
+                if (u.staged && xc.tail) {
+                    const double v = *reinterpret_cast<const double *>(xc.tail);
+                    asm volatile("st.shared.f64 [%0], %1;" ::"r"(xc.tdst), "d"(v) : "memory");
+                }
+            }
             __syncwarp();
             if (tr && lane == 0) s_tarr[b] = globaltimer();
             if (lane == 0) mbar_arrive(&s_full[b]);
@@ -650,9 +1163,10 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
             if (tr && lane == 0) tr_add(10, clock64() - c5);
         }
         if (lane == 0 && s_final < 0) s_final = i;  // units 0..i-1 were handed over
+      }
     } else {
         // ------------------------------------------------------------------ compute warps
-        const int cw = warp - 1;
+        const int cw = warp - kCtl;
         Prefetch<M> pf;
         pf.unit = -1;
         for (int i = 0;; ++i) {
@@ -693,7 +1207,11 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
                     tr_add(15, 1);
                 }
             }
-            {
+            if constexpr (XS) {
+                const long long c1 = tr ? clock64() : 0;
+                phase_x<M, MODE, VT, SH>(a, epoch, s_u, b, sval0, slc0, sx0, s_done, s_empty, cw, lane, i);
+                if (tr && lane == 0) tr_add(13, clock64() - c1);
+            } else {
                 const long long c0 = tr ? clock64() : 0;
                 phase_a<M, (kStageEntries > 0)>(a, s_u[b], b, kStageCol ? scol0 + b * kStageEntries : a.col + s_u[b].ebase,
                                                  cw, lane, pf);
@@ -705,10 +1223,10 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
                     asm volatile("add.u32 %0, %1, 0;" : "=r"(d) : "r"(h));
                     const long long c1 = clock64();
                     if (lane == 0) tr_add(12, c1 - c0);
-                    phase_b<M, MODE, VT, SH>(a, epoch, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane);
+                    phase_b<M, MODE, VT, SH>(a, epoch, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane, i);
                     if (lane == 0) tr_add(13, clock64() - c1);
                 } else {
-                    phase_b<M, MODE, VT, SH>(a, epoch, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane);
+                    phase_b<M, MODE, VT, SH>(a, epoch, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane, i);
                 }
                 pf.unit = -1;
             }
@@ -772,5 +1290,6 @@ template <int SH> int smem_bytes_shape(int vtype) {
 void *select_mpk_shape0(int mode, int m, bool trace, int vtype);
 void *select_mpk_shape1(int mode, int m, bool trace, int vtype);
 void *select_mpk_shape2(int mode, int m, bool trace, int vtype);
+void *select_mpk_shape3(int mode, int m, bool trace, int vtype);
 
 }  // namespace mpk

@@ -75,6 +75,7 @@ extern "C" mpk_status mpk_apply_noalloc(const mpk_plan_t *Ph, const double *X, i
             std::memset(&a, 0, sizeof(a));
             a.val = P.val;
             a.col = P.col;
+            a.lcol = P.lcol;
             a.slice_ptr = P.slice_ptr;
             a.rowlen = P.rowlen;
             a.chunk_row = P.chunk_row;

@@ -3,6 +3,7 @@
 #include "mpk_internal.h"
 
 #include <algorithm>
+#include <climits>
 
 namespace mpk {
 
@@ -167,12 +168,73 @@ __global__ void k_dep_ranges(int32_t nchunks, const int2 *hull, const int64_t *w
     }
 }
 
+// Input-row windows of shape 3: for chunk c and its dependency range q, the smallest and the
+// largest column (plan numbering) that a row of c reads from the chunks of range q.  The
+// ranges are disjoint and cover every chunk that c reads, so the windows are disjoint and
+// hold every column of c.  xw[kXWin * c + q] = (min, max), (INT_MAX, -1) when c reads none.
+__global__ void k_xwin(int32_t n, const int32_t *rowlen, const int32_t *chunk_row, const int32_t *chunk_slice,
+                       const int32_t *cor, const int64_t *slice_ptr, const int32_t *scol, const int4 *ranges,
+                       int2 *xw) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
+        const int32_t c = cor[r];
+        const int32_t local = (int32_t)r - chunk_row[c];
+        const int64_t base = slice_ptr[chunk_slice[c] + (local >> 5)] + (local & 31);
+        const int4 r0 = ranges[2 * c], r1 = ranges[2 * c + 1];
+        const int32_t rlo[kXWin] = {r0.x, r0.z, r1.x, r1.z}, rhi[kXWin] = {r0.y, r0.w, r1.y, r1.w};
+        int32_t mn[kXWin], mx[kXWin];
+        for (int q = 0; q < kXWin; ++q) {
+            mn[q] = INT_MAX;
+            mx[q] = -1;
+        }
+        for (int32_t j = 0; j < rowlen[r]; ++j) {
+            const int32_t col = scol[base + 32 * (int64_t)j];
+            const int32_t cc = cor[col];
+            for (int q = 0; q < kXWin; ++q)
+                if (cc >= rlo[q] && cc <= rhi[q]) {
+                    mn[q] = min(mn[q], col);
+                    mx[q] = max(mx[q], col);
+                    break;
+                }
+        }
+        for (int q = 0; q < kXWin; ++q)
+            if (mx[q] >= 0) {
+                atomicMin(&xw[kXWin * c + q].x, mn[q]);
+                atomicMax(&xw[kXWin * c + q].y, mx[q]);
+            }
+    }
+}
+
+// 16-bit position of every entry's column in its chunk's window area: the window q holding
+// the column (win[3 kXWin c + 3q ..] = first row, rows, position in rows) gives
+// position + column - first row.  Padding keeps 0xffff.
+__global__ void k_lcol(int32_t n, const int32_t *rowlen, const int32_t *chunk_row, const int32_t *chunk_slice,
+                       const int32_t *cor, const int64_t *slice_ptr, const int32_t *scol, const int32_t *win,
+                       uint16_t *lcol) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += stride) {
+        const int32_t c = cor[r];
+        const int32_t local = (int32_t)r - chunk_row[c];
+        const int64_t base = slice_ptr[chunk_slice[c] + (local >> 5)] + (local & 31);
+        const int32_t *w = win + 3 * kXWin * (int64_t)c;
+        for (int32_t j = 0; j < rowlen[r]; ++j) {
+            const int32_t col = scol[base + 32 * (int64_t)j];
+            for (int q = 0; q < kXWin; ++q)
+                if (w[3 * q + 1] > 0 && col >= w[3 * q] && col < w[3 * q] + w[3 * q + 1]) {
+                    lcol[base + 32 * (int64_t)j] = (uint16_t)(w[3 * q + 2] + col - w[3 * q]);
+                    break;
+                }
+        }
+    }
+}
+
 // One record of kRecInts ints per chunk with everything the kernel's control warp needs:
 // [row0, row1, slice0, padded entries, first entry (lo, hi 32 bits), staged, slices,
 //  kDepRanges (lo, hi) dependency ranges, slice widths as bytes].  A chunk is staged in
 // shared memory when its entries fit a buffer and its widths fit the record.
 __global__ void k_chunk_records(int32_t nchunks, const int32_t *chunk_row, const int32_t *chunk_slice,
-                                const int64_t *slice_ptr, const int4 *ranges, int32_t stage_entries, int32_t *rec) {
+                                const int64_t *slice_ptr, const int4 *ranges, int32_t stage_entries, const int32_t *win,
+                                int32_t *rec) {
     for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nchunks; c += gridDim.x * blockDim.x) {
         const int32_t sl0 = chunk_slice[c], sl1 = chunk_slice[c + 1], nsl = sl1 - sl0;
         const int64_t e0 = slice_ptr[sl0], e1 = slice_ptr[sl1];
@@ -197,6 +259,7 @@ __global__ void k_chunk_records(int32_t nchunks, const int32_t *chunk_row, const
                 wb[q >> 2] |= (w & 0xffu) << (8 * (q & 3));
             }
         for (int q = 0; q < kRecSlices / 4; ++q) o[16 + q] = (int32_t)wb[q];
+        for (int q = 0; q < 3 * kXWin; ++q) o[kRecWin + q] = win ? win[3 * kXWin * (int64_t)c + q] : 0;
     }
 }
 
@@ -400,57 +463,33 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         // ---- block shape: shape 0 when its slot holds a full chunk of slices of the mean
         //      width, else shape 1 when its slot holds at least a third of a chunk, else
         //      unstaged (measured: 27-point stencils run 1.7x faster unstaged, banded graphs
-        //      of ~15 entries a row 10% faster on shape 1)
+        //      of ~15 entries a row 10% faster on shape 1).  Shape 3 (input rows staged too)
+        //      is taken only when the options name it; it is not chosen automatically, since on
+        //      the 3-D Laplacian it measured slower than shape 0 (its control warp, not the
+        //      FP64 pipe, sets the pace).
         if (o->shape < 0 || o->shape > kNumShapes) fail(MPK_ERR_INVALID, "shape must be in [0, %d]", kNumShapes);
+        int fallback_shape = 0;
+        bool try_x = false;
         if (o->shape > 0) {
-            P->shape = o->shape - 1;
+            fallback_shape = o->shape - 1;
+            try_x = fallback_shape == kShapeX;
         } else {
             auto fits = [&](int sh, int slices) {
                 return (int64_t)slices * P->padded <= (int64_t)kShapes[sh].stage_entries * std::max(NS, 1);
             };
-            P->shape = fits(0, kShapes[0].comp_warps) ? 0 : (fits(1, kShapes[1].comp_warps / 3) ? 1 : 2);
+            fallback_shape = fits(0, kShapes[0].comp_warps) ? 0 : (fits(1, kShapes[1].comp_warps / 3) ? 1 : 2);
+            try_x = false;
         }
-        const int32_t stage_entries = kShapes[P->shape].stage_entries;
-        const int64_t chunk_entries = stage_entries > 0 ? stage_entries : INT64_MAX;
-        if (chunk_rows == 0) chunk_rows = 32 * kShapes[P->shape].comp_warps;
-        P->chunk_rows = chunk_rows;
+        const bool x_forced = o->shape - 1 == kShapeX;
 
-        // ---- chunks: consecutive slices of one group, at most chunk_rows rows and at most
-        //      stage_entries padded entries (a single wider slice forms its own chunk)
-        std::vector<int32_t> c_row, c_slice, g_chunk;
-        c_row.push_back(0);
-        c_slice.push_back(0);
-        for (int32_t g = 0; g < G; ++g) {
-            g_chunk.push_back((int32_t)c_row.size() - 1);
-            int32_t s0 = g_slice[g];
-            while (s0 < g_slice[g + 1]) {
-                int32_t s1 = s0 + 1;
-                while (s1 < g_slice[g + 1] && s_row[s1 + 1] - s_row[s0] <= chunk_rows &&
-                       sptr[s1 + 1] - sptr[s0] <= chunk_entries)
-                    ++s1;
-                c_row.push_back(s_row[s1]);
-                c_slice.push_back(s1);
-                s0 = s1;
-            }
-        }
-        g_chunk.push_back((int32_t)c_row.size() - 1);
-        const int32_t NC = (int32_t)c_row.size() - 1;
-        P->h_chunk_row = c_row;
-        if (NC >= (1 << 26)) fail(MPK_ERR_TOO_LARGE, "too many chunks (%d)", NC);
-        P->num_chunks = NC;
-        P->chunk_row = P->arena.alloc_n<int32_t>(NC + 1);
-        P->chunk_slice = P->arena.alloc_n<int32_t>(NC + 1);
+        // ---- sliced copy and group tables (independent of the chunks)
         P->group_row_ptr = P->arena.alloc_n<int32_t>(G + 1);
-        MPK_CUDA(cudaMemcpyAsync(P->chunk_row, c_row.data(), sizeof(int32_t) * (NC + 1), cudaMemcpyHostToDevice, s));
-        MPK_CUDA(cudaMemcpyAsync(P->chunk_slice, c_slice.data(), sizeof(int32_t) * (NC + 1), cudaMemcpyHostToDevice, s));
         MPK_CUDA(cudaMemcpyAsync(P->group_row_ptr, g_row.data(), sizeof(int32_t) * (G + 1), cudaMemcpyHostToDevice, s));
         if (!P->identity) {
             P->group_level_ptr = P->arena.alloc_n<int32_t>(G + 1);
             MPK_CUDA(cudaMemcpyAsync(P->group_level_ptr, g_level.data(), sizeof(int32_t) * (G + 1),
                                      cudaMemcpyHostToDevice, s));
         }
-
-        // ---- sliced copy
         P->slice_ptr = P->arena.alloc_n<int64_t>((int64_t)NS + 1);
         MPK_CUDA(cudaMemcpyAsync(P->slice_ptr, sptr.data(), sizeof(int64_t) * ((size_t)NS + 1), cudaMemcpyHostToDevice, s));
         Tmp<int32_t> cor(n);
@@ -458,71 +497,187 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         P->col = P->arena.alloc_n<int32_t>(P->padded + 32);
         MPK_CUDA(cudaMemsetAsync(P->val, 0, (size_t)P->val_bytes * (size_t)(P->padded + 32), s));  // +0 in every type
         MPK_CUDA(cudaMemsetAsync(P->col, 0xff, sizeof(int32_t) * (size_t)(P->padded + 32), s));  // padding: col = -1
-        P->dep = P->arena.alloc_n<int2>(NC > 0 ? NC : 1);
-        if (NC > 0) {
-            k_dep_init<<<grid_n(NC), 256, 0, s>>>(P->dep, NC);
-            MPK_LAUNCHED();
-            k_chunk_of_row<<<grid_n((int64_t)NC * 256), 256, 0, s>>>(P->chunk_row, NC, cor.p);
-            MPK_LAUNCHED();
+
+        std::vector<int32_t> c_row, c_slice, g_chunk;
+        std::vector<int32_t> h_win;  // shape 3: kXWin (first row, rows, position) per chunk
+        int32_t NC = 0, stage_entries = 0;
+        for (int attempt = 0;; ++attempt) {
+            P->shape = (attempt == 0 && try_x) ? kShapeX : fallback_shape;
+            if (attempt > 0 && P->shape == kShapeX) fail(MPK_ERR_UNSUPPORTED, "block shape 3 does not fit this plan");
+            stage_entries = kShapes[P->shape].stage_entries;
+            const int64_t chunk_entries = stage_entries > 0 ? stage_entries : INT64_MAX;
+            chunk_rows = o->chunk_rows ? o->chunk_rows : 32 * kShapes[P->shape].comp_warps;
+            P->chunk_rows = chunk_rows;
+
+            // ---- chunks: consecutive slices of one group, at most chunk_rows rows and at most
+            //      stage_entries padded entries (a single wider slice forms its own chunk)
+            c_row.assign(1, 0);
+            c_slice.assign(1, 0);
+            g_chunk.clear();
+            for (int32_t g = 0; g < G; ++g) {
+                g_chunk.push_back((int32_t)c_row.size() - 1);
+                int32_t s0 = g_slice[g];
+                while (s0 < g_slice[g + 1]) {
+                    int32_t s1 = s0 + 1;
+                    while (s1 < g_slice[g + 1] && s_row[s1 + 1] - s_row[s0] <= chunk_rows &&
+                           sptr[s1 + 1] - sptr[s0] <= chunk_entries)
+                        ++s1;
+                    c_row.push_back(s_row[s1]);
+                    c_slice.push_back(s1);
+                    s0 = s1;
+                }
+            }
+            g_chunk.push_back((int32_t)c_row.size() - 1);
+            NC = (int32_t)c_row.size() - 1;
+            P->h_chunk_row = c_row;
+            if (NC >= (1 << 26)) fail(MPK_ERR_TOO_LARGE, "too many chunks (%d)", NC);
+            P->num_chunks = NC;
+            P->chunk_row = P->arena.alloc_n<int32_t>(NC + 1);
+            P->chunk_slice = P->arena.alloc_n<int32_t>(NC + 1);
+            MPK_CUDA(cudaMemcpyAsync(P->chunk_row, c_row.data(), sizeof(int32_t) * (NC + 1), cudaMemcpyHostToDevice, s));
+            MPK_CUDA(cudaMemcpyAsync(P->chunk_slice, c_slice.data(), sizeof(int32_t) * (NC + 1), cudaMemcpyHostToDevice,
+                                     s));
+
+            // ---- fill the sliced copy; dependency hulls of the chunks
+            P->dep = P->arena.alloc_n<int2>(NC > 0 ? NC : 1);
+            if (NC > 0) {
+                k_dep_init<<<grid_n(NC), 256, 0, s>>>(P->dep, NC);
+                MPK_LAUNCHED();
+                k_chunk_of_row<<<grid_n((int64_t)NC * 256), 256, 0, s>>>(P->chunk_row, NC, cor.p);
+                MPK_LAUNCHED();
 #define FILL(T)                                                                                            \
     k_fill<T><<<grid_n(n), 256, 0, s>>>(n, A->row_ptr, A->col, static_cast<const T *>(A->val), P->perm,    \
                                         P->iperm, P->chunk_row, P->chunk_slice, cor.p, P->slice_ptr,         \
                                         static_cast<T *>(P->val), P->col, P->dep, A->is_symmetric ? 1 : 0, special.p)
-            Tmp<int32_t> special(1);
-            MPK_CUDA(cudaMemsetAsync(special.p, 0, sizeof(int32_t), s));
-            if (P->val_type == MPK_F64)
-                FILL(double);
-            else if (P->val_type == MPK_F32)
-                FILL(float);
-            else
-                FILL(uint16_t);
+                Tmp<int32_t> special(1);
+                MPK_CUDA(cudaMemsetAsync(special.p, 0, sizeof(int32_t), s));
+                if (P->val_type == MPK_F64)
+                    FILL(double);
+                else if (P->val_type == MPK_F32)
+                    FILL(float);
+                else
+                    FILL(uint16_t);
 #undef FILL
-            MPK_LAUNCHED();
-            int32_t has_special = 0;
-            MPK_CUDA(cudaMemcpyAsync(&has_special, special.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-            MPK_CUDA(cudaStreamSynchronize(s));
-            if (has_special)
-                fail(MPK_ERR_UNSUPPORTED,
-                     "float32/bfloat16 storage holds zeros and normal numbers only (a value is subnormal, "
-                     "infinite or NaN in the narrow type): use MPK_F64 values");
-        }
-        // ---- dependency ranges: exact chunk sets as bitmaps over each hull, compressed
-        P->dep_ranges = P->arena.alloc_n<int4>(2 * (int64_t)(NC > 0 ? NC : 1));
-        if (NC > 0) {
-            std::vector<int2> hull((size_t)NC);
-            MPK_CUDA(cudaMemcpyAsync(hull.data(), P->dep, sizeof(int2) * (size_t)NC, cudaMemcpyDeviceToHost, s));
-            MPK_CUDA(cudaStreamSynchronize(s));
-            std::vector<int64_t> woff((size_t)NC + 1, 0);
-            for (int32_t c = 0; c < NC; ++c) woff[c + 1] = woff[c] + (hull[c].y - hull[c].x + 32) / 32;
-            const int64_t words = woff[NC];
-            if (words <= ((int64_t)1 << 27)) {
-                Tmp<int64_t> d_woff((int64_t)NC + 1);
-                Tmp<uint32_t> d_bits(words);
-                MPK_CUDA(cudaMemcpyAsync(d_woff.p, woff.data(), sizeof(int64_t) * ((size_t)NC + 1),
-                                         cudaMemcpyHostToDevice, s));
-                MPK_CUDA(cudaMemsetAsync(d_bits.p, 0, sizeof(uint32_t) * (size_t)words, s));
-                k_dep_bits<<<grid_n(n), 256, 0, s>>>(n, P->rowlen, P->chunk_row, P->chunk_slice, cor.p, P->slice_ptr,
-                                                     P->col, P->dep, d_woff.p, d_bits.p, A->is_symmetric ? 1 : 0);
                 MPK_LAUNCHED();
-                k_dep_ranges<<<grid_n(NC), 256, 0, s>>>(NC, P->dep, d_woff.p, d_bits.p, P->dep_ranges);
-                MPK_LAUNCHED();
+                int32_t has_special = 0;
+                MPK_CUDA(cudaMemcpyAsync(&has_special, special.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
                 MPK_CUDA(cudaStreamSynchronize(s));
-            } else {  // bitmaps too large: one range per chunk, the hull
-                std::vector<int4> rr((size_t)2 * NC);
-                for (int32_t c = 0; c < NC; ++c) {
-                    rr[2 * c] = make_int4(hull[c].x, hull[c].y, 0, -1);
-                    rr[2 * c + 1] = make_int4(0, -1, 0, -1);
-                }
-                MPK_CUDA(cudaMemcpyAsync(P->dep_ranges, rr.data(), sizeof(int4) * rr.size(), cudaMemcpyHostToDevice, s));
-                MPK_CUDA(cudaStreamSynchronize(s));
+                if (has_special)
+                    fail(MPK_ERR_UNSUPPORTED,
+                         "float32/bfloat16 storage holds zeros and normal numbers only (a value is subnormal, "
+                         "infinite or NaN in the narrow type): use MPK_F64 values");
             }
+            // ---- dependency ranges: exact chunk sets as bitmaps over each hull, compressed
+            P->dep_ranges = P->arena.alloc_n<int4>(2 * (int64_t)(NC > 0 ? NC : 1));
+            if (NC > 0) {
+                std::vector<int2> hull((size_t)NC);
+                MPK_CUDA(cudaMemcpyAsync(hull.data(), P->dep, sizeof(int2) * (size_t)NC, cudaMemcpyDeviceToHost, s));
+                MPK_CUDA(cudaStreamSynchronize(s));
+                std::vector<int64_t> woff((size_t)NC + 1, 0);
+                for (int32_t c = 0; c < NC; ++c) woff[c + 1] = woff[c] + (hull[c].y - hull[c].x + 32) / 32;
+                const int64_t words = woff[NC];
+                if (words <= ((int64_t)1 << 27)) {
+                    Tmp<int64_t> d_woff((int64_t)NC + 1);
+                    Tmp<uint32_t> d_bits(words);
+                    MPK_CUDA(cudaMemcpyAsync(d_woff.p, woff.data(), sizeof(int64_t) * ((size_t)NC + 1),
+                                             cudaMemcpyHostToDevice, s));
+                    MPK_CUDA(cudaMemsetAsync(d_bits.p, 0, sizeof(uint32_t) * (size_t)words, s));
+                    k_dep_bits<<<grid_n(n), 256, 0, s>>>(n, P->rowlen, P->chunk_row, P->chunk_slice, cor.p,
+                                                         P->slice_ptr, P->col, P->dep, d_woff.p, d_bits.p,
+                                                         A->is_symmetric ? 1 : 0);
+                    MPK_LAUNCHED();
+                    k_dep_ranges<<<grid_n(NC), 256, 0, s>>>(NC, P->dep, d_woff.p, d_bits.p, P->dep_ranges);
+                    MPK_LAUNCHED();
+                    MPK_CUDA(cudaStreamSynchronize(s));
+                } else {  // bitmaps too large: one range per chunk, the hull
+                    std::vector<int4> rr((size_t)2 * NC);
+                    for (int32_t c = 0; c < NC; ++c) {
+                        rr[2 * c] = make_int4(hull[c].x, hull[c].y, 0, -1);
+                        rr[2 * c + 1] = make_int4(0, -1, 0, -1);
+                    }
+                    MPK_CUDA(cudaMemcpyAsync(P->dep_ranges, rr.data(), sizeof(int4) * rr.size(), cudaMemcpyHostToDevice,
+                                             s));
+                    MPK_CUDA(cudaStreamSynchronize(s));
+                }
+            }
+            // ---- shape 3: input-row windows per chunk, laid out in the slot's window area
+            //      (rows from position 1 on, a gap of 2 / nrhs rows between windows, positions
+            //      of the parity of the first row when nrhs = 1; see x_copy in the kernel)
+            if (P->shape == kShapeX) {
+                bool ok = NC > 0;
+                h_win.assign((size_t)3 * kXWin * std::max(NC, 1), 0);
+                if (ok) {
+                    Tmp<int2> d_xw((int64_t)kXWin * NC);
+                    std::vector<int2> xw((size_t)kXWin * NC, make_int2(INT_MAX, -1));
+                    MPK_CUDA(cudaMemcpyAsync(d_xw.p, xw.data(), sizeof(int2) * xw.size(), cudaMemcpyHostToDevice, s));
+                    k_xwin<<<grid_n(n), 256, 0, s>>>(n, P->rowlen, P->chunk_row, P->chunk_slice, cor.p, P->slice_ptr,
+                                                     P->col, P->dep_ranges, d_xw.p);
+                    MPK_LAUNCHED();
+                    MPK_CUDA(cudaMemcpyAsync(xw.data(), d_xw.p, sizeof(int2) * xw.size(), cudaMemcpyDeviceToHost, s));
+                    MPK_CUDA(cudaStreamSynchronize(s));
+                    const int64_t XW = kShapes[kShapeX].x_words;
+                    for (int32_t c = 0; c < NC && ok; ++c) {
+                        // every chunk must be staged: its entries fit the slot and its widths the record
+                        if (c_slice[c + 1] - c_slice[c] > kRecSlices ||
+                            sptr[c_slice[c + 1]] - sptr[c_slice[c]] > stage_entries)
+                            ok = false;
+                        int64_t pos = 1;
+                        for (int q = 0; q < kXWin && ok; ++q) {
+                            const int2 w = xw[(size_t)kXWin * c + q];
+                            if (w.y < w.x) continue;
+                            const int64_t len = (int64_t)w.y - w.x + 1;
+                            if (m == 1 && ((pos ^ w.x) & 1)) ++pos;
+                            if (m * (pos + len) + 2 > XW) {
+                                ok = false;
+                                break;
+                            }
+                            int32_t *hw = &h_win[(size_t)3 * kXWin * c + 3 * q];
+                            hw[0] = w.x;
+                            hw[1] = (int32_t)len;
+                            hw[2] = (int32_t)pos;
+                            pos += len + (m == 1 ? 2 : 1);
+                        }
+                    }
+                }
+                if (!ok) {
+                    if (x_forced)
+                        fail(MPK_ERR_UNSUPPORTED,
+                             "block shape 3: a chunk's input rows do not fit a staging slot (fewer chunk_rows, or "
+                             "another shape)");
+                    P->arena.free(P->chunk_row);
+                    P->arena.free(P->chunk_slice);
+                    P->arena.free(P->dep);
+                    P->arena.free(P->dep_ranges);
+                    P->chunk_row = P->chunk_slice = nullptr;
+                    P->dep = nullptr;
+                    P->dep_ranges = nullptr;
+                    h_win.clear();
+                    continue;
+                }
+                Tmp<int32_t> d_win((int64_t)h_win.size());
+                MPK_CUDA(cudaMemcpyAsync(d_win.p, h_win.data(), sizeof(int32_t) * h_win.size(), cudaMemcpyHostToDevice,
+                                         s));
+                P->lcol = P->arena.alloc_n<uint16_t>(P->padded + 32);
+                MPK_CUDA(cudaMemsetAsync(P->lcol, 0xff, sizeof(uint16_t) * (size_t)(P->padded + 32), s));
+                k_lcol<<<grid_n(n), 256, 0, s>>>(n, P->rowlen, P->chunk_row, P->chunk_slice, cor.p, P->slice_ptr,
+                                                 P->col, d_win.p, P->lcol);
+                MPK_LAUNCHED();
+                MPK_CUDA(cudaStreamSynchronize(s));  // d_win goes out of scope
+            }
+            break;
         }
 
         P->chunk_rec = reinterpret_cast<int4 *>(P->arena.alloc_n<int32_t>((int64_t)kRecInts * (NC > 0 ? NC : 1)));
         if (NC > 0) {
+            Tmp<int32_t> d_win(P->shape == kShapeX ? (int64_t)h_win.size() : 0);
+            if (P->shape == kShapeX)
+                MPK_CUDA(cudaMemcpyAsync(d_win.p, h_win.data(), sizeof(int32_t) * h_win.size(), cudaMemcpyHostToDevice,
+                                         s));
             k_chunk_records<<<grid_n(NC), 256, 0, s>>>(NC, P->chunk_row, P->chunk_slice, P->slice_ptr, P->dep_ranges,
-                                                      stage_entries, reinterpret_cast<int32_t *>(P->chunk_rec));
+                                                      stage_entries, d_win.p,
+                                                      reinterpret_cast<int32_t *>(P->chunk_rec));
             MPK_LAUNCHED();
+            MPK_CUDA(cudaStreamSynchronize(s));
         }
 
         // ---- unit tables: Lp-diagram cells (group g, power k) along lines g + kSlotSkew*k

@@ -40,13 +40,27 @@ void *Arena::alloc(int64_t nbytes) {
         fail(MPK_ERR_OOM, "cudaMalloc(%lld) failed: %s", (long long)nbytes, cudaGetErrorString(e));
     }
     ptrs.push_back(p);
+    sizes.push_back(nbytes);
     bytes += nbytes;
     return p;
+}
+
+void Arena::free(void *p) {
+    if (!p) return;
+    for (size_t i = 0; i < ptrs.size(); ++i)
+        if (ptrs[i] == p) {
+            cudaFree(p);
+            bytes -= sizes[i];
+            ptrs.erase(ptrs.begin() + i);
+            sizes.erase(sizes.begin() + i);
+            return;
+        }
 }
 
 void Arena::release() {
     for (void *p : ptrs) cudaFree(p);
     ptrs.clear();
+    sizes.clear();
     bytes = 0;
 }
 

@@ -424,23 +424,76 @@ def test_apply_replays_from_cuda_graph(mpk):
         _check_powers(Ys, oracle.mpk(A, X, 6)[:, pe, :])
 
 
-@pytest.mark.parametrize("shape", [1, 2, 3])
-@pytest.mark.parametrize("name", ["lap3d_17x9x6", "band_3000", "int_nonsym_500", "xxz_10", "empty_rows"])
+@pytest.mark.parametrize("shape", [1, 2, 3, 4])
+@pytest.mark.parametrize("name", ["lap3d_17x9x6", "lap2d_64", "band_3000", "int_nonsym_500", "xxz_10", "empty_rows",
+                                  "disconnected", "single"])
 def test_apply_every_block_shape(mpk, shape, name):
-    # the three block shapes of the staged kernel (13 warps with 3072-entry slots, 15 warps
-    # with 4096, 15 warps reading entries from global memory) give the same bits
+    # the block shapes of the staged kernel (13 warps with 3072-entry slots, 15 warps with
+    # 4096, 15 warps reading entries from global memory, and input rows staged as well) give
+    # the same bits; shape 3 refuses a plan whose chunks read input rows beyond a slot
     make, sym = MATRICES[name]
     A = make()
     dA = _dev(A, mpk, sym)
     L = mpk.build_levels(dA, 0)
     X = gen.vector(A.n, 2, stream=98)
-    P = mpk.plan(dA, L, p_max=7, nrhs=2, cache_bytes=30000, shape=shape)
+    try:
+        P = mpk.plan(dA, L, p_max=7, nrhs=2, cache_bytes=30000, shape=shape)
+    except mpk.MpkError as e:
+        assert shape == 4 and e.status == 7
+        pytest.skip("input rows of a chunk exceed a shape-3 slot")
     assert P.describe()["shape"] == shape - 1
     Y = P.apply(torch.from_numpy(X).cuda(), 7, Y=_poisoned((8, A.n, 2)))
     P.sync_status()
     _check_powers(Y, oracle.mpk(A, X, 7))
     with pytest.raises(mpk.MpkError):
-        mpk.plan(dA, L, p_max=3, shape=4)
+        mpk.plan(dA, L, p_max=3, shape=5)
+
+
+@pytest.mark.parametrize("m", [1, 2])
+@pytest.mark.parametrize("order", [0, 1])
+def test_input_rows_staged_shape(mpk, m, order):
+    # shape 3 on grids whose chunks' input rows fit a slot: powers, Chebyshev, several cache
+    # budgets and chunk sizes (ragged last chunks, chunks over two levels), into NaN-poisoned
+    # outputs; the input vector starts 8 bytes past a 16-byte boundary in one of the runs
+    for A in (gen.laplacian_3d(21, 13, 11), gen.laplacian_2d(90, 70), gen.laplacian_3d(40, 40, 40)):
+        dA = _dev(A, mpk, True)
+        L = mpk.build_levels(dA, 0)
+        pe = L.perm.cpu().numpy()
+        X = gen.vector(A.n, m, stream=171)
+        Yo = oracle.mpk(A, X, 8)
+        built = 0
+        for cache, cr in ((30000, 0), (400000, 96), (0, 288), (0, 160)):
+            try:
+                P = mpk.plan(dA, L, p_max=8, nrhs=m, cache_bytes=cache, order=order, chunk_rows=cr, shape=4)
+            except mpk.MpkError as e:  # a chunk's input rows exceed a slot: refused, never wrong
+                assert e.status == 7
+                continue
+            built += 1
+            assert P.describe()["shape"] == 3
+            Xin = X if order == 0 else np.ascontiguousarray(X[pe])
+            for shift in (0, 1):
+                buf = torch.zeros(A.n * m + 1, dtype=torch.float64, device="cuda")
+                Xd = buf[shift:shift + A.n * m].view(A.n, m)
+                Xd.copy_(torch.from_numpy(Xin))
+                Y = P.apply(Xd, 8, Y=_poisoned((9, A.n, m)))
+                P.sync_status()
+                _check_powers(Y, Yo if order == 0 else Yo[:, pe, :])
+        assert built >= 2
+        if m == 2:
+            lo, hi = gen.gershgorin_bounds(A)
+            c = gen.uniform(gen.derive_seed(172), 20)
+            P = None
+            for cr in (0, 160, 96, 64):
+                try:
+                    P = mpk.plan(dA, L, p_max=8, nrhs=2, cache_bytes=60000, order=0, chunk_rows=cr, shape=4)
+                    break
+                except mpk.MpkError as e:
+                    assert e.status == 7
+            assert P is not None
+            got = P.cheb_filter(torch.from_numpy(X).cuda(), 19, c, scale=(hi - lo) / 2 * 1.01, shift=(hi + lo) / 2)
+            P.sync_status()
+            want = oracle.cheb(A, X, 19, c, scale=(hi - lo) / 2 * 1.01, shift=(hi + lo) / 2)
+            assert np.array_equal(got.cpu().numpy().view(np.uint64), want.view(np.uint64))
 
 
 def test_automatic_block_shape(mpk):
