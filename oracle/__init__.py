@@ -55,8 +55,12 @@ def _L():
             lib.orc_cheb.argtypes = [i32, _i32p, _i32p, _f64p, i32, _f64p, i32, _f64p, C.c_void_p,
                                      f64, f64, _f64p]
             lib.orc_bessel_j.argtypes = [i32, f64, _f64p]
+            lib.orc_mpk_acc32.argtypes = [i32, _i32p, _i32p, _f64p, i32, _f64p, i32, _f64p]
+            lib.orc_cheb_acc32.argtypes = [i32, _i32p, _i32p, _f64p, i32, _f64p, i32, _f64p, C.c_void_p,
+                                           f64, f64, _f64p]
             for f in ("orc_mpk", "orc_mpk_longdouble", "orc_levels", "orc_permute", "orc_groups",
-                      "orc_lp_labels", "orc_lb_mpk", "orc_cheb", "orc_bessel_j"):
+                      "orc_lp_labels", "orc_lb_mpk", "orc_cheb", "orc_bessel_j", "orc_mpk_acc32",
+                      "orc_cheb_acc32"):
                 getattr(lib, f).restype = C.c_int
             _lib = lib
     return _lib
@@ -86,6 +90,17 @@ def mpk(A, X, p: int) -> np.ndarray:
     m = X.shape[1]
     Y = np.empty((p + 1, A.n, m), dtype=np.float64)
     _check(_L().orc_mpk(A.n, rp, ci, va, m, X, p, Y), "mpk")
+    return Y
+
+
+def mpk_acc32(A, X, p: int) -> np.ndarray:
+    """Powers with binary32 row sums over binary32-rounded inputs, binary64 vectors (the
+    values of A must be exact in binary32); shape (p+1, n, m)."""
+    rp, ci, va = _csr(A)
+    X = _block(X, A.n)
+    m = X.shape[1]
+    Y = np.empty((p + 1, A.n, m), dtype=np.float64)
+    _check(_L().orc_mpk_acc32(A.n, rp, ci, va, m, X, p, Y), "mpk_acc32")
     return Y
 
 
@@ -168,6 +183,24 @@ def cheb(A, X, degree: int, coeff_re, coeff_im=None, scale: float = 1.0, shift: 
     out = np.empty((A.n, m), np.float64)
     ptr = cim.ctypes.data_as(C.c_void_p) if cim is not None else None
     _check(_L().orc_cheb(A.n, rp, ci, va, m, X, degree, cr, ptr, float(scale), float(shift), out), "cheb")
+    return out
+
+
+def cheb_acc32(A, X, degree: int, coeff_re, coeff_im=None, scale: float = 1.0, shift: float = 0.0) -> np.ndarray:
+    """cheb() with the matrix-vector products accumulated in binary32, recurrence in binary64."""
+    rp, ci, va = _csr(A)
+    X = _block(X, A.n)
+    m = X.shape[1]
+    cr = np.ascontiguousarray(coeff_re, np.float64)
+    assert cr.size >= degree + 1
+    cim = None
+    if coeff_im is not None:
+        cim = np.ascontiguousarray(coeff_im, np.float64)
+        assert cim.size >= degree + 1
+    out = np.empty((A.n, m), np.float64)
+    ptr = cim.ctypes.data_as(C.c_void_p) if cim is not None else None
+    _check(_L().orc_cheb_acc32(A.n, rp, ci, va, m, X, degree, cr, ptr, float(scale), float(shift), out),
+           "cheb_acc32")
     return out
 
 

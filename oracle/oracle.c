@@ -57,6 +57,44 @@ int orc_mpk(int32_t n, const int32_t *rp, const int32_t *ci, const double *va, i
 }
 
 /*
+ * Single-precision accumulation of the same powers (Sec. 3's MPK, y_k = A y_{k-1}, with a
+ * narrower arithmetic): the vectors stay binary64, each row sum runs in binary32 over the
+ * binary32 roundings of its inputs, and its result is stored widened (exactly) to binary64:
+ *     s = +0.0f;  s = fmaf(a_ij, (float) y_{k-1}[j], s)   in stored order,   y_k[i] = (double) s,
+ * (float) rounding to nearest-even and fmaf rounding once.  From power 2 on the inputs are
+ * widened binary32 values, so only X is actually rounded.  The matrix values must be exact
+ * in binary32 (va holds them as doubles; each converts exactly); ORC_EINVAL otherwise.
+ */
+int orc_mpk_acc32(int32_t n, const int32_t *rp, const int32_t *ci, const double *va, int32_t m,
+                  const double *X, int32_t p, double *Y)
+{
+    if (n < 0 || m < 1 || p < 0) return ORC_EINVAL;
+    for (int64_t e = 0; e < (n > 0 ? rp[n] : 0); ++e)
+        if ((double)(float)va[e] != va[e]) return ORC_EINVAL;
+    const int64_t nm = (int64_t)n * m;
+    float *xf = malloc(sizeof(float) * (size_t)(nm > 0 ? nm : 1));
+    float *s = malloc(sizeof(float) * (size_t)m);
+    if (!xf || !s) { free(xf); free(s); return ORC_ENOMEM; }
+    memcpy(Y, X, sizeof(double) * (size_t)nm);
+    for (int32_t k = 1; k <= p; ++k) {
+        const double *xin = Y + (int64_t)(k - 1) * nm;
+        double *yout = Y + (int64_t)k * nm;
+        for (int64_t t = 0; t < nm; ++t) xf[t] = (float)xin[t];
+        for (int64_t i = 0; i < n; ++i) {
+            for (int32_t r = 0; r < m; ++r) s[r] = 0.0f;
+            for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+                const float a = (float)va[e];
+                const float *xr = xf + (int64_t)ci[e] * m;
+                for (int32_t r = 0; r < m; ++r) s[r] = fmaf(a, xr[r], s[r]);
+            }
+            for (int32_t r = 0; r < m; ++r) yout[i * m + r] = (double)s[r];
+        }
+    }
+    free(xf); free(s);
+    return ORC_OK;
+}
+
+/*
  * Same powers accumulated in long double with separate multiply and add: an
  * independent, more precise evaluation used only to bound the rounding error of
  * orc_mpk on small cases.
@@ -331,6 +369,78 @@ int orc_cheb(int32_t n, const int32_t *rp, const int32_t *ci, const double *va, 
         double *t = vprev; vprev = vcur; vcur = vnext; vnext = t;
     }
     free(vprev); free(vcur); free(vnext); free(w);
+    return ORC_OK;
+}
+
+/*
+ * The Chebyshev expansion of orc_cheb with the matrix-vector product accumulated in binary32
+ * (as orc_mpk_acc32: w = sum fmaf(a_ij, (float) v_k[j], w) in stored order, widened exactly)
+ * while the recurrence v_{k+1} = fma(alpha, w, fma(beta, v_k, -v_{k-1})), the vectors and the
+ * accumulator stay binary64: the three-term recurrence, whose stability needs it, keeps
+ * double precision.  Same arguments and layout as orc_cheb.
+ */
+int orc_cheb_acc32(int32_t n, const int32_t *rp, const int32_t *ci, const double *va, int32_t m,
+                   const double *X, int32_t degree, const double *coeff_re, const double *coeff_im,
+                   double scale, double shift, double *out)
+{
+    if (n < 0 || m < 1 || degree < 0 || scale == 0.0) return ORC_EINVAL;
+    if (coeff_im && (m % 2)) return ORC_EINVAL;
+    for (int64_t e = 0; e < (n > 0 ? rp[n] : 0); ++e)
+        if ((double)(float)va[e] != va[e]) return ORC_EINVAL;
+    const int64_t nm = (int64_t)n * m;
+    const double alpha = 2.0 / scale, beta = -2.0 * shift / scale;
+    const double halpha = 1.0 / scale, hbeta = -shift / scale;
+    double *vprev = malloc(sizeof(double) * (size_t)(nm > 0 ? nm : 1));
+    double *vcur = malloc(sizeof(double) * (size_t)(nm > 0 ? nm : 1));
+    double *vnext = malloc(sizeof(double) * (size_t)(nm > 0 ? nm : 1));
+    float *vf = malloc(sizeof(float) * (size_t)(nm > 0 ? nm : 1));
+    float *w = malloc(sizeof(float) * (size_t)m);
+    if (!vprev || !vcur || !vnext || !vf || !w) {
+        free(vprev); free(vcur); free(vnext); free(vf); free(w);
+        return ORC_ENOMEM;
+    }
+    memcpy(vcur, X, sizeof(double) * (size_t)nm);
+    for (int64_t t = 0; t < nm; ++t) out[t] = coeff_re[0] * vcur[t];
+    if (coeff_im)
+        for (int64_t i = 0; i < n; ++i)
+            for (int32_t r = 0; r < m; r += 2) {
+                const int64_t o = i * m + r;
+                out[o] = fma(-coeff_im[0], vcur[o + 1], out[o]);
+                out[o + 1] = coeff_re[0] * vcur[o + 1];
+                out[o + 1] = fma(coeff_im[0], vcur[o], out[o + 1]);
+            }
+    for (int32_t k = 0; k < degree; ++k) {
+        for (int64_t t = 0; t < nm; ++t) vf[t] = (float)vcur[t];
+        for (int64_t i = 0; i < n; ++i) {
+            for (int32_t r = 0; r < m; ++r) w[r] = 0.0f;
+            for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+                const float a = (float)va[e];
+                const float *xr = vf + (int64_t)ci[e] * m;
+                for (int32_t r = 0; r < m; ++r) w[r] = fmaf(a, xr[r], w[r]);
+            }
+            for (int32_t r = 0; r < m; ++r) {
+                const int64_t o = i * m + r;
+                const double wd = (double)w[r];
+                vnext[o] = (k == 0) ? fma(halpha, wd, hbeta * vcur[o]) : fma(alpha, wd, fma(beta, vcur[o], -vprev[o]));
+            }
+        }
+        const double cr = coeff_re[k + 1];
+        if (!coeff_im) {
+            for (int64_t t = 0; t < nm; ++t) out[t] = fma(cr, vnext[t], out[t]);
+        } else {
+            const double cim = coeff_im[k + 1];
+            for (int64_t i = 0; i < n; ++i)
+                for (int32_t r = 0; r < m; r += 2) {
+                    const int64_t o = i * m + r;
+                    out[o] = fma(cr, vnext[o], out[o]);
+                    out[o] = fma(-cim, vnext[o + 1], out[o]);
+                    out[o + 1] = fma(cr, vnext[o + 1], out[o + 1]);
+                    out[o + 1] = fma(cim, vnext[o], out[o + 1]);
+                }
+        }
+        double *t = vprev; vprev = vcur; vcur = vnext; vnext = t;
+    }
+    free(vprev); free(vcur); free(vnext); free(vf); free(w);
     return ORC_OK;
 }
 

@@ -355,3 +355,84 @@ def test_cheb_time_step_matches_exponential():
     got = out[:, 0] + 1j * out[:, 1]
     want = np.exp(-1j * dt * lam) * v
     assert np.linalg.norm(got - want) / np.linalg.norm(want) < 1e-12
+
+
+# ----------------------------------------------------------------------------- binary32 accumulation
+def test_mpk_acc32_exact_when_every_sum_fits_binary32():
+    # small integers: every product, partial sum and power is an integer below 2^24, so the
+    # binary32 row sums are exact and equal the binary64 oracle and exact integer arithmetic
+    A = gen.random_int_matrix(40, 3, 31)
+    x = (gen.splitmix64(gen.derive_seed(131), 40 * 2) % np.uint64(5)).astype(np.float64).reshape(40, 2) - 2
+    Y32 = oracle.mpk_acc32(A, x, 5)
+    assert np.abs(Y32).max() < 2 ** 24
+    assert np.array_equal(Y32.view(np.uint64), oracle.mpk(A, x, 5).view(np.uint64))
+    for r in range(2):
+        ref = _dense_int_powers(A, x[:, r].astype(np.int64), 5)
+        for k in range(6):
+            assert np.array_equal(Y32[k, :, r], np.array(ref[k], dtype=np.float64))
+
+
+def test_mpk_acc32_rounds_input_sum_and_product_once():
+    # hand-computed binary32 cases, u = 2^-24:
+    # (a) the input is rounded: x = 1 + 2^-30 -> 1.0f, so 3 x -> 3 exactly (binary64 keeps 3 + 3*2^-30);
+    A = gen.CSR([0, 1], [0], np.array([3.0]))
+    assert oracle.mpk_acc32(A, np.array([1 + 2.0 ** -30]), 1)[1, 0, 0] == 3.0
+    assert oracle.mpk(A, np.array([1 + 2.0 ** -30]), 1)[1, 0, 0] == 3 + 3 * 2.0 ** -30
+    # (b) the sum is rounded: 1 + 2^-24 is a tie between 1 and 1 + 2^-23 -> 1.0f (even);
+    A = gen.CSR([0, 2, 3], [0, 1, 1], np.array([1.0, 1.0, 1.0]))
+    y = oracle.mpk_acc32(A, np.array([1.0, 2.0 ** -24]), 1)[1, :, 0]
+    assert y[0] == 1.0 and y[1] == 2.0 ** -24
+    # (c) product and sum are rounded once (fmaf): stored order (-1, then a), a = x0 = 1 + 2^-12:
+    #     fmaf(a, x0, -1) = 2^-11 + 2^-24 exactly, while a rounded product gives 2^-11
+    a = 1 + 2.0 ** -12
+    A = gen.CSR([0, 2, 3], [1, 0, 1], np.array([-1.0, a, 1.0]))
+    y = oracle.mpk_acc32(A, np.array([a, 1.0]), 1)[1, :, 0]
+    assert y[0] == 2.0 ** -11 + 2.0 ** -24
+    # values that binary32 cannot hold are refused
+    with pytest.raises(RuntimeError):
+        oracle.mpk_acc32(gen.CSR([0, 1], [0], np.array([0.1])), np.array([1.0]), 1)
+
+
+def test_mpk_acc32_elementwise_error_bound():
+    # each power is the binary32 evaluation of A times the binary32 rounding of the previous
+    # power: |y_k - A fl32(y_{k-1})| <= gamma_w (|A| |fl32(y_{k-1})|) row by row, gamma_w = w u / (1 - w u)
+    # with w the row's entry count and u = 2^-24 (the standard bound for a recursive fma sum)
+    A = gen.banded_random(500, stream=132)
+    vals = A.val.astype(np.float32).astype(np.float64)
+    A = gen.CSR(A.row_ptr, A.col, vals)
+    X = gen.vector(A.n, 1, stream=133)
+    Y = oracle.mpk_acc32(A, X, 6)
+    D = A.to_dense().astype(np.longdouble)
+    w = np.diff(A.row_ptr).astype(np.longdouble)
+    u = np.longdouble(2.0) ** -24
+    gamma = w * u / (1 - w * u)
+    err_total = 0.0
+    for k in range(1, 7):
+        xin = Y[k - 1, :, 0].astype(np.float32).astype(np.longdouble)
+        exact = D @ xin
+        bound = gamma * (np.abs(D) @ np.abs(xin))
+        diff = np.abs(Y[k, :, 0].astype(np.longdouble) - exact)
+        assert np.all(diff <= bound), k
+        err_total += float(np.sum(diff))
+    assert err_total > 0  # the binary32 path really rounds
+
+
+def test_cheb_acc32_integer_case_equals_binary64():
+    # scale 1, shift 0 and small integers: A' = A, every w and every recurrence value is an
+    # integer below 2^24, so the binary32 products are exact and the two oracles agree
+    A = gen.random_int_matrix(25, 2, 34)
+    x = (gen.splitmix64(gen.derive_seed(134), 25 * 2) % np.uint64(3)).astype(np.float64).reshape(25, 2) - 1
+    c = np.array([1.0, -2.0, 0.5, 3.0, 1.0, -1.0])
+    want = oracle.cheb(A, x, 5, c, scale=1.0, shift=0.0)
+    got = oracle.cheb_acc32(A, x, 5, c, scale=1.0, shift=0.0)
+    assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+
+
+def test_cheb_acc32_keeps_the_recurrence_in_binary64():
+    # 1 x 1 matrix [2], x = 1 + 2^-30, scale 1, shift 0: w = 2 * fl32(x) = 2, then
+    # v_1 = fma(1, 2, 0 * x) = 2, v_2 = fma(2, 2 * fl32(v_1) = 4, fma(0, v_1, -x)) = 8 - x,
+    # which keeps x's low bits (a binary32 recurrence would lose them)
+    A = gen.CSR([0, 1], [0], np.array([2.0]))
+    x = 1 + 2.0 ** -30
+    got = oracle.cheb_acc32(A, np.array([x]), 2, np.array([0.0, 0.0, 1.0]), scale=1.0, shift=0.0)
+    assert got[0, 0] == 8 - x
