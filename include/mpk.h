@@ -138,9 +138,10 @@ typedef struct {
                                mpk_cheb_filter rejects such a plan                           */
     int32_t engine;         /* MPK_ENGINE_STAGED (0, default) or MPK_ENGINE_WARP (1), below  */
     int32_t shape;          /* block shape of the staged engine: 0 = chosen from the mean
-                               row width; 1 = 13 compute warps, 3072-entry slots, 3 blocks
-                               per SM (rows up to ~7 entries); 2 = 15 warps, 4096 entries,
-                               2 blocks; 3 = 15 warps, entries read from global memory;
+                               row width (2, else 3 for rows too wide to stage); 1 = 13
+                               compute warps, 3072-entry slots, 3 blocks per SM; 2 = 16
+                               warps, 4608 entries, 2 blocks; 3 = 15 warps, entries read from
+                               global memory;
                                4 = 10 compute warps, 2304-entry slots that also hold the
                                input rows the chunk reads (at most 4 row windows, 1664
                                doubles), 3 blocks per SM: the compute warps read only shared
@@ -149,6 +150,17 @@ typedef struct {
     int64_t shuffle_seed;   /* race-detection aid: non-zero permutes the staged engine's work
                                units inside every line of the schedule (a valid order whose
                                results must be the same bits); 0 = the natural order         */
+    int32_t accum;          /* arithmetic of the row sums: MPK_F64 (0, default) or MPK_F32.
+                               MPK_F32 needs values stored as MPK_F32 or MPK_BF16 and the staged
+                               (shapes 0-2) or sweep engine, without trace, level caps or
+                               batching (else MPK_ERR_UNSUPPORTED).  Each row sum then runs in
+                               binary32, one fmaf per entry in stored order, over the binary32
+                               rounding (nearest even) of its inputs, and is stored widened
+                               exactly into the binary64 results; X, Y, the Chebyshev vectors,
+                               its three-term recurrence and its accumulator stay binary64.  The
+                               plan keeps a ring of two binary32 copies of the current input
+                               (8 * n * nrhs bytes).  mpk_spmv_powers refuses such a plan (its
+                               comparator is a plan of engine MPK_ENGINE_SWEEP)               */
 } mpk_plan_opts;
 
 /* Engines of the level-blocked kernel (same results bit for bit, same Lp-diagram order):
@@ -191,6 +203,7 @@ typedef struct {
     int32_t shape;                /* block shape of the staged engine (0..3, opts.shape - 1) */
     int32_t engine;               /* MPK_ENGINE_STAGED or MPK_ENGINE_WARP                 */
     int32_t chunk_rows;           /* rows per chunk limit in effect                      */
+    int32_t accum;                /* MPK_F64 or MPK_F32 (opts.accum)                     */
 } mpk_plan_desc;
 
 mpk_status mpk_plan_describe(const mpk_plan_t *P, mpk_plan_desc *out);

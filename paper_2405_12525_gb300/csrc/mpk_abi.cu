@@ -110,6 +110,7 @@ extern "C" mpk_status mpk_plan_describe(const mpk_plan_t *P, mpk_plan_desc *d) {
     d->shape = p.shape;
     d->engine = p.engine;
     d->chunk_rows = p.chunk_rows;
+    d->accum = p.accum;
     return MPK_OK;
 }
 
@@ -170,6 +171,7 @@ KArgs mpk::base_args(Plan &P, int32_t p) {
     a.trace = P.trace;
     P.drop_unit = -1;
     a.ystride = (int64_t)P.n * P.m;
+    a.shadow = P.shadow;
     a.p_launch = p;
     if (P.engine == MPK_ENGINE_WARP) {
         a.w_item = P.w_item + P.w_cell_off[p];
@@ -215,6 +217,7 @@ extern "C" mpk_status mpk_apply(const mpk_plan_t *Ph, const double *X, int32_t p
         a.y0copy = (Y != X) ? Y : nullptr;
         if (a.y0copy && P.level0_rows > 0)  // level 0 of a level-capped plan has no units
             MPK_CUDA(cudaMemcpyAsync(Y, X, sizeof(double) * (size_t)P.level0_rows * P.m, cudaMemcpyDeviceToDevice, s));
+        if (P.accum == MPK_F32) launch_round_f32(X, nm, P.shadow, s);  // binary32 input of power 1
         launch_mpk(P, a, 0, s);
     } else {
         // gather X into plan order, compute every power in plan order in the workspace,
@@ -223,6 +226,7 @@ extern "C" mpk_status mpk_apply(const mpk_plan_t *Ph, const double *X, int32_t p
         if (Y != X) MPK_CUDA(cudaMemcpyAsync(Y, X, sizeof(double) * nm, cudaMemcpyDeviceToDevice, s));
         a.x0 = P.work;
         a.ybase = P.work;
+        if (P.accum == MPK_F32) launch_round_f32(P.work, nm, P.shadow, s);
         launch_mpk(P, a, 0, s);
         launch_scatter_powers(P.work, P.iperm, Y, P.n, P.m, p, s);
     }
@@ -235,6 +239,9 @@ extern "C" mpk_status mpk_spmv_powers(const mpk_plan_t *Ph, const double *X, int
     MPK_GUARD_BEGIN
     check_apply_args(Ph, X, p, Y);
     Plan &P = *const_cast<Plan *>(Ph->impl);
+    if (P.accum != MPK_F64)
+        fail(MPK_ERR_UNSUPPORTED, "the row-range SpMV accumulates in binary64: compare binary32 accumulation with a "
+                                  "plan of engine MPK_ENGINE_SWEEP");
     cudaStream_t s = as_stream(stream);
     const int64_t nm = (int64_t)P.n * P.m;
     if (P.n == 0) return MPK_OK;
@@ -269,6 +276,12 @@ static void cheb_steps(Plan &P, double *ring, double *acc, int32_t k_begin, int3
     // same expressions as the recurrence's definition: 2A'v = alpha Av + beta v
     const double alpha = 2.0 / scale, beta = -2.0 * shift / scale;
     const double halpha = 1.0 / scale, hbeta = -shift / scale;
+    // binary32 accumulation: the input of step k_begin + 1 is the binary32 rounding of the
+    // state's v_{k_begin}; every launch then leaves the rounding of its last step behind
+    if (P.accum == MPK_F32 && k_end > k_begin) {
+        const int64_t nm = (int64_t)P.n * P.m;
+        launch_round_f32(ring + (int64_t)(k_begin % 3) * nm, nm, P.shadow + (int64_t)(k_begin & 1) * nm, s);
+    }
     for (int32_t j0 = k_begin; j0 < k_end; j0 += P.p_max) {
         const int32_t pb = std::min(P.p_max, k_end - j0);
         next_epoch(P, s);

@@ -156,8 +156,9 @@ constexpr int kMaxP = 31;
 // after the dependency poll the control warp copies the (at most four) row windows of the
 // input vector that the chunk reads into the slot, and the chunk's column indices are
 // staged as 16-bit positions in that window area, so that the compute warps read nothing
-// but shared memory.  The planner picks shape 3 when every chunk's windows fit a slot, else
-// a shape from the mean slice width, unless the plan options name one.
+// but shared memory.  Every block also has a publisher warp (see publisher_loop).  The
+// planner picks shape 1 when its slot holds at least 6 slices of the mean width, else
+// shape 2, unless the plan options name a shape (0 or 3 included).
 struct BlockShape {
     int comp_warps, stage_entries, blocks, slots, x_words, ctrl_warps;
 };
@@ -180,14 +181,13 @@ struct BlockShape {
 #define MPK_XS_CTL 1
 #endif
 constexpr BlockShape kShapes[4] = {{13, 3072, 3, 2, 0, 1},
-                                   {15, 4096, 2, 2, 0, 1},
+                                   {16, 4608, 2, 2, 0, 1},
                                    {15, 0, 2, 2, 0, 1},
                                    {MPK_XS_WARPS, MPK_XS_ENTRIES, MPK_XS_BLOCKS, MPK_XS_SLOTS, MPK_XS_WORDS, MPK_XS_CTL}};
 constexpr int kNumShapes = 4;
 constexpr int kShapeX = 3;  // the shape that stages input rows
 // input-row windows of a chunk (shape 3): one per dependency range
 constexpr int kXWin = 4;
-constexpr int kMaxStageEntries = 4096;
 // 1: chunks whose entries fit a buffer are copied to shared memory by the bulk-copy engine;
 // 0: every unit reads its entries from global memory (L2) directly
 #ifndef MPK_STAGE
@@ -242,6 +242,8 @@ struct KArgs {
     int64_t ystride;
     int32_t ring;
     double *y0copy;    // if set, units of power 1 copy their rows of x0 here
+    float *shadow;     // binary32 accumulation: ring of 2 blocks (ystride floats apart); slot j & 1
+                       // holds the binary32 rounding of step j, the input of step j + 1
     int32_t k_offset;  // absolute index of local power 0 (Chebyshev blocks)
     // Chebyshev recurrence
     double alpha, beta, halpha, hbeta;
@@ -272,6 +274,8 @@ constexpr int kWarpQueues = 16;
 struct Plan {
     int32_t n = 0, nnz = 0, m = 1, p_max = 8, order = MPK_ORDER_ORIGINAL;
     int32_t val_type = MPK_F64, val_bytes = 8;  // storage of the matrix values (mpk_dtype)
+    int32_t accum = MPK_F64;                     // row-sum arithmetic: MPK_F64 or MPK_F32
+    float *shadow = nullptr;                     // binary32 accumulation: 2 x n x m binary32 input ring
     int32_t num_levels = 0, num_groups = 0, num_chunks = 0, num_slices = 0;
     int32_t chunk_rows = 512;
     int32_t shape = 0;  // block shape of the level-blocked kernel (kShapes)
@@ -358,7 +362,9 @@ void launch_scatter_rows(const double *src, const int32_t *iperm, double *dst, i
                          cudaStream_t s);
 void launch_cheb_init(const double *v0, double *acc, int32_t n, int32_t m, double c0re, double c0im,
                       int complex_coeff, cudaStream_t s);
-int occupancy_grid(int mode, int m, bool trace, int vtype, int shape);
+int occupancy_grid(int mode, int m, bool trace, int vtype, int shape, bool a32 = false);
+// dst[i] = src[i] rounded to binary32, nearest even (binary32 accumulation: its first input)
+void launch_round_f32(const double *src, int64_t n, float *dst, cudaStream_t s);
 // dst[i] = src[i] widened to float64 (src of mpk_dtype vtype), exact
 void widen_values(int vtype, const void *src, int64_t n, double *dst, cudaStream_t s);
 

@@ -13,6 +13,8 @@
 // bit for bit.
 #include "mpk_kernel_dev.cuh"
 
+#include <type_traits>
+
 namespace mpk {
 
 // ----------------------------------------------------------------------------- K-MPK, warp engine
@@ -115,12 +117,8 @@ __global__ void __launch_bounds__(kWarpBS, (WarpOcc<M, MODE, VT>::blocks)) k_mpk
             if (r < gr1) {
                 const int64_t e0 = __ldg(a.slice_ptr + sl), e1 = __ldg(a.slice_ptr + sl + 1);
                 double w[M];
-                row_sum<M, B>(GVal<VT>{val}, GCol{a.col}, e0 + lane, (int)((e1 - e0) >> 5), xin, w);
-                row_epilogue<M, MODE>(a, k, r, w, xin);
-                if (k == 1 && a.y0copy) {
-#pragma unroll
-                    for (int i = 0; i < M; ++i) a.y0copy[r * M + i] = a.x0[r * M + i];
-                }
+                row_sum<M, B, double>(GVal<VT>{val}, GCol{a.col}, e0 + lane, (int)((e1 - e0) >> 5), xin, w);
+                row_epilogue<M, MODE, double>(a, k, r, w, xin);
             }
         }
         __syncwarp();
@@ -150,11 +148,13 @@ __global__ void __launch_bounds__(kWarpBS, (WarpOcc<M, MODE, VT>::blocks)) k_mpk
 // slices, with the level-blocked kernel's row body and epilogue (plain powers or the
 // Chebyshev recurrence), so the results are the same bits.  One launch per power; stream
 // order supplies every dependency.
-template <int M, int MODE, class VT>
+template <int M, int MODE, class VT, bool A32 = false>
 __global__ void __launch_bounds__(kSpmvBS) k_sweep(const KArgs a, int k) {
+    using AT = typename std::conditional<A32, float, double>::type;
     const int lane = threadIdx.x & 31;
     const auto *val = static_cast<const typename VT::T *>(a.val);
     const double *xin = input_block<M>(a, k);
+    const AT *xacc = InputAcc<M, AT>::get(a, k);
     for (int c = blockIdx.x; c < a.nchunks; c += gridDim.x) {
         const int r0 = a.chunk_row[c], r1 = a.chunk_row[c + 1], sl0 = a.chunk_slice[c];
         const int nsl = (r1 - r0 + 31) >> 5;
@@ -162,30 +162,36 @@ __global__ void __launch_bounds__(kSpmvBS) k_sweep(const KArgs a, int k) {
             const int64_t r = (int64_t)r0 + 32 * sl + lane;
             if (r < r1) {
                 const int64_t e0 = a.slice_ptr[sl0 + sl], e1 = a.slice_ptr[sl0 + sl + 1];
-                double w[M];
-                row_sum<M, Batch<M>::B>(GVal<VT>{val}, GCol{a.col}, e0 + lane, (int)((e1 - e0) >> 5), xin, w);
-                row_epilogue<M, MODE>(a, k, r, w, xin);
-                if (k == 1 && a.y0copy) {
-#pragma unroll
-                    for (int i = 0; i < M; ++i) a.y0copy[r * M + i] = a.x0[r * M + i];
-                }
+                AT w[M];
+                row_sum<M, Batch<M>::B, AT>(GVal<VT, AT>{val}, GCol{a.col}, e0 + lane, (int)((e1 - e0) >> 5), xacc,
+                                            w);
+                row_epilogue<M, MODE, AT>(a, k, r, w, xin);
             }
         }
     }
 }
 
-template <class VT> static void *select_sweep_vt(int mode, int m) {
-#define SEL(MM)                                                                                \
-    if (m == MM) return mode == MODE_POWERS ? (void *)k_sweep<MM, MODE_POWERS, VT> : (void *)k_sweep<MM, MODE_CHEB, VT>;
+template <class VT> static void *select_sweep_vt(int mode, int m, bool a32) {
+#define SEL(MM)                                                                                              \
+    if (m == MM) {                                                                                           \
+        if (a32) {                                                                                           \
+            if constexpr (std::is_same<VT, ValF64>::value)                                                   \
+                fail(MPK_ERR_UNSUPPORTED, "binary32 accumulation needs float32 or bfloat16 values");          \
+            else                                                                                             \
+                return mode == MODE_POWERS ? (void *)k_sweep<MM, MODE_POWERS, VT, true>                      \
+                                           : (void *)k_sweep<MM, MODE_CHEB, VT, true>;                       \
+        }                                                                                                    \
+        return mode == MODE_POWERS ? (void *)k_sweep<MM, MODE_POWERS, VT> : (void *)k_sweep<MM, MODE_CHEB, VT>; \
+    }
     SEL(1) SEL(2) SEL(4) SEL(8)
 #undef SEL
     fail(MPK_ERR_UNSUPPORTED, "nrhs %d", m);
 }
 
-static void *select_sweep(int mode, int m, int vtype) {
-    if (vtype == MPK_F64) return select_sweep_vt<ValF64>(mode, m);
-    if (vtype == MPK_F32) return select_sweep_vt<ValF32>(mode, m);
-    if (vtype == MPK_BF16) return select_sweep_vt<ValBF16>(mode, m);
+static void *select_sweep(int mode, int m, int vtype, bool a32) {
+    if (vtype == MPK_F64) return select_sweep_vt<ValF64>(mode, m, a32);
+    if (vtype == MPK_F32) return select_sweep_vt<ValF32>(mode, m, a32);
+    if (vtype == MPK_BF16) return select_sweep_vt<ValBF16>(mode, m, a32);
     fail(MPK_ERR_UNSUPPORTED, "value type %d", vtype);
 }
 
@@ -212,7 +218,7 @@ __global__ void __launch_bounds__(kSpmvBS) k_spmv_rows(const RowSegs segs) {
             if (r < r1 && r >= g.lo && r < g.hi) {
                 const int64_t s0 = g.slice_ptr[sl0 + sl], s1 = g.slice_ptr[sl0 + sl + 1];
                 double w[M];
-                row_sum<M, Batch<M>::B>(GVal<VT>{val}, GCol{g.col}, s0 + lane, (int)((s1 - s0) >> 5), g.x, w);
+                row_sum<M, Batch<M>::B, double>(GVal<VT>{val}, GCol{g.col}, s0 + lane, (int)((s1 - s0) >> 5), g.x, w);
 #pragma unroll
                 for (int i = 0; i < M; ++i) g.y[r * M + i] = w[i];
             }
@@ -304,6 +310,13 @@ __global__ void k_gather_rows(const double *src, const int32_t *perm, int32_t ba
     }
 }
 
+// dst[i] = src[i] rounded to the nearest binary32 (ties to even): the binary32 input of the
+// first step of binary32 accumulation
+__global__ void k_round_f32(const double *src, int64_t n, float *dst) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += stride) dst[i] = __double2float_rn(src[i]);
+}
+
 // Chebyshev k = 0 term: acc = c0 * v0 (complex: pairs of columns)
 __global__ void k_cheb_init(const double *v0, double *acc, int32_t n, int32_t m, double cr, double ci, int cplx) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -384,6 +397,12 @@ void launch_scatter_powers(const double *W, const int32_t *iperm, double *Y, int
     MPK_LAUNCHED();
 }
 
+void launch_round_f32(const double *src, int64_t n, float *dst, cudaStream_t s) {
+    if (n <= 0) return;
+    k_round_f32<<<grid_rows(n), 256, 0, s>>>(src, n, dst);
+    MPK_LAUNCHED();
+}
+
 void launch_cheb_init(const double *v0, double *acc, int32_t n, int32_t m, double c0re, double c0im, int cplx,
                       cudaStream_t s) {
     if (n <= 0) return;
@@ -392,11 +411,11 @@ void launch_cheb_init(const double *v0, double *acc, int32_t n, int32_t m, doubl
 }
 
 // ----------------------------------------------------------------------------- launches
-static void *select_mpk(int mode, int m, bool trace, int vtype, int shape) {
-    if (shape == 0) return select_mpk_shape0(mode, m, trace, vtype);
-    if (shape == 1) return select_mpk_shape1(mode, m, trace, vtype);
-    if (shape == 2) return select_mpk_shape2(mode, m, trace, vtype);
-    return select_mpk_shape3(mode, m, trace, vtype);
+static void *select_mpk(int mode, int m, bool trace, int vtype, int shape, bool a32) {
+    if (shape == 0) return select_mpk_shape0(mode, m, trace, vtype, a32);
+    if (shape == 1) return select_mpk_shape1(mode, m, trace, vtype, a32);
+    if (shape == 2) return select_mpk_shape2(mode, m, trace, vtype, a32);
+    return select_mpk_shape3(mode, m, trace, vtype, a32);
 }
 
 static int mpk_smem_bytes(int vtype, int shape) {
@@ -417,13 +436,13 @@ static int mpk_block_size(int shape) {
     }
 }
 
-int occupancy_grid(int mode, int m, bool trace, int vtype, int shape) {
-    static int cache[3][2][2][9][kNumShapes] = {};
+int occupancy_grid(int mode, int m, bool trace, int vtype, int shape, bool a32) {
+    static int cache[3][2][2][9][kNumShapes][2] = {};
     if (vtype < 0 || vtype > 2) fail(MPK_ERR_UNSUPPORTED, "value type %d", vtype);
     if (shape < 0 || shape >= kNumShapes) fail(MPK_ERR_UNSUPPORTED, "block shape %d", shape);
-    int &c = cache[vtype][mode][trace ? 1 : 0][m][shape];
+    int &c = cache[vtype][mode][trace ? 1 : 0][m][shape][a32 ? 1 : 0];
     if (c) return c;
-    void *fn = select_mpk(mode, m, trace, vtype, shape);
+    void *fn = select_mpk(mode, m, trace, vtype, shape, a32);
     const int smem = mpk_smem_bytes(vtype, shape);
     MPK_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int per_sm = 0;
@@ -461,9 +480,10 @@ static int occupancy_grid_w(int mode, int m, int vtype) {
 }
 
 void launch_mpk(const Plan &P, KArgs &a, int mode, cudaStream_t s) {
+    const bool a32 = P.accum == MPK_F32;
     if (P.engine == MPK_ENGINE_SWEEP && a.trace == nullptr && a.drop_unit < 0 && a.w_item == nullptr) {
         if (P.num_chunks <= 0) return;
-        void *fn = select_sweep(mode, P.m, P.val_type);
+        void *fn = select_sweep(mode, P.m, P.val_type, a32);
         const int grid = std::min(P.num_chunks, 64 * device_sms());
         for (int k = 1; k <= a.p_launch; ++k) {
             void *args[] = {&a, &k};
@@ -485,9 +505,9 @@ void launch_mpk(const Plan &P, KArgs &a, int mode, cudaStream_t s) {
     }
     if (a.nunits <= 0) return;
     const bool trace = a.trace != nullptr;
-    int grid = occupancy_grid(mode, P.m, trace, P.val_type, P.shape);
+    int grid = occupancy_grid(mode, P.m, trace, P.val_type, P.shape, a32);
     if ((int64_t)grid > a.nunits) grid = (int)a.nunits;
-    void *fn = select_mpk(mode, P.m, trace, P.val_type, P.shape);
+    void *fn = select_mpk(mode, P.m, trace, P.val_type, P.shape, a32);
     void *args[] = {&a};
     MPK_CUDA(cudaLaunchKernel(fn, dim3(grid), dim3(mpk_block_size(P.shape)), args, mpk_smem_bytes(P.val_type, P.shape),
                               s));

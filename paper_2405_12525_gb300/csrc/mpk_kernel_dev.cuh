@@ -7,6 +7,7 @@
 #include "mpk_internal.h"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace mpk {
 
@@ -14,7 +15,7 @@ namespace mpk {
 template <int SH> struct Shape {
     static constexpr int CW = kShapes[SH].comp_warps;
     static constexpr int SE = kShapes[SH].stage_entries;
-    static constexpr int BS = 32 * (kShapes[SH].ctrl_warps + CW);
+    static constexpr int BS = 32 * (kShapes[SH].ctrl_warps + 1 + CW);  // control, publisher, compute
     static constexpr int SL = kShapes[SH].slots;    // staging slots
     static constexpr int CTL = kShapes[SH].ctrl_warps;  // control warps: 1, or 2 (poll + stage)
     static constexpr int XW = kShapes[SH].x_words;  // input-row words per slot (0: not staged)
@@ -122,15 +123,20 @@ template <int M> struct Batch {
     static constexpr int B = M == 1 ? 8 : (M == 2 ? 4 : (M == 4 ? 2 : 1));
 };
 
-// acc[i] = sum_j val[j] * x[col[j]*M + i] over a row's entries, in stored order.  Entry j
-// of the row is at val[off + 32 j] / col[off + 32 j] (global or shared memory), j < width
+// Fused multiply-add of the accumulator type: binary64, or binary32 (one rounding each).
+__device__ __forceinline__ double afma(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float afma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// acc[i] = sum_j val[j] * x[col[j]*M + i] over a row's entries, in stored order, in the
+// accumulator type AT (binary64, or binary32 with x the binary32 shadow of the input).  Entry
+// j of the row is at val[off + 32 j] / col[off + 32 j] (global or shared memory), j < width
 // of the row's slice; entries past the row's end are padding with col < 0 and are skipped.
-template <int M, int B, class VP, class CP>
-__device__ __forceinline__ void row_sum(VP val, CP col, int64_t off, int width, const double *x, double (&acc)[M]) {
+template <int M, int B, class AT, class VP, class CP>
+__device__ __forceinline__ void row_sum(VP val, CP col, int64_t off, int width, const AT *x, AT (&acc)[M]) {
 #pragma unroll
-    for (int i = 0; i < M; ++i) acc[i] = 0.0;
+    for (int i = 0; i < M; ++i) acc[i] = AT(0);
     for (int j0 = 0; j0 < width; j0 += B) {
-        double v[B];
+        AT v[B];
         int32_t c[B];
 #pragma unroll
         for (int b = 0; b < B; ++b) {
@@ -138,30 +144,30 @@ __device__ __forceinline__ void row_sum(VP val, CP col, int64_t off, int width, 
                 v[b] = val[off + 32 * (int64_t)(j0 + b)];
                 c[b] = col[off + 32 * (int64_t)(j0 + b)];
             } else {
-                v[b] = 0.0;
+                v[b] = AT(0);
                 c[b] = -1;
             }
         }
-        double xv[B][M];
+        AT xv[B][M];
 #pragma unroll
         for (int b = 0; b < B; ++b)
 #pragma unroll
-            for (int i = 0; i < M; ++i) xv[b][i] = (c[b] >= 0) ? x[(int64_t)c[b] * M + i] : 0.0;
+            for (int i = 0; i < M; ++i) xv[b][i] = (c[b] >= 0) ? x[(int64_t)c[b] * M + i] : AT(0);
 #pragma unroll
         for (int b = 0; b < B; ++b)
             if (c[b] >= 0) {
 #pragma unroll
-                for (int i = 0; i < M; ++i) acc[i] = fma(v[b], xv[b][i], acc[i]);
+                for (int i = 0; i < M; ++i) acc[i] = afma(v[b], xv[b][i], acc[i]);
             }
     }
 }
 
 // Continues a row sum from entry j0 (acc already holds entries 0..j0-1).
-template <int M, int B, class VP, class CP>
-__device__ __forceinline__ void row_sum_from(VP val, CP col, int64_t off, int j_start, int width, const double *x,
-                                             double (&acc)[M]) {
+template <int M, int B, class AT, class VP, class CP>
+__device__ __forceinline__ void row_sum_from(VP val, CP col, int64_t off, int j_start, int width, const AT *x,
+                                             AT (&acc)[M]) {
     for (int j0 = j_start; j0 < width; j0 += B) {
-        double v[B];
+        AT v[B];
         int32_t c[B];
 #pragma unroll
         for (int b = 0; b < B; ++b) {
@@ -169,20 +175,20 @@ __device__ __forceinline__ void row_sum_from(VP val, CP col, int64_t off, int j_
                 v[b] = val[off + 32 * (int64_t)(j0 + b)];
                 c[b] = col[off + 32 * (int64_t)(j0 + b)];
             } else {
-                v[b] = 0.0;
+                v[b] = AT(0);
                 c[b] = -1;
             }
         }
-        double xv[B][M];
+        AT xv[B][M];
 #pragma unroll
         for (int b = 0; b < B; ++b)
 #pragma unroll
-            for (int i = 0; i < M; ++i) xv[b][i] = (c[b] >= 0) ? x[(int64_t)c[b] * M + i] : 0.0;
+            for (int i = 0; i < M; ++i) xv[b][i] = (c[b] >= 0) ? x[(int64_t)c[b] * M + i] : AT(0);
 #pragma unroll
         for (int b = 0; b < B; ++b)
             if (c[b] >= 0) {
 #pragma unroll
-                for (int i = 0; i < M; ++i) acc[i] = fma(v[b], xv[b][i], acc[i]);
+                for (int i = 0; i < M; ++i) acc[i] = afma(v[b], xv[b][i], acc[i]);
             }
     }
 }
@@ -194,29 +200,64 @@ __device__ __forceinline__ void row_sum_from(VP val, CP col, int64_t off, int j_
 struct ValF64 {
     using T = double;
     static __device__ __forceinline__ double widen(double v) { return v; }
+    static __device__ __forceinline__ float widen32(double v) { return (float)v; }  // never instantiated
 };
 struct ValF32 {
     using T = float;
     static __device__ __forceinline__ double widen(float v) { return widen_normal32(__float_as_uint(v)); }
+    static __device__ __forceinline__ float widen32(float v) { return v; }
 };
 struct ValBF16 {
     using T = uint16_t;  // bfloat16 bits
     static __device__ __forceinline__ double widen(uint16_t v) { return widen_normal32((uint32_t)v << 16); }
+    // a bfloat16 is the upper half of a binary32
+    static __device__ __forceinline__ float widen32(uint16_t v) { return __uint_as_float((uint32_t)v << 16); }
+};
+// the stored value in the accumulator type (exact: both types hold every stored value)
+template <class VT, class AT> struct ToAcc;
+template <class VT> struct ToAcc<VT, double> {
+    static __device__ __forceinline__ double get(typename VT::T v) { return VT::widen(v); }
+};
+template <class VT> struct ToAcc<VT, float> {
+    static __device__ __forceinline__ float get(typename VT::T v) { return VT::widen32(v); }
 };
 
-// read-only views returning widened values: the immutable matrix copy in global memory, or a
-// staged slot in shared memory
-template <class VT> struct GVal {
+// read-only views returning values in the accumulator type: the immutable matrix copy in
+// global memory, or a staged slot in shared memory
+template <class VT, class AT = double> struct GVal {
     const typename VT::T *p;
-    __device__ __forceinline__ double operator[](int64_t i) const { return VT::widen(__ldg(p + i)); }
+    __device__ __forceinline__ AT operator[](int64_t i) const { return ToAcc<VT, AT>::get(__ldg(p + i)); }
 };
-template <class VT> struct SVal {
+template <class VT, class AT = double> struct SVal {
     const typename VT::T *p;
-    __device__ __forceinline__ double operator[](int64_t i) const { return VT::widen(p[i]); }
+    __device__ __forceinline__ AT operator[](int64_t i) const { return ToAcc<VT, AT>::get(p[i]); }
 };
 struct GCol {
     const int32_t *p;
     __device__ __forceinline__ int32_t operator[](int64_t i) const { return __ldg(p + i); }
+};
+
+__device__ __forceinline__ int hi_bits(double v) { return __double2hiint(v); }
+__device__ __forceinline__ int hi_bits(float v) { return __float_as_int(v); }
+
+// A row sum in binary64: binary64 sums as they are, binary32 sums widened exactly (integer
+// operations on the encoding, every binary32 value including subnormals, infinities, NaNs).
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(float v) { return widen_binary32(__float_as_uint(v)); }
+
+// The input block the row sums of local power k read: binary64 powers, or, with binary32
+// accumulation, the binary32 shadow ring (slot j & 1 holds the binary32 rounding of step j).
+template <int M>
+__device__ __forceinline__ const double *input_block(const KArgs &a, int k) {
+    return (k == 1 && a.k_offset == 0) ? a.x0 : a.ybase + (int64_t)((a.k_offset + k - 1) % a.ring) * a.ystride;
+}
+template <int M, class AT> struct InputAcc {
+    static __device__ __forceinline__ const double *get(const KArgs &a, int k) { return input_block<M>(a, k); }
+};
+template <int M> struct InputAcc<M, float> {
+    static __device__ __forceinline__ const float *get(const KArgs &a, int k) {
+        return a.shadow + (int64_t)((a.k_offset + k - 1) & 1) * a.ystride;
+    }
 };
 
 // Rows of global memory a row's epilogue reads, loaded before its FMAs so that their latency
@@ -244,12 +285,19 @@ __device__ __forceinline__ void epilogue_load(const KArgs &a, int k, int64_t r, 
     }
 }
 // Epilogue of one row at local power k with its rows loaded: store into the plan-order slot
-// (and Y[0] for power 1), or advance the Chebyshev recurrence.
-template <int M, int MODE>
-__device__ __forceinline__ void row_epilogue_loaded(const KArgs &a, int k, int64_t r, const double (&w)[M],
+// (and Y[0] for power 1), or advance the Chebyshev recurrence (binary64 in both accumulator
+// types).  With binary32 accumulation the step's binary32 shadow is stored too: the row sum
+// itself for powers, the binary32 rounding of the new recurrence value for Chebyshev.
+template <int M, int MODE, class AT>
+__device__ __forceinline__ void row_epilogue_loaded(const KArgs &a, int k, int64_t r, const AT (&wa)[M],
                                                     const EpiRows<M> &e) {
+    constexpr bool A32 = sizeof(AT) == 4;
     const int j = a.k_offset + k;  // absolute power / recurrence step
+    double w[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) w[i] = to_f64(wa[i]);
     double *y = a.ybase + (int64_t)(j % a.ring) * a.ystride + r * M;
+    float *sh = A32 ? a.shadow + (int64_t)(j & 1) * a.ystride + r * M : nullptr;
     if constexpr (MODE == MODE_CHEB) {
         double vn[M];
         if (j == 1) {
@@ -261,6 +309,10 @@ __device__ __forceinline__ void row_epilogue_loaded(const KArgs &a, int k, int64
         }
 #pragma unroll
         for (int i = 0; i < M; ++i) y[i] = vn[i];
+        if constexpr (A32) {
+#pragma unroll
+            for (int i = 0; i < M; ++i) sh[i] = __double2float_rn(vn[i]);
+        }
         double *acc = a.acc + r * M;
         const double cr = a.cre[k];
         if (!a.complex_coeff) {
@@ -282,6 +334,10 @@ __device__ __forceinline__ void row_epilogue_loaded(const KArgs &a, int k, int64
     } else {
 #pragma unroll
         for (int i = 0; i < M; ++i) y[i] = w[i];
+        if constexpr (A32) {
+#pragma unroll
+            for (int i = 0; i < M; ++i) sh[i] = (float)wa[i];
+        }
         if (k == 1 && a.y0copy) {
 #pragma unroll
             for (int i = 0; i < M; ++i) a.y0copy[r * M + i] = e.own[i];
@@ -289,47 +345,13 @@ __device__ __forceinline__ void row_epilogue_loaded(const KArgs &a, int k, int64
     }
 }
 
-// Epilogue of one row at local power k: store into the plan-order slot, or advance the
-// Chebyshev recurrence.
-template <int M, int MODE>
-__device__ __forceinline__ void row_epilogue(const KArgs &a, int k, int64_t r, const double (&w)[M],
-                                             const double *xin) {
-    const int j = a.k_offset + k;  // absolute power / recurrence step
-    double *y = a.ybase + (int64_t)(j % a.ring) * a.ystride + r * M;
-    if constexpr (MODE == MODE_CHEB) {
-        double vn[M];
-        if (j == 1) {
-#pragma unroll
-            for (int i = 0; i < M; ++i) vn[i] = fma(a.halpha, w[i], a.hbeta * xin[r * M + i]);
-        } else {
-            const double *vp2 = a.ybase + (int64_t)((j - 2) % a.ring) * a.ystride + r * M;
-#pragma unroll
-            for (int i = 0; i < M; ++i) vn[i] = fma(a.alpha, w[i], fma(a.beta, xin[r * M + i], -vp2[i]));
-        }
-#pragma unroll
-        for (int i = 0; i < M; ++i) y[i] = vn[i];
-        double *acc = a.acc + r * M;
-        const double cr = a.cre[k];
-        if (!a.complex_coeff) {
-#pragma unroll
-            for (int i = 0; i < M; ++i) acc[i] = fma(cr, vn[i], acc[i]);
-        } else {
-            const double ci = a.cim[k];
-#pragma unroll
-            for (int i = 0; i + 1 < M; i += 2) {
-                double re = acc[i], im = acc[i + 1];
-                re = fma(cr, vn[i], re);
-                re = fma(-ci, vn[i + 1], re);
-                im = fma(cr, vn[i + 1], im);
-                im = fma(ci, vn[i], im);
-                acc[i] = re;
-                acc[i + 1] = im;
-            }
-        }
-    } else {
-#pragma unroll
-        for (int i = 0; i < M; ++i) y[i] = w[i];
-    }
+// Epilogue of one row at local power k: loads its rows, then as row_epilogue_loaded (the
+// y0copy of power 1 included).
+template <int M, int MODE, class AT>
+__device__ __forceinline__ void row_epilogue(const KArgs &a, int k, int64_t r, const AT (&w)[M], const double *xin) {
+    EpiRows<M> e;
+    epilogue_load<M, MODE>(a, k, r, xin, e);
+    row_epilogue_loaded<M, MODE, AT>(a, k, r, w, e);
 }
 
 // ----------------------------------------------------------------------------- K-MPK
@@ -382,29 +404,24 @@ __device__ __forceinline__ int slice_width(const int (&w)[4], int q) {
 // publishes the unit.  Phase B directly follows phase A of the same unit: a warp holds no
 // unit across a wait, so its lanes, which wait on the slot's mbarrier one by one, always
 // work on the same unit.
-template <int M> struct Prefetch {
+template <int M, class AT = double> struct Prefetch {
     static constexpr int B = Batch<M>::B;
     int unit;             // -1: nothing pending
     int slot;
     int r;                // this lane's row in the warp's first slice, -1 if none
     int off;              // offset of that row's entries in the slot (staged units)
     int width;            // width of the warp's first slice (staged units)
-    double x[B][M];       // x values of the first batch (entries j < min(B, width))
+    AT x[B][M];           // x values of the first batch (entries j < min(B, width))
 };
 
-template <int M>
-__device__ __forceinline__ const double *input_block(const KArgs &a, int k) {
-    return (k == 1 && a.k_offset == 0) ? a.x0 : a.ybase + (int64_t)((a.k_offset + k - 1) % a.ring) * a.ystride;
-}
-
 // phase A: request the x values of the warp's first batch of unit u (slot b)
-template <int M, bool STAGING>
+template <int M, bool STAGING, class AT>
 __device__ __forceinline__ void phase_a(const KArgs &a, const UnitInfo &u, int b, const int32_t *scol, int cwarp,
-                                        int lane, Prefetch<M> &pf) {
+                                        int lane, Prefetch<M, AT> &pf) {
     constexpr int B = Batch<M>::B;
     pf.unit = u.unit;
     pf.slot = b;
-    const double *xin = input_block<M>(a, u.unit & 31);
+    const AT *xin = InputAcc<M, AT>::get(a, u.unit & 31);
     pf.r = -1;
     pf.width = 0;
     pf.off = 0;
@@ -421,20 +438,22 @@ __device__ __forceinline__ void phase_a(const KArgs &a, const UnitInfo &u, int b
     for (int q = 0; q < B; ++q) {
         const int c = (pf.r >= 0 && q < pf.width) ? scol[pf.off + 32 * q] : -1;
 #pragma unroll
-        for (int i = 0; i < M; ++i) pf.x[q][i] = (c >= 0) ? xin[(int64_t)c * M + i] : 0.0;
+        for (int i = 0; i < M; ++i) pf.x[q][i] = (c >= 0) ? xin[(int64_t)c * M + i] : AT(0);
     }
 }
 
 // Completion of a unit by the compute warps.  Each warp releases the unit's slot (empty[b])
 // as soon as it has read everything it needs from the slot into registers, so that the
-// control warp can refill the slot while the warp still runs its FMA chain and stores; the
-// last warp to finish the unit publishes it.  The finish counters are indexed by the unit's
-// sequence number in the block (modulo kDoneRing), not by the slot, since a slot may hold the
-// next unit while warps still finish the previous one: a warp reaches unit seq + kDoneRing
-// only after every warp released unit seq + kDoneRing - slots >= seq + 1, which each warp
-// does after finishing unit seq.
-constexpr int kDoneRing = 2 * kMaxSlots;
-
+// control warp can refill the slot while the warp still runs its FMA chain and stores.
+// Publication is the publisher warp's job: a compute warp that finished the unit orders its
+// stores at block scope and adds one to the unit's finish counter; the publisher warp sees
+// the counters of up to 32 consecutive units reach the number of compute warps, issues one
+// fence at GPU scope for all of them (it acquires the compute warps' stores through the
+// counters and releases them to other blocks) and stores their flags.  No compute warp ever
+// waits for a fence at GPU scope.  The counters are indexed by the unit's sequence number in
+// the block modulo kDoneRing and only grow (use n of a counter completes at n times the
+// number of compute warps), so a lagging publisher never sees a counter that was reset.
+constexpr int kDoneRing = 64;
 // shapes 0-2 release the slot before their FMA chain too (1), or after their unit (0): the
 // early path holds a batch of entries in registers, more than shape 0's 40 a thread allow
 #ifndef MPK_EARLY_RELEASE_B
@@ -450,75 +469,111 @@ template <int CW>
 __device__ __forceinline__ void publish_unit(const KArgs &a, int32_t epoch, int unit, int seq, int *s_done, int lane) {
     __syncwarp();
     if (lane == 0) {
-        // the last compute warp to finish the unit publishes it (release at gpu scope after
-        // the other warps' stores were ordered at block scope)
-        __threadfence_block();
-        const int d = seq % kDoneRing;
-        if (atomicAdd(&s_done[d], 1) == CW - 1) {
-            s_done[d] = 0;
-            fence_acq_rel_gpu();
-            if (unit != a.drop_unit) st_relaxed(a.flags + (int64_t)(unit & 31) * a.nchunks + (unit >> 5), epoch);
+        __threadfence_block();  // this warp's stores before the count (block scope)
+        atomicAdd(&s_done[seq % kDoneRing], 1);
+    }
+}
+// The control warp may record sequence number i in the ring only once the publisher is past
+// i - kDoneRing (normally at once; bounded: false if the publisher made no progress in time).
+__device__ __forceinline__ bool useq_slot_free(volatile int *s_published, int i, int64_t limit) {
+    if (i - *s_published < kDoneRing) return true;
+    const uint64_t t0 = globaltimer();
+    while (i - *s_published >= kDoneRing)
+        if (timed_out(t0, limit)) return false;
+    __threadfence_block();
+    return true;
+}
+__device__ __forceinline__ int ld_relaxed_cta_shared(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.cta.shared.b32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+    return v;
+}
+// The publisher warp: publishes the block's units in sequence order, up to 32 at a time, until
+// every unit handed over (s_final, once set) is published.  Bounded like the compute warps.
+template <int CW>
+__device__ __forceinline__ void publisher_loop(const KArgs &a, int32_t epoch, const int *s_done, const int *s_useq,
+                                               volatile int *s_final, volatile int *s_published, int lane) {
+    int j = 0;
+    uint64_t t_idle = globaltimer();
+    for (;;) {
+        const int fin = *s_final;
+        const int jl = j + lane;
+        bool done = false;
+        if (fin < 0 || jl < fin) done = ld_relaxed_cta_shared(&s_done[jl % kDoneRing]) >= CW * (jl / kDoneRing + 1);
+        const unsigned int m = __ballot_sync(0xffffffffu, done);
+        const int cnt = (m == 0xffffffffu) ? 32 : __ffs(~m) - 1;  // finished units from j on, in a row
+        if (cnt > 0) {
+            fence_acq_rel_gpu();  // acquires the counted stores, releases them before the flags
+            if (lane < cnt) {
+                const int un = s_useq[jl % kDoneRing];
+                if (un != a.drop_unit) st_relaxed(a.flags + (int64_t)(un & 31) * a.nchunks + (un >> 5), epoch);
+            }
+            j += cnt;
+            __threadfence_block();  // the reads of s_useq before the progress that lets it be reused
+            if (lane == 0) *s_published = j;
+            t_idle = globaltimer();
+            continue;
         }
+        if (fin >= 0 && j >= fin) break;  // every unit handed over is published
+        if (timed_out(t_idle, 2 * a.wait_ns + 100000000LL)) break;  // the compute warps gave up
+        __nanosleep(32);
     }
 }
 
 // phase B: finish unit pf (all of the warp's rows), release its slot and publish it
-template <int M, int MODE, class VT, int SH>
-__device__ __forceinline__ void phase_b(const KArgs &a, int32_t epoch, const Prefetch<M> &pf, const UnitInfo *s_u,
+template <int M, int MODE, class VT, int SH, class AT>
+__device__ __forceinline__ void phase_b(const KArgs &a, int32_t epoch, const Prefetch<M, AT> &pf, const UnitInfo *s_u,
                                         const typename VT::T *sval0, const int32_t *scol0, int *s_done, uint64_t *s_empty,
                                         int cwarp, int lane, int seq) {
     constexpr int B = Batch<M>::B;
     const UnitInfo u = s_u[pf.slot];  // a copy: the slot is refilled once released
     const int k = pf.unit & 31;
     const double *xin = input_block<M>(a, k);
+    const AT *xacc = InputAcc<M, AT>::get(a, k);
     constexpr int kCompWarps = Shape<SH>::CW;
-    const SVal<VT> sval{sval0 + pf.slot * Shape<SH>::SE};
+    const SVal<VT, AT> sval{sval0 + pf.slot * Shape<SH>::SE};
     const int32_t *scol = kStageCol ? scol0 + pf.slot * Shape<SH>::SE : a.col + u.ebase;
     bool released = false;
     if (kEarlyReleaseB && Shape<SH>::SE > 0 && u.staged && u.nsl <= kCompWarps && pf.width <= B) {
         // the warp's one slice fits one batch: read its entries, release the slot, then compute
-        double v[B];
+        AT v[B];
         bool on[B];
 #pragma unroll
         for (int q = 0; q < B; ++q) {
             on[q] = pf.r >= 0 && q < pf.width && scol[pf.off + 32 * q] >= 0;
-            v[q] = on[q] ? sval[pf.off + 32 * q] : 0.0;
+            v[q] = on[q] ? sval[pf.off + 32 * q] : AT(0);
         }
         EpiRows<M> er;
         if (pf.r >= 0) epilogue_load<M, MODE>(a, k, pf.r, xin, er);
         release_slot<kCompWarps>(s_empty, pf.slot, lane);
         released = true;
         if (pf.r >= 0) {
-            double w[M];
+            AT w[M];
 #pragma unroll
-            for (int i = 0; i < M; ++i) w[i] = 0.0;
+            for (int i = 0; i < M; ++i) w[i] = AT(0);
 #pragma unroll
             for (int q = 0; q < B; ++q)
                 if (on[q]) {
 #pragma unroll
-                    for (int i = 0; i < M; ++i) w[i] = fma(v[q], pf.x[q][i], w[i]);
+                    for (int i = 0; i < M; ++i) w[i] = afma(v[q], pf.x[q][i], w[i]);
                 }
-            row_epilogue_loaded<M, MODE>(a, k, pf.r, w, er);
+            row_epilogue_loaded<M, MODE, AT>(a, k, pf.r, w, er);
         }
     } else if (Shape<SH>::SE > 0 && u.staged) {
         if (pf.r >= 0) {  // first slice: prefetched first batch, then the rest of the row
-            double w[M];
+            AT w[M];
 #pragma unroll
-            for (int i = 0; i < M; ++i) w[i] = 0.0;
+            for (int i = 0; i < M; ++i) w[i] = AT(0);
 #pragma unroll
             for (int q = 0; q < B; ++q) {
                 if (q < pf.width && scol[pf.off + 32 * q] >= 0) {
-                    const double v = sval[pf.off + 32 * q];
+                    const AT v = sval[pf.off + 32 * q];
 #pragma unroll
-                    for (int i = 0; i < M; ++i) w[i] = fma(v, pf.x[q][i], w[i]);
+                    for (int i = 0; i < M; ++i) w[i] = afma(v, pf.x[q][i], w[i]);
                 }
             }
-            if (pf.width > B) row_sum_from<M, 2>(sval, scol, pf.off, B, pf.width, xin, w);  // rare: wide rows
-            row_epilogue<M, MODE>(a, k, pf.r, w, xin);
-            if (k == 1 && a.y0copy) {
-#pragma unroll
-                for (int i = 0; i < M; ++i) a.y0copy[(int64_t)pf.r * M + i] = a.x0[(int64_t)pf.r * M + i];
-            }
+            if (pf.width > B) row_sum_from<M, 2, AT>(sval, scol, pf.off, B, pf.width, xacc, w);  // rare: wide rows
+            row_epilogue<M, MODE, AT>(a, k, pf.r, w, xin);
         }
         for (int sl = cwarp + kCompWarps; sl < u.nsl; sl += kCompWarps) {  // further slices (wide chunks)
             const int64_t r = (int64_t)u.row0 + 32 * sl + lane;
@@ -526,13 +581,9 @@ __device__ __forceinline__ void phase_b(const KArgs &a, int32_t epoch, const Pre
 #pragma unroll
             for (int q = 0; q < kRecSlices; ++q) pre += (q < sl) ? slice_width(u.widths, q) : 0;
             if (r >= u.row1) continue;
-            double w[M];
-            row_sum<M, 2>(sval, scol, 32 * pre + lane, slice_width(u.widths, sl), xin, w);  // rare: wide chunks
-            row_epilogue<M, MODE>(a, k, r, w, xin);
-            if (k == 1 && a.y0copy) {
-#pragma unroll
-                for (int i = 0; i < M; ++i) a.y0copy[r * M + i] = a.x0[r * M + i];
-            }
+            AT w[M];
+            row_sum<M, 2, AT>(sval, scol, 32 * pre + lane, slice_width(u.widths, sl), xacc, w);  // rare: wide chunks
+            row_epilogue<M, MODE, AT>(a, k, r, w, xin);
         }
     } else {  // entries in global memory (chunk too large to stage): the slot holds nothing
         release_slot<kCompWarps>(s_empty, pf.slot, lane);
@@ -541,22 +592,19 @@ __device__ __forceinline__ void phase_b(const KArgs &a, int32_t epoch, const Pre
             const int64_t r = (int64_t)u.row0 + 32 * sl + lane;
             if (r >= u.row1) continue;
             const int64_t s0 = __ldg(a.slice_ptr + u.slice0 + sl), s1 = __ldg(a.slice_ptr + u.slice0 + sl + 1);
-            double w[M];
+            AT w[M];
             // entries whose x loads are issued together: the unstaged shape issues a row's
             // loads in batches; the staged shapes keep this rare path small (registers)
             constexpr int BU = Shape<SH>::SE == 0 ? Batch<M>::B : 1;
-            row_sum<M, BU>(GVal<VT>{static_cast<const typename VT::T *>(a.val) + u.ebase}, GCol{a.col + u.ebase},
-                           s0 - u.ebase + lane, (int)((s1 - s0) >> 5), xin, w);
-            row_epilogue<M, MODE>(a, k, r, w, xin);
-            if (k == 1 && a.y0copy) {
-#pragma unroll
-                for (int i = 0; i < M; ++i) a.y0copy[r * M + i] = a.x0[r * M + i];
-            }
+            row_sum<M, BU, AT>(GVal<VT, AT>{static_cast<const typename VT::T *>(a.val) + u.ebase},
+                               GCol{a.col + u.ebase}, s0 - u.ebase + lane, (int)((s1 - s0) >> 5), xacc, w);
+            row_epilogue<M, MODE, AT>(a, k, r, w, xin);
         }
     }
     if (!released) release_slot<kCompWarps>(s_empty, pf.slot, lane);
     publish_unit<kCompWarps>(a, epoch, pf.unit, seq, s_done, lane);
 }
+
 // dependency flags v0 .. v0+127 of a unit (4 per lane); flags past `total` read as ready
 __device__ __forceinline__ void dep_load(const KArgs &a, int32_t epoch, int k, const int (&lo)[kDepRanges],
                                          const int (&len)[kDepRanges], int total, int v0, int lane, int (&got)[4]) {
@@ -685,7 +733,7 @@ __device__ __forceinline__ void phase_x(const KArgs &a, int32_t epoch, const Uni
 #pragma unroll
                     for (int i = 0; i < M; ++i) w[i] = fma(v[q], xv[q][i], w[i]);
                 }
-            row_epilogue_loaded<M, MODE>(a, k, r, w, er);
+            row_epilogue_loaded<M, MODE, double>(a, k, r, w, er);
         }
         publish_unit<CW>(a, epoch, u.unit, seq, s_done, lane);
         return;
@@ -723,18 +771,21 @@ __device__ __forceinline__ void phase_x(const KArgs &a, int32_t epoch, const Uni
                     for (int i = 0; i < M; ++i) w[i] = fma(v[q], xv[q][i], w[i]);
                 }
         }
-        row_epilogue_loaded<M, MODE>(a, k, r, w, er);
+        row_epilogue_loaded<M, MODE, double>(a, k, r, w, er);
     }
     release_slot<CW>(s_empty, b, lane);
     publish_unit<CW>(a, epoch, u.unit, seq, s_done, lane);
 }
 
-template <int M, int MODE, bool TRACE, class VT, int SH>
+template <int M, int MODE, bool TRACE, class VT, int SH, bool A32 = false>
 __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::blocks)) k_mpk(const KArgs a) {
+    using AT = typename std::conditional<A32, float, double>::type;  // accumulator of the row sums
+    static_assert(!(A32 && Shape<SH>::X), "shape 3 stages binary64 input rows only");
     constexpr int kCompWarps = Shape<SH>::CW, kStageEntries = Shape<SH>::SE;
     constexpr int kSlots = Shape<SH>::SL;
     constexpr bool XS = Shape<SH>::X;
     constexpr int kCtl = Shape<SH>::CTL;
+    constexpr int kPub = kCtl;  // warp index of the publisher warp (after the control warps)
     constexpr int kRing = 4;  // split control: ready units between the poll and the stage warp
     static_assert(kSlots >= 2 && kSlots <= kMaxSlots, "slots");
     using T = typename VT::T;
@@ -745,6 +796,8 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
     __shared__ UnitInfo s_u[kSlots];
     __shared__ volatile int s_final;  // units handed over in total; -1 while the control warp runs
     __shared__ int s_done[kDoneRing];  // compute warps finished with a unit (by its sequence number)
+    __shared__ int s_useq[kDoneRing];  // unit id of each sequence number (for the publisher warp)
+    __shared__ volatile int s_published;  // units published so far (the publisher's progress)
     // split control (two control warps): ring of ready units, its mbarriers, stop flag
     __shared__ __align__(8) uint64_t s_rfull[kCtl == 2 ? kRing : 1];
     __shared__ __align__(8) uint64_t s_rfree[kCtl == 2 ? kRing : 1];
@@ -773,6 +826,7 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
     if (tid == 0) {
         s_epoch = (int32_t)ld_relaxed(reinterpret_cast<const int32_t *>(a.epoch_word)) + 1;
         s_final = -1;
+        s_published = 0;
         s_stop = 0;
         for (int q = 0; q < kDoneRing; ++q) s_done[q] = 0;
         for (int q = 0; q < kSlots; ++q) {
@@ -789,7 +843,9 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
     __syncthreads();
     const int32_t epoch = s_epoch;
 
-    if (warp < kCtl) {
+    if (warp == kPub) {
+        publisher_loop<kCompWarps>(a, epoch, s_done, s_useq, &s_final, &s_published, lane);
+    } else if (warp < kCtl) {
       if constexpr (kCtl == 2) {
         // ---------------------------------------------------------- split control (shape 3)
         // Warp 0 claims units in ticket order, polls their dependencies and pushes each ready
@@ -967,6 +1023,15 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
                         asm volatile("st.shared.f64 [%0], %1;" ::"r"(xc.tdst), "d"(v) : "memory");
                     }
                 }
+                if (!useq_slot_free(&s_published, i, a.wait_ns)) {  // (split control: copies may be in flight)
+                    record_timeout();
+                    if (lane == 0) mbar_arrive(&s_full[b]);
+                    const uint64_t t1 = globaltimer();
+                    while (!mbar_try_wait(&s_full[b], (i / kSlots) & 1))
+                        if (timed_out(t1, a.wait_ns)) break;
+                    break;
+                }
+                if (lane == 0) s_useq[i % kDoneRing] = un;
                 __syncwarp();
                 if (tr && lane == 0) s_tarr[b] = globaltimer();
                 if (lane == 0) mbar_arrive(&s_full[b]);
@@ -1137,6 +1202,23 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
                     asm volatile("st.shared.f64 [%0], %1;" ::"r"(xc.tdst), "d"(v) : "memory");
                 }
             }
+            if (!useq_slot_free(&s_published, i, a.wait_ns)) {
+                // the unit's entries are staged but it is not handed over: record the failure,
+                // complete the slot's phase for its bulk copy and wait for the copy, then stop
+                record_timeout();
+                if (lane == 0) {
+                    s_final = i;
+                    mbar_arrive(&s_full[b]);
+                }
+                if (u.staged) {
+                    const uint64_t t1 = globaltimer();
+                    while (!mbar_try_wait(&s_full[b], (i / kSlots) & 1))
+                        if (timed_out(t1, a.wait_ns)) break;
+                }
+                aborted = true;
+                break;
+            }
+            if (lane == 0) s_useq[i % kDoneRing] = u.unit;
             __syncwarp();
             if (tr && lane == 0) s_tarr[b] = globaltimer();
             if (lane == 0) mbar_arrive(&s_full[b]);
@@ -1166,8 +1248,8 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
       }
     } else {
         // ------------------------------------------------------------------ compute warps
-        const int cw = warp - kCtl;
-        Prefetch<M> pf;
+        const int cw = warp - kCtl - 1;
+        Prefetch<M, AT> pf;
         pf.unit = -1;
         for (int i = 0;; ++i) {
             const int b = i % kSlots;
@@ -1213,20 +1295,21 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
                 if (tr && lane == 0) tr_add(13, clock64() - c1);
             } else {
                 const long long c0 = tr ? clock64() : 0;
-                phase_a<M, (kStageEntries > 0)>(a, s_u[b], b, kStageCol ? scol0 + b * kStageEntries : a.col + s_u[b].ebase,
-                                                 cw, lane, pf);
+                phase_a<M, (kStageEntries > 0), AT>(a, s_u[b], b,
+                                                     kStageCol ? scol0 + b * kStageEntries : a.col + s_u[b].ebase, cw,
+                                                     lane, pf);
                 if (tr) {  // wait for the gathers (integer ops only) to split the unit time
                     int h = 0;
 #pragma unroll
-                    for (int q = 0; q < Batch<M>::B; ++q) h ^= __double2hiint(pf.x[q][0]);
+                    for (int q = 0; q < Batch<M>::B; ++q) h ^= hi_bits(pf.x[q][0]);
                     int d;
                     asm volatile("add.u32 %0, %1, 0;" : "=r"(d) : "r"(h));
                     const long long c1 = clock64();
                     if (lane == 0) tr_add(12, c1 - c0);
-                    phase_b<M, MODE, VT, SH>(a, epoch, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane, i);
+                    phase_b<M, MODE, VT, SH, AT>(a, epoch, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane, i);
                     if (lane == 0) tr_add(13, clock64() - c1);
                 } else {
-                    phase_b<M, MODE, VT, SH>(a, epoch, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane, i);
+                    phase_b<M, MODE, VT, SH, AT>(a, epoch, pf, s_u, sval0, scol0, s_done, s_empty, cw, lane, i);
                 }
                 pf.unit = -1;
             }
@@ -1258,26 +1341,34 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
 
 
 // ----------------------------------------------------------------------------- shape entry points
-template <int M, int MODE, class VT, int SH> static void *mpk_fn(bool trace) {
+template <int M, int MODE, class VT, int SH> static void *mpk_fn(bool trace, bool a32) {
+    if (a32) {
+        if constexpr (Shape<SH>::X || std::is_same<VT, ValF64>::value) {
+            fail(MPK_ERR_UNSUPPORTED, "binary32 accumulation needs float32 or bfloat16 values and a shape other than 3");
+        } else {
+            if (trace) fail(MPK_ERR_UNSUPPORTED, "trace counters need binary64 accumulation");
+            return (void *)k_mpk<M, MODE, false, VT, SH, true>;
+        }
+    }
     return trace ? (void *)k_mpk<M, MODE, true, VT, SH> : (void *)k_mpk<M, MODE, false, VT, SH>;
 }
 
-template <class VT, int SH> static void *select_mpk_vs(int mode, int m, bool trace) {
-#define SEL(MM)                                                                 \
-    if (m == MM) {                                                              \
-        if (mode == MODE_POWERS) return mpk_fn<MM, MODE_POWERS, VT, SH>(trace); \
-        return mpk_fn<MM, MODE_CHEB, VT, SH>(trace);                            \
+template <class VT, int SH> static void *select_mpk_vs(int mode, int m, bool trace, bool a32) {
+#define SEL(MM)                                                                           \
+    if (m == MM) {                                                                        \
+        if (mode == MODE_POWERS) return mpk_fn<MM, MODE_POWERS, VT, SH>(trace, a32);      \
+        return mpk_fn<MM, MODE_CHEB, VT, SH>(trace, a32);                                 \
     }
     SEL(1) SEL(2) SEL(4) SEL(8)
 #undef SEL
     fail(MPK_ERR_UNSUPPORTED, "nrhs %d", m);
 }
 
-// k_mpk of block shape SH for (mode, nrhs, trace, value type), and its dynamic shared memory
-template <int SH> void *select_mpk_shape(int mode, int m, bool trace, int vtype) {
-    if (vtype == MPK_F64) return select_mpk_vs<ValF64, SH>(mode, m, trace);
-    if (vtype == MPK_F32) return select_mpk_vs<ValF32, SH>(mode, m, trace);
-    if (vtype == MPK_BF16) return select_mpk_vs<ValBF16, SH>(mode, m, trace);
+// k_mpk of block shape SH for (mode, nrhs, trace, value type, accumulator), and its dynamic shared memory
+template <int SH> void *select_mpk_shape(int mode, int m, bool trace, int vtype, bool a32) {
+    if (vtype == MPK_F64) return select_mpk_vs<ValF64, SH>(mode, m, trace, a32);
+    if (vtype == MPK_F32) return select_mpk_vs<ValF32, SH>(mode, m, trace, a32);
+    if (vtype == MPK_BF16) return select_mpk_vs<ValBF16, SH>(mode, m, trace, a32);
     fail(MPK_ERR_UNSUPPORTED, "value type %d", vtype);
 }
 
@@ -1287,9 +1378,9 @@ template <int SH> int smem_bytes_shape(int vtype) {
 }
 
 // defined in mpk_kshape<N>.cu
-void *select_mpk_shape0(int mode, int m, bool trace, int vtype);
-void *select_mpk_shape1(int mode, int m, bool trace, int vtype);
-void *select_mpk_shape2(int mode, int m, bool trace, int vtype);
-void *select_mpk_shape3(int mode, int m, bool trace, int vtype);
+void *select_mpk_shape0(int mode, int m, bool trace, int vtype, bool a32);
+void *select_mpk_shape1(int mode, int m, bool trace, int vtype, bool a32);
+void *select_mpk_shape2(int mode, int m, bool trace, int vtype, bool a32);
+void *select_mpk_shape3(int mode, int m, bool trace, int vtype, bool a32);
 
 }  // namespace mpk

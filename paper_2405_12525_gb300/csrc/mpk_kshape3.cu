@@ -2,5 +2,7 @@
 #include "mpk_kernel_dev.cuh"
 
 namespace mpk {
-void *select_mpk_shape3(int mode, int m, bool trace, int vtype) { return select_mpk_shape<3>(mode, m, trace, vtype); }
+void *select_mpk_shape3(int mode, int m, bool trace, int vtype, bool a32) {
+    return select_mpk_shape<3>(mode, m, trace, vtype, a32);
+}
 }  // namespace mpk

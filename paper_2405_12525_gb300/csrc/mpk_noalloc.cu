@@ -98,12 +98,14 @@ extern "C" mpk_status mpk_apply_noalloc(const mpk_plan_t *Ph, const double *X, i
             a.x0 = X;
             a.ybase = Y;
             a.ystride = (int64_t)P.n * P.m;
+            a.shadow = P.shadow;
             a.ring = p + 1;
             a.p_launch = p;
             a.y0copy = (Y != X) ? Y : nullptr;
             if (a.y0copy && P.level0_rows > 0)  // level 0 of a level-capped plan has no units
                 MPK_CUDA(cudaMemcpyAsync(Y, X, sizeof(double) * (size_t)P.level0_rows * P.m,
                                          cudaMemcpyDeviceToDevice, s));
+            if (P.accum == MPK_F32) launch_round_f32(X, (int64_t)P.n * P.m, P.shadow, s);  // plan-owned ring
             launch_mpk(P, a, 0, s);
         }
         if (status) {

@@ -343,6 +343,19 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         P->p_max = pmax;
         P->val_type = A->val_type;
         P->val_bytes = A->val_type == MPK_F64 ? 8 : (A->val_type == MPK_F32 ? 4 : 2);
+        // binary32 accumulation: values stored in float32 or bfloat16 (exact in binary32), the
+        // staged or sweep engine, single plans
+        if (o->accum != MPK_F64 && o->accum != MPK_F32) fail(MPK_ERR_INVALID, "accum must be MPK_F64 or MPK_F32");
+        P->accum = o->accum;
+        if (P->accum == MPK_F32) {
+            if (A->val_type == MPK_F64)
+                fail(MPK_ERR_UNSUPPORTED, "binary32 accumulation needs values stored as float32 or bfloat16");
+            if (o->engine == MPK_ENGINE_WARP || o->trace || o->level_capped || inst_row != nullptr ||
+                o->shape - 1 == kShapeX)
+                fail(MPK_ERR_UNSUPPORTED,
+                     "binary32 accumulation runs on the staged engine (shapes 0-2) or the sweep engine, without "
+                     "trace, level caps or batching");
+        }
         P->order = o->order;
         P->identity = (L == nullptr);
         P->chunk_rows = chunk_rows;
@@ -460,13 +473,12 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         for (int32_t i = 0; i < NS; ++i) sptr[i + 1] = sptr[i] + 32 * (int64_t)width[i];
         P->padded = sptr[NS];
 
-        // ---- block shape: shape 0 when its slot holds a full chunk of slices of the mean
-        //      width, else shape 1 when its slot holds at least a third of a chunk, else
-        //      unstaged (measured: 27-point stencils run 1.7x faster unstaged, banded graphs
-        //      of ~15 entries a row 10% faster on shape 1).  Shape 3 (input rows staged too)
-        //      is taken only when the options name it; it is not chosen automatically, since on
-        //      the 3-D Laplacian it measured slower than shape 0 (its control warp, not the
-        //      FP64 pipe, sets the pace).
+        // ---- block shape: shape 1 when its slot holds at least 6 slices of the mean
+        //      width, else unstaged (measured: 27-point stencils run 1.7x
+        //      faster unstaged).  Shape 1's fewer, larger units beat shape 0 on the 3-D
+        //      Laplacian (2.20 ms against 2.58 ms at 256^3, p = 8), since the per-unit work of
+        //      the control warp sets the pace; shapes 0 and 3 (input rows staged too) are taken
+        //      only when the options name them.
         if (o->shape < 0 || o->shape > kNumShapes) fail(MPK_ERR_INVALID, "shape must be in [0, %d]", kNumShapes);
         int fallback_shape = 0;
         bool try_x = false;
@@ -477,7 +489,7 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
             auto fits = [&](int sh, int slices) {
                 return (int64_t)slices * P->padded <= (int64_t)kShapes[sh].stage_entries * std::max(NS, 1);
             };
-            fallback_shape = fits(0, kShapes[0].comp_warps) ? 0 : (fits(1, kShapes[1].comp_warps / 3) ? 1 : 2);
+            fallback_shape = fits(1, 6) ? 1 : 2;  // up to 24 entries a row on average
             try_x = false;
         }
         const bool x_forced = o->shape - 1 == kShapeX;
@@ -817,6 +829,7 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         MPK_CUDA(cudaMemsetAsync(P->ctl, 0, 8 * sizeof(unsigned int), s));
         P->work_slots = std::max(pmax + 1, 4);  // all powers (original order) or ring of 3 + accumulator
         P->work = P->arena.alloc_n<double>((int64_t)P->work_slots * n * m + 1);
+        if (P->accum == MPK_F32) P->shadow = P->arena.alloc_n<float>(2 * (int64_t)n * m + 1);
         MPK_CUDA(cudaStreamSynchronize(s));  // host vectors above must outlive their copies
     } catch (...) {
         P->arena.release();

@@ -428,8 +428,8 @@ def test_apply_replays_from_cuda_graph(mpk):
 @pytest.mark.parametrize("name", ["lap3d_17x9x6", "lap2d_64", "band_3000", "int_nonsym_500", "xxz_10", "empty_rows",
                                   "disconnected", "single"])
 def test_apply_every_block_shape(mpk, shape, name):
-    # the block shapes of the staged kernel (13 warps with 3072-entry slots, 15 warps with
-    # 4096, 15 warps reading entries from global memory, and input rows staged as well) give
+    # the block shapes of the staged kernel (13 warps with 3072-entry slots, 16 warps with
+    # 4608, 15 warps reading entries from global memory, and input rows staged as well) give
     # the same bits; shape 3 refuses a plan whose chunks read input rows beyond a slot
     make, sym = MATRICES[name]
     A = make()
@@ -497,13 +497,13 @@ def test_input_rows_staged_shape(mpk, m, order):
 
 
 def test_automatic_block_shape(mpk):
-    # rows of 7 entries fill a 3072-entry slot with 13 slices (shape 0); 13-15 entries a row
-    # fill a 4096-entry slot with at least 5 (shape 1); 27-point rows go unstaged (shape 2)
-    for A, want in ((gen.laplacian_3d(30, 30, 30), 0), (gen.xxz_chain(12, stream=99), 1), (gen.stencil27(40), 2)):
+    # rows of 7 and of 13-15 entries fill a 4608-entry slot with at least 6 of 16 slices
+    # (shape 1); 27-point rows go unstaged (shape 2)
+    for A, want in ((gen.laplacian_3d(30, 30, 30), 1), (gen.xxz_chain(12, stream=99), 1), (gen.stencil27(40), 2)):
         dA = _dev(A, mpk, True)
         P = mpk.plan(dA, mpk.build_levels(dA, 0), p_max=4)
         d = P.describe()
-        assert d["shape"] == want and d["engine"] == 0 and d["chunk_rows"] == 32 * (13 if want == 0 else 15)
+        assert d["shape"] == want and d["engine"] == 0 and d["chunk_rows"] == 32 * (16 if want == 1 else 15)
 
 
 @pytest.mark.parametrize("seed", [1, 2, 0x5EED])
