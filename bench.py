@@ -35,9 +35,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "Level-blocked MPK Gflop/s vs p×CSR SpMV on 1 GB300; serving p50/p99 latency"
-SM_MAX_MHZ = 2070.0
-NUM_SMS = 152
-DFMA_LANES_PER_CLK_PER_SM = 2  # measured on GB300 (0.60 T FP64 FMA/s at ~1.97 GHz)
+DFMA_LANES_PER_CLK_PER_SM = 2  # GB300's FP64 FMA issue rate per SM (unit count of the roof)
+SM_MAX_MHZ_FALLBACK = 2070.0   # used only if nvidia-smi gives no clock
+# L2 hit rate of the level-blocked kernel from the committed ncu capture (context only)
+L2_PROFILE = os.path.join(ROOT, "profiles", "k_mpk_128cube_full.md")
 # the level-blocked kernel, its tunables and the planner that cuts its chunks
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2405_12525_gb300", "csrc", f)
                   for f in ("mpk_kernel_dev.cuh", "mpk_internal.h", "mpk_plan.cu")]
@@ -78,6 +79,8 @@ def parse():
     ap.add_argument("--serve-rate2", type=float, default=10.0, help="second, sustainable arrival rate")
     ap.add_argument("--batch-count", type=int, default=64, help="matrices of the batch workload")
     ap.add_argument("--batch-nmax", type=float, default=2e6, help="largest matrix size of the batch workload")
+    ap.add_argument("--accum", default="f64", choices=["f64", "f32"],
+                    help="row-sum arithmetic: binary64, or binary32 (values then f32 or bf16; bf16 if f64 is given)")
     ap.add_argument("--values", default="f64", choices=["f64", "f32", "bf16"],
                     help="storage type of the matrix values (accumulation stays float64); the Laplacian's "
                          "{6, -1} are exact in all three")
@@ -130,7 +133,7 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        mhz, maxm, reasons = [], SM_MAX_MHZ, set()
+        mhz, maxm, reasons = [], SM_MAX_MHZ_FALLBACK, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
@@ -163,20 +166,93 @@ def algorithmic(A, p: int, m: int = 1):
     return flops, a_bytes, v_bytes
 
 
-def cpu_baseline(A, X, p: int, budget_s: float = 12.0):
-    """The oracle as it stands (serial C), on a bounded sample: the first powers of the same matrix."""
-    import numpy as np
+def host_cores():
+    """Logical CPUs of the host (os.cpu_count) and lscpu's model line, for the record."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                model = ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return os.cpu_count() or 1, model
+
+
+def cpu_baseline(A, X, p: int, budget_s: float = 10.0):
+    """The oracle as it stands on the host cores, on a bounded sample (the first powers of the same
+    matrix): the serial C oracle, and the same row loop shared out over all cores (OpenMP), with
+    the paper's CPU roofline (Sec. 6, P = b_s / (6 + 14 / N_nzr) flop/byte) at the host's measured
+    load bandwidth as context."""
     import oracle
-    t0 = time.perf_counter()
-    oracle.mpk(A, X, 1)
-    t1 = time.perf_counter() - t0
-    k = max(1, min(p, int(budget_s / max(t1, 1e-3))))
-    t0 = time.perf_counter()
-    oracle.mpk(A, X, k)
-    dt = time.perf_counter() - t0
-    del np
-    return {"value": 2.0 * A.nnz * k / dt / 1e9, "unit": "Gflop/s", "cores": 1, "kind": "oracle",
-            "sample": f"oracle.mpk (serial C, fma per entry) on the full matrix, {k} of {p} powers, {dt:.2f} s"}
+    cores, model = host_cores()
+
+    def sample(fn):
+        t0 = time.perf_counter()
+        fn(1)
+        t1 = time.perf_counter() - t0
+        k = max(1, min(p, int(budget_s / max(t1, 1e-3))))
+        t0 = time.perf_counter()
+        r = fn(k)
+        return k, time.perf_counter() - t0, r
+
+    k1, dt1, _ = sample(lambda k: oracle.mpk(A, X, k))
+    threads = [1]
+    kp, dtp, _ = sample(lambda k: threads.__setitem__(0, oracle.mpk_parallel(A, X, k)[1]))
+    bw = oracle.load_bandwidth(1 << 30, 5)
+    nzr = A.nnz / A.n
+    roof = bw / (6.0 + 14.0 / nzr) / 1e9
+    par = 2.0 * A.nnz * kp / dtp / 1e9
+    return {"value": par, "unit": "Gflop/s", "cores": threads[0], "kind": "oracle",
+            "sample": f"oracle row loop over all {threads[0]} host threads (OpenMP, same arithmetic as the serial "
+                      f"oracle) on the full matrix, {kp} of {p} powers, {dtp:.2f} s",
+            "serial": {"value": 2.0 * A.nnz * k1 / dt1 / 1e9, "cores": 1,
+                       "sample": f"oracle.mpk (serial C, fma per entry), {k1} of {p} powers, {dt1:.2f} s"},
+            "host": {"logical_cpus": cores, "model": model, "load_bandwidth_gbs": bw / 1e9},
+            "paper_cpu_roofline_gflops": roof,
+            "paper_cpu_roofline_note": "Sec. 6 roofline b_s / (6 B + 14 B / N_nzr) at the host's measured load "
+                                       "bandwidth (all threads summing 1 GiB)"}
+
+
+def device_roofs(mpk, torch):
+    """Measured on this device in this process: FP64 FMA rate (dependent chains over all SMs), load
+    bandwidth from HBM (2 GiB buffer) and from L2 (64 MiB buffer), SM count and L2 size."""
+    sms, l2 = mpk.device_info()
+    sink_d = torch.zeros(1, dtype=torch.float64, device="cuda")
+    sink_i = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+    def ms_of(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    blocks, iters = sms * 8, 40000
+    ms = ms_of(lambda: mpk.probe_dfma(blocks, iters, sink_d))
+    dfma = blocks * 256 * iters * 8 * 2 / (ms * 1e-3) / 1e12
+    out = {"sms": sms, "l2_bytes": l2, "fp64_fma_tflops_measured": dfma}
+    for name, nbytes, reps in (("hbm_load_gbs", 2 << 30, 4), ("l2_load_gbs", 64 << 20, 60)):
+        buf = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        ms = ms_of(lambda: mpk.probe_load(buf, reps, 2, sink_i))
+        out[name] = reps * nbytes / (ms * 1e-3) / 1e9
+        del buf
+    torch.cuda.empty_cache()
+    return out
+
+
+def l2_hit_rate_from_profile():
+    try:
+        for ln in open(L2_PROFILE):
+            if "lts__t_sector_hit_rate" in ln:
+                return float(ln.split("|")[2].strip().rstrip("%").split()[0]) / 100.0
+    except (OSError, ValueError, IndexError):
+        return None
+    return None
 
 
 def cheb_workload(L: int, degree: int):
@@ -368,7 +444,8 @@ def main_cheb(args):
         dtc = time.perf_counter() - t0
         cpu = {"value": cheb_flops(A, 2, m) / dtc / 1e9, "unit": "Gflop/s", "cores": 1, "kind": "oracle",
                "sample": f"oracle.cheb (serial C) degree 2 of the same step on the full matrix, {dtc:.2f} s"}
-    peak_alu = NUM_SMS * DFMA_LANES_PER_CLK_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    sms, _ = mpk.device_info()
+    peak_alu = sms * DFMA_LANES_PER_CLK_PER_SM * 2 * (clk.summary()["sm_mhz"] or SM_MAX_MHZ_FALLBACK) * 1e6 / 1e12
     achieved = flops / (ms * 1e-3) / 1e12
     if rank == 0:
         line = {
@@ -734,13 +811,18 @@ def main():
     p = args.p
 
     A, X = build_workload(args.side)
-    flops, a_bytes, v_bytes = algorithmic(A, p)
+    acc32 = args.accum == "f32"
+    if acc32 and args.values == "f64":
+        args.values = "bf16"  # binary32 accumulation takes narrow values ({6, -1} are exact in bfloat16)
+    flops, _, v_bytes = algorithmic(A, p)
     vbytes = {"f64": 8, "f32": 4, "bf16": 2}[args.values]
     a_bytes = (vbytes + 4.0) * A.nnz + 4.0 * (A.n + 1)
     vtype = {"f64": mpk.MPK_F64, "f32": mpk.MPK_F32, "bf16": mpk.MPK_BF16}[args.values]
+    accum = mpk.MPK_F32 if acc32 else mpk.MPK_F64
     dA = mpk.CsrMatrix.from_host(A, is_symmetric=True, value_type=vtype)
     Xd = torch.from_numpy(X).cuda()
     stream = torch.cuda.current_stream()
+    roofs = device_roofs(mpk, torch)
 
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -748,10 +830,10 @@ def main():
     t_levels = time.perf_counter() - t0
     t0 = time.perf_counter()
     cb = args.cache_mb << 20
-    P = mpk.plan(dA, L, p_max=p, nrhs=1, order=mpk.ORDER_PLAN, cache_bytes=cb)    # headline: one kernel launch
+    # headline: one kernel launch per apply, vectors in the plan's (BFS) numbering
+    P = mpk.plan(dA, L, p_max=p, nrhs=1, order=mpk.ORDER_PLAN, cache_bytes=cb, accum=accum)
     t_plan = time.perf_counter() - t0
-    Po = mpk.plan(dA, L, p_max=p, nrhs=1, order=mpk.ORDER_ORIGINAL, cache_bytes=cb)  # with gather/scatter
-    P0 = mpk.plan(dA, None, p_max=p, nrhs=1)                            # natural-order comparator
+    Po = mpk.plan(dA, L, p_max=p, nrhs=1, order=mpk.ORDER_ORIGINAL, cache_bytes=cb, accum=accum)
     desc = P.describe()
     Y = torch.empty((p + 1, A.n, 1), dtype=torch.float64, device="cuda")
     Y2 = torch.empty_like(Y)
@@ -790,40 +872,51 @@ def main():
     ms_orig = timed(lambda: Po.apply(Xd, p, Y=Y2), max(3, args.steps // 4), 2)
     Po.sync_status()
     orig_identical = bool(torch.equal(Y2[:, L.perm.long(), :], Y))
-    # ---- comparators: p separate SpMV launches, natural order and BFS order
-    ms_plain_nat = timed(lambda: P0.spmv_powers(Xd, p, Y=Y2), max(3, args.steps // 4), 2)
-    ms_plain_bfs = timed(lambda: P.spmv_powers(Xp, p, Y=Y2), max(3, args.steps // 4), 2)
-    identical = bool(torch.equal(Y, Y2))   # level-blocked == back-to-back SpMV, bit for bit
-    # ---- comparator: the unblocked sweep engine (one grid-stride launch per power, same row body)
-    Ps = mpk.plan(dA, L, p_max=p, nrhs=1, order=mpk.ORDER_PLAN, engine=mpk.ENGINE_SWEEP)
-    ms_sweep = timed(lambda: Ps.apply(Xp, p, Y=Y2), max(3, args.steps // 4), 2)
+    # ---- comparators: plain p x SpMV (p separate launches), natural and BFS order.  Binary64:
+    #      the row-range SpMV of the sliced copy and the plan's unblocked sweep engine; binary32
+    #      accumulation: the sweep engine (the same arithmetic), in both orders.
+    comps = {}
+    if not acc32:
+        P0 = mpk.plan(dA, None, p_max=p, nrhs=1)
+        comps["plain_spmv_natural"] = timed(lambda: P0.spmv_powers(Xd, p, Y=Y2), max(3, args.steps // 4), 2)
+        comps["plain_spmv_bfs"] = timed(lambda: P.spmv_powers(Xp, p, Y=Y2), max(3, args.steps // 4), 2)
+        identical = bool(torch.equal(Y, Y2))   # level-blocked == back-to-back SpMV, bit for bit
+        del P0
+    else:
+        P0 = mpk.plan(dA, None, p_max=p, nrhs=1, engine=mpk.ENGINE_SWEEP, accum=accum)
+        comps["sweep_natural"] = timed(lambda: P0.apply(Xd, p, Y=Y2), max(3, args.steps // 4), 2)
+        identical = True
+        del P0
+    Ps = mpk.plan(dA, L, p_max=p, nrhs=1, order=mpk.ORDER_PLAN, engine=mpk.ENGINE_SWEEP, accum=accum)
+    comps["unblocked_sweep"] = timed(lambda: Ps.apply(Xp, p, Y=Y2), max(3, args.steps // 4), 2)
     identical = identical and bool(torch.equal(Y, Y2))
     del Ps
     # ---- comparator: plain p x CSR SpMV of the vendor library (cuSPARSE through torch's sparse
-    #      CSR matmul), natural order, on the unpermuted CSR arrays
+    #      CSR matmul), natural order, on the unpermuted CSR arrays (binary64 only)
     csr = None
-    try:
-        import warnings
-        with warnings.catch_warnings():
-            warnings.simplefilter("ignore")
-            Acsr = torch.sparse_csr_tensor(torch.as_tensor(A.row_ptr).cuda(), torch.as_tensor(A.col).cuda(),
-                                           torch.as_tensor(A.val, dtype=torch.float64).cuda(), size=(A.n, A.n))
+    if not acc32:
+        try:
+            import warnings
+            with warnings.catch_warnings():
+                warnings.simplefilter("ignore")
+                Acsr = torch.sparse_csr_tensor(torch.as_tensor(A.row_ptr).cuda(), torch.as_tensor(A.col).cuda(),
+                                               torch.as_tensor(A.val, dtype=torch.float64).cuda(), size=(A.n, A.n))
 
-            def csr_powers():
-                v = Xd
-                for _ in range(p):
-                    v = Acsr @ v
-                return v
+                def csr_powers():
+                    v = Xd
+                    for _ in range(p):
+                        v = Acsr @ v
+                    return v
 
-            ms_csr = timed(csr_powers, max(3, args.steps // 4), 2)
-            v = csr_powers()
-            rel = float(torch.linalg.norm(v[:, 0] - Y2[p, :, 0].index_select(0, L.iperm.long())) /
-                        torch.linalg.norm(v[:, 0]))
-            csr = {"ms": ms_csr, "gflops": flops / (ms_csr * 1e-3) / 1e9, "speedup": ms_csr / ms,
-                   "rel_diff_power_p": rel, "library": "cuSPARSE (torch sparse CSR matmul)"}
-            del Acsr, v
-    except Exception as e:  # the comparator is optional; the headline does not depend on it
-        csr = {"unavailable": f"{type(e).__name__}: {e}"}
+                ms_csr = timed(csr_powers, max(3, args.steps // 4), 2)
+                v = csr_powers()
+                rel = float(torch.linalg.norm(v[:, 0] - Y2[p, :, 0].index_select(0, L.iperm.long())) /
+                            torch.linalg.norm(v[:, 0]))
+                csr = {"ms": ms_csr, "gflops": flops / (ms_csr * 1e-3) / 1e9, "speedup": ms_csr / ms,
+                       "rel_diff_power_p": rel, "library": "cuSPARSE (torch sparse CSR matmul)"}
+                del Acsr, v
+        except Exception as e:  # the comparator is optional; the headline does not depend on it
+            csr = {"unavailable": f"{type(e).__name__}: {e}"}
 
     # ---- end to end through the C ABI with host buffers (pinned), plan-order vectors
     e2e = None
@@ -846,47 +939,88 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(A, X, p)
 
-    peak_alu = NUM_SMS * DFMA_LANES_PER_CLK_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12  # TFLOP/s
-    achieved = flops / (ms * 1e-3) / 1e12
-    best_plain = min(ms_plain_nat, ms_plain_bfs, ms_sweep)
     clocks = clk.summary()
+    mhz = clocks["sm_mhz"] or SM_MAX_MHZ_FALLBACK
+    achieved = flops / (ms * 1e-3) / 1e12
+    best_name = min(comps, key=comps.get)
+    best_plain = comps[best_name]
+    # memory roofs of one apply (Sec. 6 roofline reasoning on this device's measured bandwidths):
+    # A once, X once and every power written once from / to HBM; p passes over A and the two
+    # vectors of a power from L2.  With binary32 accumulation a power also writes its binary32
+    # copy (4 B a row) and reads the previous one.
+    out_row = 8.0 + (4.0 if acc32 else 0.0)
+    hbm_bytes = a_bytes + 8.0 * A.n + p * out_row * A.n
+    l2_bytes = p * (a_bytes + (4.0 if acc32 else 8.0) * A.n + out_row * A.n)
+    bw_h, bw_l2 = roofs["hbm_load_gbs"] * 1e9, roofs["l2_load_gbs"] * 1e9
+    t_hbm, t_l2 = hbm_bytes / bw_h, l2_bytes / bw_l2
+    roof_blocked_ms = max(t_hbm, t_l2) * 1e3
+    plain_bytes = p * (a_bytes + (4.0 if acc32 else 8.0) * A.n + out_row * A.n)
+    peak_nominal = roofs["sms"] * DFMA_LANES_PER_CLK_PER_SM * 2 * mhz * 1e6 / 1e12  # TFLOP/s
+    if not acc32:
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak_nominal, "unit": "TFLOP/s",
+                    "frac": achieved / peak_nominal, "traffic": measured_traffic(args.side),
+                    "peak_note": f"{roofs['sms']} SMs x {DFMA_LANES_PER_CLK_PER_SM} FP64 FMA lanes/clk x 2 flop x "
+                                 f"{mhz:.0f} MHz (median SM clock sampled during the timed region)",
+                    "measured_fp64_peak": roofs["fp64_fma_tflops_measured"],
+                    "frac_of_measured_fp64_peak": achieved / roofs["fp64_fma_tflops_measured"],
+                    "measured_fp64_note": "FP64 FMA rate of dependent chains over all SMs (mpk_probe_dfma), this "
+                                          "process; the pipe sustains ~84% of the unit-count rate"}
+    else:
+        achieved_gbs = hbm_bytes / (ms * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": roofs["hbm_load_gbs"], "unit": "GB/s",
+                    "frac": achieved_gbs / roofs["hbm_load_gbs"], "traffic": None,
+                    "peak_note": "load bandwidth from HBM measured in this process (mpk_probe_load, 2 GiB)",
+                    "achieved_note": "algorithmic HBM bytes of one apply (A once, X once, p binary64 powers and "
+                                     "their binary32 copies written) / kernel time"}
+    roofline.update({
+        "kernel": "k_mpk (persistent level-blocked kernel), one launch per step", "kernel_ms": ms,
+        "algorithmic": "2 flop per stored entry per power: 2*nnz*p per launch",
+        "l2_blocked_roof_ms": roof_blocked_ms, "frac_of_l2_blocked_roof": roof_blocked_ms / ms,
+        "l2_blocked_roof": f"max((A_B + (p+1) V) / BW_HBM, p (A_B + 2V) / BW_L2) = max({t_hbm * 1e3:.3f}, "
+                           f"{t_l2 * 1e3:.3f}) ms with BW_HBM {roofs['hbm_load_gbs']:.0f} GB/s, BW_L2 "
+                           f"{roofs['l2_load_gbs']:.0f} GB/s measured in this process",
+        "plain_hbm_roof_ms": plain_bytes / bw_h * 1e3,
+        "effective_bandwidth_gbs": p * a_bytes / (ms * 1e-3) / 1e9,
+        "effective_bandwidth_note": "p x matrix bytes / kernel time",
+        "algorithmic_hbm_bytes": hbm_bytes, "algorithmic_l2_bytes": l2_bytes,
+        "l2_hit_rate_profile": l2_hit_rate_from_profile(),
+        "device": roofs})
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "Gflop/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"3-D 7-point Laplacian {args.side}^3 lexicographic, FP64 CSR, x~U[-1,1), "
-                                   f"p={p}, nrhs=1, level-blocked apply with vectors in BFS order"
-                                   + ("" if args.values == "f64" else f", values stored as {args.values}"),
-                       "values": args.values,
+            "vs_baseline": None, "dtype": "f32acc" if acc32 else "f64", "data": "synthetic",
+            "config": {"workload": f"3-D 7-point Laplacian {args.side}^3 lexicographic, x~U[-1,1), p={p}, nrhs=1, "
+                                   f"level-blocked apply with vectors in BFS order, values {args.values}, "
+                                   + ("binary32 row sums (binary64 vectors)" if acc32 else "binary64 arithmetic"),
+                       "values": args.values, "accum": args.accum,
                        "n": A.n, "nnz": A.nnz, "p": p, "nrhs": 1, "parallelism": f"replicas x{world}",
-                       "l2": f"no flush: inputs exceed L2 (matrix {a_bytes / 1e9:.2f} GB, L2 129 MB)",
+                       "l2": f"no flush: inputs exceed L2 (matrix {a_bytes / 1e9:.2f} GB, L2 "
+                             f"{roofs['l2_bytes'] / 1e6:.0f} MB)",
                        "levels": desc["num_levels"], "groups": desc["num_groups"], "chunks": desc["num_chunks"],
+                       "shape": desc["shape"], "chunk_rows": desc["chunk_rows"],
                        "cache_bytes": desc["cache_bytes"], "window": desc["window"]},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_alu, "unit": "TFLOP/s",
-                         "frac": achieved / peak_alu, "traffic": measured_traffic(args.side),
-                         "kernel": "k_mpk<1,0> (persistent level-blocked kernel), one launch per step",
-                         "kernel_ms": ms,
-                         "peak_note": "152 SMs x 2 FP64 FMA lanes/clk x 2 flop x 2070 MHz (lane rate measured)",
-                         "algorithmic": "2 flop per stored entry per power: 2*nnz*p per launch"},
+            "roofline": roofline,
             "original_order": {"ms_per_step": ms_orig, "gflops": flops / (ms_orig * 1e-3) / 1e9,
                                "note": "gather X, level-blocked kernel, tiled permuted write of Y[1..p]",
                                "bit_identical_to_plan_order": orig_identical},
-            "comparator": {"plain_spmv_natural_gflops": flops / (ms_plain_nat * 1e-3) / 1e9,
-                           "plain_spmv_bfs_gflops": flops / (ms_plain_bfs * 1e-3) / 1e9,
-                           "unblocked_sweep_gflops": flops / (ms_sweep * 1e-3) / 1e9,
+            "comparator": {**{k + "_gflops": flops / (v * 1e-3) / 1e9 for k, v in comps.items()},
+                           **{k + "_ms": v for k, v in comps.items()},
+                           "best_plain": best_name,
                            "speedup_vs_best_plain": best_plain / ms,
                            "speedup_original_order_vs_best_plain": best_plain / ms_orig,
-                           "plain_hbm_gbs": p * (a_bytes + 2 * v_bytes) / (best_plain * 1e-3) / 1e9,
+                           "plain_hbm_gbs": plain_bytes / (best_plain * 1e-3) / 1e9,
                            "bit_identical_to_plain": identical,
-                           "plain_spmv_note": "plain_* and unblocked_sweep use this library's sliced (SELL-32) copy; "
-                                              "the sweep is the plan's unblocked engine (one launch per power, "
-                                              "the level-blocked kernel's row body); best_plain is the fastest",
+                           "plain_spmv_note": "plain p x SpMV: p separate launches over this library's sliced "
+                                              "(SELL-32) copy (the row-range SpMV, or the plan's unblocked sweep "
+                                              "engine, whose row body is the level-blocked kernel's); best_plain "
+                                              "is the fastest" + ("; binary32 accumulation in every comparator"
+                                                                  if acc32 else ""),
                            "vendor_csr": csr},
             "preprocess": {"levels_ms": t_levels * 1e3, "plan_ms": t_plan * 1e3,
                            "spmv_equivalents": (t_levels + t_plan) * 1e3 / (best_plain / p)},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-            "gpu_launches": args.steps,
+            "gpu_launches": args.steps * (2 if acc32 else 1),
         }
         print(json.dumps(line), flush=True)
     if dist:

@@ -34,7 +34,9 @@ def build(force: bool = False) -> str:
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-fno-fast-math",
                "-o", tmp, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        # the row-parallel timing leg uses OpenMP where the compiler has it (same arithmetic either way)
+        if subprocess.run(cmd[:1] + ["-fopenmp"] + cmd[1:], capture_output=True).returncode != 0:
+            subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -58,7 +60,10 @@ def _L():
             lib.orc_mpk_acc32.argtypes = [i32, _i32p, _i32p, _f64p, i32, _f64p, i32, _f64p]
             lib.orc_cheb_acc32.argtypes = [i32, _i32p, _i32p, _f64p, i32, _f64p, i32, _f64p, C.c_void_p,
                                            f64, f64, _f64p]
-            for f in ("orc_mpk", "orc_mpk_longdouble", "orc_levels", "orc_permute", "orc_groups",
+            lib.orc_mpk_omp.argtypes = [i32, _i32p, _i32p, _f64p, i32, _f64p, i32, _f64p, C.POINTER(i32)]
+            lib.orc_load_sum.argtypes = [_f64p, i64, i32]
+            lib.orc_load_sum.restype = f64
+            for f in ("orc_mpk", "orc_mpk_omp", "orc_mpk_longdouble", "orc_levels", "orc_permute", "orc_groups",
                       "orc_lp_labels", "orc_lb_mpk", "orc_cheb", "orc_bessel_j", "orc_mpk_acc32",
                       "orc_cheb_acc32"):
                 getattr(lib, f).restype = C.c_int
@@ -91,6 +96,28 @@ def mpk(A, X, p: int) -> np.ndarray:
     Y = np.empty((p + 1, A.n, m), dtype=np.float64)
     _check(_L().orc_mpk(A.n, rp, ci, va, m, X, p, Y), "mpk")
     return Y
+
+
+def mpk_parallel(A, X, p: int):
+    """orc_mpk with each power's rows shared out over the host cores (same bits); returns
+    (Y, threads used)."""
+    rp, ci, va = _csr(A)
+    X = _block(X, A.n)
+    m = X.shape[1]
+    Y = np.empty((p + 1, A.n, m), dtype=np.float64)
+    t = C.c_int32(0)
+    _check(_L().orc_mpk_omp(A.n, rp, ci, va, m, X, p, Y, C.byref(t)), "mpk_omp")
+    return Y, t.value
+
+
+def load_bandwidth(nbytes: int = 1 << 30, reps: int = 5) -> float:
+    """Host load bandwidth in bytes/s: all threads sum a buffer of nbytes, `reps` times."""
+    import time
+    buf = np.ones(nbytes // 8, np.float64)
+    _L().orc_load_sum(buf, buf.size, 1)  # touch
+    t0 = time.perf_counter()
+    _L().orc_load_sum(buf, buf.size, reps)
+    return reps * buf.nbytes / (time.perf_counter() - t0)
 
 
 def mpk_acc32(A, X, p: int) -> np.ndarray:

@@ -18,6 +18,9 @@
  */
 #include <math.h>
 #include <stdint.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdlib.h>
 #include <string.h>
 
@@ -54,6 +57,57 @@ int orc_mpk(int32_t n, const int32_t *rp, const int32_t *ci, const double *va, i
         for (int64_t i = 0; i < n; ++i) row_times_block(rp, ci, va, m, xin, i, yout + i * m);
     }
     return ORC_OK;
+}
+
+/*
+ * orc_mpk with the rows of each power shared out over the host's cores (OpenMP, when the
+ * oracle is built with it): the same row body, so the same bits as orc_mpk.  A timing leg of
+ * the CPU baseline only; the tests check it against orc_mpk.  *threads receives the number of
+ * threads that ran.
+ */
+int orc_mpk_omp(int32_t n, const int32_t *rp, const int32_t *ci, const double *va, int32_t m,
+                const double *X, int32_t p, double *Y, int32_t *threads)
+{
+    if (n < 0 || m < 1 || p < 0) return ORC_EINVAL;
+    const int64_t nm = (int64_t)n * m;
+    memcpy(Y, X, sizeof(double) * (size_t)nm);
+    int32_t used = 1;
+    for (int32_t k = 1; k <= p; ++k) {
+        const double *xin = Y + (int64_t)(k - 1) * nm;
+        double *yout = Y + (int64_t)k * nm;
+#ifdef _OPENMP
+#pragma omp parallel
+        {
+#pragma omp single
+            used = omp_get_num_threads();
+#pragma omp for schedule(static)
+            for (int64_t i = 0; i < n; ++i) row_times_block(rp, ci, va, m, xin, i, yout + i * m);
+        }
+#else
+        for (int64_t i = 0; i < n; ++i) row_times_block(rp, ci, va, m, xin, i, yout + i * m);
+#endif
+    }
+    *threads = used;
+    return ORC_OK;
+}
+
+/*
+ * Host load bandwidth, for the context line of the CPU baseline (the paper's roofline of
+ * Sec. 6 takes the saturated load bandwidth b_s): `reps` sums over buf[0..n) by all
+ * threads; returns the sum so that the loads cannot be dropped.
+ */
+double orc_load_sum(const double *buf, int64_t n, int32_t reps)
+{
+    double total = 0.0;
+    for (int32_t r = 0; r < reps; ++r) {
+        double s = 0.0;
+#ifdef _OPENMP
+#pragma omp parallel for reduction(+ : s) schedule(static)
+#endif
+        for (int64_t i = 0; i < n; ++i) s += buf[i];
+        total += s;
+    }
+    return total;
 }
 
 /*

@@ -436,3 +436,13 @@ def test_cheb_acc32_keeps_the_recurrence_in_binary64():
     x = 1 + 2.0 ** -30
     got = oracle.cheb_acc32(A, np.array([x]), 2, np.array([0.0, 0.0, 1.0]), scale=1.0, shift=0.0)
     assert got[0, 0] == 8 - x
+
+
+def test_parallel_oracle_leg_is_the_same_computation():
+    # the row-parallel timing leg of the CPU baseline runs the serial row body on several
+    # threads: the same bits as the serial oracle
+    A = gen.banded_random(3000, stream=135)
+    X = gen.vector(A.n, 2, stream=136)
+    Y, threads = oracle.mpk_parallel(A, X, 5)
+    assert threads >= 1
+    assert np.array_equal(Y.view(np.uint64), oracle.mpk(A, X, 5).view(np.uint64))
