@@ -79,6 +79,8 @@ def parse():
     ap.add_argument("--serve-rate2", type=float, default=10.0, help="second, sustainable arrival rate")
     ap.add_argument("--batch-count", type=int, default=64, help="matrices of the batch workload")
     ap.add_argument("--batch-nmax", type=float, default=2e6, help="largest matrix size of the batch workload")
+    ap.add_argument("--split", action="store_true",
+                    help="split bulky levels into budget-sized groups (plan option split_levels, wave-ordered units)")
     ap.add_argument("--accum", default="f64", choices=["f64", "f32"],
                     help="row-sum arithmetic: binary64, or binary32 (values then f32 or bf16; bf16 if f64 is given)")
     ap.add_argument("--values", default="f64", choices=["f64", "f32", "bf16"],
@@ -361,7 +363,7 @@ def main_cheb(args):
     L = mpk.build_levels(dA, 0)
     t_levels = time.perf_counter() - t0
     t0 = time.perf_counter()
-    P = mpk.plan(dA, L, p_max=p, nrhs=m, order=mpk.ORDER_PLAN)
+    P = mpk.plan(dA, L, p_max=p, nrhs=m, order=mpk.ORDER_PLAN, split_levels=args.split)
     t_plan = time.perf_counter() - t0
     perm = L.perm.long()
     psi_p = torch.from_numpy(psi).cuda()[perm].contiguous()   # state in the plan's numbering
@@ -831,9 +833,10 @@ def main():
     t0 = time.perf_counter()
     cb = args.cache_mb << 20
     # headline: one kernel launch per apply, vectors in the plan's (BFS) numbering
-    P = mpk.plan(dA, L, p_max=p, nrhs=1, order=mpk.ORDER_PLAN, cache_bytes=cb, accum=accum)
+    P = mpk.plan(dA, L, p_max=p, nrhs=1, order=mpk.ORDER_PLAN, cache_bytes=cb, accum=accum, split_levels=args.split)
     t_plan = time.perf_counter() - t0
-    Po = mpk.plan(dA, L, p_max=p, nrhs=1, order=mpk.ORDER_ORIGINAL, cache_bytes=cb, accum=accum)
+    Po = mpk.plan(dA, L, p_max=p, nrhs=1, order=mpk.ORDER_ORIGINAL, cache_bytes=cb, accum=accum,
+                  split_levels=args.split)
     desc = P.describe()
     Y = torch.empty((p + 1, A.n, 1), dtype=torch.float64, device="cuda")
     Y2 = torch.empty_like(Y)
@@ -998,7 +1001,7 @@ def main():
                        "l2": f"no flush: inputs exceed L2 (matrix {a_bytes / 1e9:.2f} GB, L2 "
                              f"{roofs['l2_bytes'] / 1e6:.0f} MB)",
                        "levels": desc["num_levels"], "groups": desc["num_groups"], "chunks": desc["num_chunks"],
-                       "shape": desc["shape"], "chunk_rows": desc["chunk_rows"],
+                       "shape": desc["shape"], "chunk_rows": desc["chunk_rows"], "split_levels": args.split,
                        "cache_bytes": desc["cache_bytes"], "window": desc["window"]},
             "roofline": roofline,
             "original_order": {"ms_per_step": ms_orig, "gflops": flops / (ms_orig * 1e-3) / 1e9,

@@ -161,6 +161,19 @@ typedef struct {
                                plan keeps a ring of two binary32 copies of the current input
                                (8 * n * nrhs bytes).  mpk_spmv_powers refuses such a plan (its
                                comparator is a plan of engine MPK_ENGINE_SWEEP)               */
+    int32_t split_levels;   /* 1: bulky levels are split (Sec. 6's recursion stage s_m, read as
+                               breaking a level too large for the budget into pieces): levels
+                               group as above while they fit; a level whose bytes exceed
+                               floor(cache_bytes / window) closes the current group and is cut
+                               into pieces of consecutive rows, each taking rows while its bytes
+                               stay within that budget (at least one row), each a group; the next
+                               level starts a new group.  A row costs (val_bytes + 4) * nnz(row) +
+                               4 + 16 * nrhs bytes.  The work units then run in waves computed
+                               from the exact chunk dependencies (w = 3 + group for power 1, then
+                               2 more than the largest wave the unit reads), not on the lines
+                               g + 3k, so every dependency still runs first.  Needs levels and the
+                               staged or sweep engine, without level caps or batching
+                               (MPK_ERR_INVALID otherwise).  0 = whole levels (default).      */
 } mpk_plan_opts;
 
 /* Engines of the level-blocked kernel (same results bit for bit, same Lp-diagram order):
@@ -204,6 +217,8 @@ typedef struct {
     int32_t engine;               /* MPK_ENGINE_STAGED or MPK_ENGINE_WARP                 */
     int32_t chunk_rows;           /* rows per chunk limit in effect                      */
     int32_t accum;                /* MPK_F64 or MPK_F32 (opts.accum)                     */
+    int32_t split_levels;         /* opts.split_levels; group_level_ptr then holds the level
+                                     of each group's first row                             */
 } mpk_plan_desc;
 
 mpk_status mpk_plan_describe(const mpk_plan_t *P, mpk_plan_desc *out);

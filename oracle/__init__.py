@@ -60,10 +60,12 @@ def _L():
             lib.orc_mpk_acc32.argtypes = [i32, _i32p, _i32p, _f64p, i32, _f64p, i32, _f64p]
             lib.orc_cheb_acc32.argtypes = [i32, _i32p, _i32p, _f64p, i32, _f64p, i32, _f64p, C.c_void_p,
                                            f64, f64, _f64p]
+            lib.orc_groups_split.argtypes = [i32, _i32p, _i32p, i32, i32, i64, _i32p, C.POINTER(i32)]
+            lib.orc_lb_mpk_waves.argtypes = [i32, _i32p, _i32p, _f64p, i32, _f64p, i32, i32, _i32p, _f64p]
             lib.orc_mpk_omp.argtypes = [i32, _i32p, _i32p, _f64p, i32, _f64p, i32, _f64p, C.POINTER(i32)]
             lib.orc_load_sum.argtypes = [_f64p, i64, i32]
             lib.orc_load_sum.restype = f64
-            for f in ("orc_mpk", "orc_mpk_omp", "orc_mpk_longdouble", "orc_levels", "orc_permute", "orc_groups",
+            for f in ("orc_groups_split", "orc_lb_mpk_waves", "orc_mpk", "orc_mpk_omp", "orc_mpk_longdouble", "orc_levels", "orc_permute", "orc_groups",
                       "orc_lp_labels", "orc_lb_mpk", "orc_cheb", "orc_bessel_j", "orc_mpk_acc32",
                       "orc_cheb_acc32"):
                 getattr(lib, f).restype = C.c_int
@@ -173,6 +175,30 @@ def groups(level_ptr, perm_row_ptr, budget: int, val_bytes: int = 8, m: int = 1)
     _check(_L().orc_groups(L, level_ptr, np.ascontiguousarray(perm_row_ptr, np.int32), val_bytes, m,
                            int(budget), gp, C.byref(G)), "groups")
     return gp[: G.value + 1].copy()
+
+
+def groups_split(level_ptr, perm_row_ptr, budget: int, val_bytes: int = 8, m: int = 1) -> np.ndarray:
+    """First row of every group (and n) with bulky levels cut into budget-sized pieces."""
+    level_ptr = np.ascontiguousarray(level_ptr, np.int32)
+    prp = np.ascontiguousarray(perm_row_ptr, np.int32)
+    L = level_ptr.size - 1
+    gr = np.empty(prp.size, np.int32)
+    G = C.c_int32(0)
+    _check(_L().orc_groups_split(L, level_ptr, prp, val_bytes, m, int(budget), gr, C.byref(G)), "groups_split")
+    return gr[: G.value + 1].copy()
+
+
+def lb_mpk_waves(prp, pci, pva, X, p: int, group_rows) -> np.ndarray:
+    """Serial level-blocked MPK over arbitrary groups, cells in exact-dependency wave order."""
+    prp = np.ascontiguousarray(prp, np.int32)
+    n = prp.size - 1
+    X = _block(X, n)
+    m = X.shape[1]
+    gr = np.ascontiguousarray(group_rows, np.int32)
+    Y = np.full((p + 1, n, m), np.nan)
+    _check(_L().orc_lb_mpk_waves(n, prp, np.ascontiguousarray(pci, np.int32), np.ascontiguousarray(pva, np.float64),
+                                 m, X, p, gr.size - 1, gr, Y), "lb_mpk_waves")
+    return Y
 
 
 def lp_labels(L: int, pm: int, skew: int = 1) -> np.ndarray:

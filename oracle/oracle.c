@@ -306,6 +306,105 @@ int orc_groups(int32_t nlevels, const int32_t *level_ptr, const int32_t *rp, int
 }
 
 /*
+ * Groups with bulky levels split (the recursion stage s_m of Sec. 6, read as: a level too large
+ * for the budget is broken into pieces): levels are grouped as in orc_groups while they fit
+ * the budget; a level whose bytes exceed it closes the current group and is cut into pieces
+ * of consecutive rows, each piece taking rows while its bytes stay <= budget (at least one
+ * row), each piece a group of its own; the next level starts a new group.  A row costs
+ * (val_bytes + 4) * nnz(row) + 4 + 16 * m bytes, so a level costs what orc_groups charges.
+ * group_rows (room for n+1) receives the first row of every group and n; *ngroups the count.
+ */
+int orc_groups_split(int32_t nlevels, const int32_t *level_ptr, const int32_t *rp, int32_t val_bytes, int32_t m,
+                     int64_t budget, int32_t *group_rows, int32_t *ngroups)
+{
+    if (nlevels < 0 || val_bytes <= 0 || m < 1) return ORC_EINVAL;
+    int32_t G = 0;
+    int64_t cur = 0;
+    group_rows[0] = 0;
+    for (int32_t l = 0; l < nlevels; ++l) {
+        const int64_t rows = level_ptr[l + 1] - level_ptr[l];
+        const int64_t nz = (int64_t)rp[level_ptr[l + 1]] - rp[level_ptr[l]];
+        const int64_t b = ((int64_t)val_bytes + 4) * nz + 4 * rows + 16 * (int64_t)m * rows;
+        if (b > budget) {
+            if (l > 0 && group_rows[G] != level_ptr[l]) group_rows[++G] = level_ptr[l];
+            int64_t piece = 0;
+            for (int32_t r = level_ptr[l]; r < level_ptr[l + 1]; ++r) {
+                const int64_t rb = ((int64_t)val_bytes + 4) * (rp[r + 1] - rp[r]) + 4 + 16 * (int64_t)m;
+                if (r > level_ptr[l] && piece + rb > budget) {
+                    group_rows[++G] = r;
+                    piece = 0;
+                }
+                piece += rb;
+            }
+            if (l + 1 < nlevels) group_rows[++G] = level_ptr[l + 1];
+            cur = 0;
+            continue;
+        }
+        if (l > 0 && group_rows[G] == level_ptr[l]) {  /* a new group starts here (after a bulky level) */
+            cur = b;
+        } else if (l > 0 && cur + b <= budget) {
+            cur += b;
+        } else {
+            if (l > 0) group_rows[++G] = level_ptr[l];
+            cur = b;
+        }
+    }
+    if (nlevels > 0) group_rows[++G] = level_ptr[nlevels];
+    *ngroups = G;
+    return ORC_OK;
+}
+
+/*
+ * Serial level-blocked MPK over groups that need not follow the +-1 rule of whole levels
+ * (split levels): cell (g, k) runs in the order of its wave w(g, k), where w(g, 1) = 3 + g
+ * and w(g, k) = max{ w(g', k-1) : group g reads a row of group g' } + 2; cells are visited by
+ * increasing (w, k, g).  Every cell's inputs lie on smaller waves, so the result equals
+ * back-to-back SpMV bit for bit (rows keep their summation order); Y[1..p] are only written,
+ * so NaN-filled outputs expose any early read.  Arguments as orc_lb_mpk (skew replaced by the
+ * wave rule).
+ */
+int orc_lb_mpk_waves(int32_t n, const int32_t *rp, const int32_t *ci, const double *va, int32_t m,
+                     const double *X, int32_t p, int32_t G, const int32_t *group_rows, double *Y)
+{
+    if (n < 0 || m < 1 || p < 0 || G < 0) return ORC_EINVAL;
+    const int64_t nm = (int64_t)n * m;
+    memcpy(Y, X, sizeof(double) * (size_t)nm);
+    if (p == 0 || G == 0) return ORC_OK;
+    int32_t *group_of = malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    int32_t *lo = malloc(sizeof(int32_t) * (size_t)G), *hi = malloc(sizeof(int32_t) * (size_t)G);
+    int64_t *w = malloc(sizeof(int64_t) * (size_t)G * (size_t)p);
+    if (!group_of || !lo || !hi || !w) { free(group_of); free(lo); free(hi); free(w); return ORC_ENOMEM; }
+    for (int32_t g = 0; g < G; ++g)
+        for (int32_t r = group_rows[g]; r < group_rows[g + 1]; ++r) group_of[r] = g;
+    /* the groups each group reads form a contiguous hull here only as a bound; the wave takes the
+       maximum over the groups actually read */
+    for (int32_t g = 0; g < G; ++g) w[g] = 3 + g;
+    for (int32_t k = 2; k <= p; ++k)
+        for (int32_t g = 0; g < G; ++g) {
+            int64_t mx = 0;
+            for (int32_t r = group_rows[g]; r < group_rows[g + 1]; ++r)
+                for (int32_t e = rp[r]; e < rp[r + 1]; ++e) {
+                    const int64_t v = w[(int64_t)(k - 2) * G + group_of[ci[e]]];
+                    if (v > mx) mx = v;
+                }
+            w[(int64_t)(k - 1) * G + g] = mx + 2;
+        }
+    int64_t wmax = 0;
+    for (int64_t t = 0; t < (int64_t)G * p; ++t) if (w[t] > wmax) wmax = w[t];
+    for (int64_t wave = 0; wave <= wmax; ++wave)
+        for (int32_t k = 1; k <= p; ++k)
+            for (int32_t g = 0; g < G; ++g) {
+                if (w[(int64_t)(k - 1) * G + g] != wave) continue;
+                const double *xin = Y + (int64_t)(k - 1) * nm;
+                double *yout = Y + (int64_t)k * nm;
+                for (int64_t i = group_rows[g]; i < group_rows[g + 1]; ++i)
+                    row_times_block(rp, ci, va, m, xin, i, yout + i * m);
+            }
+    free(group_of); free(lo); free(hi); free(w);
+    return ORC_OK;
+}
+
+/*
  * Execution order of the Lp diagram (Sec. 3, Fig. 2): cells (i, p) with level i in
  * 0..L-1 and power p in 1..pm are visited line by line, i + skew*p increasing, and inside
  * one line from bottom-right to top-left, i.e. p ascending.  skew = 1 gives the paper's

@@ -58,7 +58,8 @@ class _Opts(C.Structure):
     _fields_ = [("p_max", C.c_int32), ("nrhs", C.c_int32), ("cache_bytes", C.c_int64), ("order", C.c_int32),
                 ("chunk_rows", C.c_int32), ("wait_limit_ns", C.c_int64), ("mem_budget", C.c_int64),
                 ("trace", C.c_int32), ("level_capped", C.c_int32), ("engine", C.c_int32),
-                ("shape", C.c_int32), ("shuffle_seed", C.c_int64), ("accum", C.c_int32)]
+                ("shape", C.c_int32), ("shuffle_seed", C.c_int64), ("accum", C.c_int32),
+                ("split_levels", C.c_int32)]
 
 
 class _Desc(C.Structure):
@@ -69,7 +70,8 @@ class _Desc(C.Structure):
                 ("device_bytes", C.c_int64), ("padded_entries", C.c_int64),
                 ("group_level_ptr_dev", C.c_void_p), ("group_row_ptr_dev", C.c_void_p),
                 ("chunk_row_ptr_dev", C.c_void_p), ("perm_dev", C.c_void_p), ("shape", C.c_int32),
-                ("engine", C.c_int32), ("chunk_rows", C.c_int32), ("accum", C.c_int32)]
+                ("engine", C.c_int32), ("chunk_rows", C.c_int32), ("accum", C.c_int32),
+                ("split_levels", C.c_int32)]
 
 
 _lib = None
@@ -476,7 +478,7 @@ class Plan:
 def plan(A: CsrMatrix, levels: Levels | None = None, p_max: int = 8, nrhs: int = 1, cache_bytes: int = 0,
          order: int = ORDER_ORIGINAL, chunk_rows: int = 0, wait_limit_ns: int = 0, mem_budget: int = 0,
          trace: bool = False, level_capped: bool = False, engine: int = ENGINE_STAGED, shape: int = 0,
-         shuffle_seed: int = 0, accum: int = MPK_F64, stream=None) -> Plan:
+         shuffle_seed: int = 0, accum: int = MPK_F64, split_levels: bool = False, stream=None) -> Plan:
     lib = load()
     o = _Opts()
     lib.mpk_plan_opts_default(C.byref(o))
@@ -488,6 +490,7 @@ def plan(A: CsrMatrix, levels: Levels | None = None, p_max: int = 8, nrhs: int =
     o.shape = int(shape)
     o.shuffle_seed = int(shuffle_seed)
     o.accum = int(accum)
+    o.split_levels = 1 if split_levels else 0
     h = C.c_void_p()
     csr = A._c()
     _check(lib.mpk_plan(C.byref(csr), levels._h if levels is not None else None, C.byref(o), _stream(stream),

@@ -111,6 +111,7 @@ extern "C" mpk_status mpk_plan_describe(const mpk_plan_t *P, mpk_plan_desc *d) {
     d->engine = p.engine;
     d->chunk_rows = p.chunk_rows;
     d->accum = p.accum;
+    d->split_levels = p.split_levels ? 1 : 0;
     return MPK_OK;
 }
 

@@ -309,6 +309,7 @@ struct Plan {
     std::vector<int32_t> inst_row, inst_p;
     std::vector<int32_t> h_chunk_row;  // chunk row offsets on the host (num_chunks + 1)
     bool level_capped = false;        // rows of level L take powers up to min(L, p) (DLB local phase)
+    bool split_levels = false;        // bulky levels cut into budget-sized groups, units in wave order
     int32_t level0_rows = 0;          // level-capped plans: rows of level 0 (no unit copies their x)
     // warp-ticketed engine (plans built with engine = MPK_ENGINE_WARP)
     int32_t engine = MPK_ENGINE_STAGED;

@@ -368,6 +368,10 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         P->level_capped = o->level_capped != 0;
         if (P->level_capped && (!L || batch || o->order != MPK_ORDER_PLAN))
             fail(MPK_ERR_INVALID, "level_capped needs levels, plan order and no batch");
+        P->split_levels = o->split_levels != 0;
+        if (P->split_levels && (!L || batch || P->level_capped || o->engine == MPK_ENGINE_WARP))
+            fail(MPK_ERR_INVALID, "split_levels needs levels and the staged or sweep engine, without level caps or "
+                                  "batching");
         if (batch) {
             if (!L || !inst_p || inst_row->size() != inst_p->size() + 1 || inst_row->back() != n)
                 fail(MPK_ERR_INVALID, "inconsistent batch description");
@@ -441,6 +445,60 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
             g_level.push_back(NL);
             if (P->level_capped && NL > 0) P->level0_rows = lp[1];
             for (int32_t gl : g_level) g_row.push_back(lp[gl]);
+            if (P->split_levels) {
+                // Bulky levels split (the recursion stage of Sec. 6, read as breaking a level too
+                // large for the budget into pieces): levels group as above while they fit; a level
+                // over the budget closes the current group and is cut into pieces of consecutive
+                // rows, each taking rows while its bytes stay <= budget (at least one row), each a
+                // group; the next level starts a new group.  A row costs (val_bytes + 4) nnz + 4 +
+                // 16 m bytes.  group_level_ptr then holds the level of each group's first row.
+                std::vector<int32_t> rl((size_t)n), prow((size_t)n + 1);
+                MPK_CUDA(cudaMemcpyAsync(rl.data(), P->rowlen, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost, s));
+                MPK_CUDA(cudaStreamSynchronize(s));
+                g_row.assign(1, 0);
+                g_level.assign(1, 0);
+                int64_t cur2 = 0;
+                for (int32_t l = 0; l < NL; ++l) {
+                    const int64_t rows = lp[l + 1] - lp[l];
+                    const int64_t nz = (int64_t)h_nz[l + 1] - h_nz[l];
+                    const int64_t b = (vb + 4) * nz + 4 * rows + 16 * (int64_t)m * rows;
+                    if (b > B) {
+                        if (l > 0 && g_row.back() != lp[l]) {
+                            g_row.push_back(lp[l]);
+                            g_level.push_back(l);
+                        }
+                        int64_t piece = 0;
+                        for (int32_t r = lp[l]; r < lp[l + 1]; ++r) {
+                            const int64_t rb = (vb + 4) * rl[r] + 4 + 16 * (int64_t)m;
+                            if (r > lp[l] && piece + rb > B) {
+                                g_row.push_back(r);
+                                g_level.push_back(l);
+                                piece = 0;
+                            }
+                            piece += rb;
+                        }
+                        if (l + 1 < NL) {
+                            g_row.push_back(lp[l + 1]);
+                            g_level.push_back(l + 1);
+                        }
+                        cur2 = 0;
+                        continue;
+                    }
+                    if (l > 0 && g_row.back() == lp[l]) {
+                        cur2 = b;
+                    } else if (l > 0 && cur2 + b <= B) {
+                        cur2 += b;
+                    } else {
+                        if (l > 0) {
+                            g_row.push_back(lp[l]);
+                            g_level.push_back(l);
+                        }
+                        cur2 = b;
+                    }
+                }
+                g_row.push_back(lp[NL]);
+                g_level.push_back(NL);
+            }
         } else {
             g_row = {0, 0};
         }
@@ -736,7 +794,68 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
             z = (z ^ (z >> 27)) * 0x94d049bb133111ebULL;
             return z ^ (z >> 31);
         };
-        for (int32_t p = 1; p <= pmax && !batch; ++p) {
+        // split plans: the groups of a split level need not read only their neighbours, so the
+        // units follow waves computed from the exact chunk dependencies: w(c, 1) = kSlotSkew + g(c),
+        // w(c, k) = max{ w(c', k-1) : c' in the dependency ranges of c } + 2, units by increasing
+        // (w, k, chunk).  Every dependency has a smaller wave, hence a smaller ticket: the
+        // schedule stays deadlock free.  (For unsplit levels this reproduces the lines g + 3k.)
+        std::vector<int64_t> wave;  // wave of unit (c, k) at (k - 1) * NC + c
+        if (P->split_levels && NC > 0) {
+            std::vector<int4> rr((size_t)2 * NC);
+            MPK_CUDA(cudaMemcpyAsync(rr.data(), P->dep_ranges, sizeof(int4) * rr.size(), cudaMemcpyDeviceToHost, s));
+            MPK_CUDA(cudaStreamSynchronize(s));
+            wave.assign((size_t)pmax * NC, 0);
+            for (int32_t g = 0; g < G; ++g)
+                for (int32_t c = g_chunk[g]; c < g_chunk[g + 1]; ++c) wave[c] = kSlotSkew + g;
+            int lg = 1;
+            while ((1 << lg) < NC) ++lg;
+            std::vector<int64_t> st((size_t)(lg + 1) * NC);  // sparse table of range maxima
+            for (int32_t k = 2; k <= pmax; ++k) {
+                const int64_t *prev = wave.data() + (size_t)(k - 2) * NC;
+                for (int32_t c = 0; c < NC; ++c) st[c] = prev[c];
+                for (int j = 1; j <= lg; ++j)
+                    for (int32_t c = 0; c + (1 << j) <= NC; ++c)
+                        st[(size_t)j * NC + c] =
+                            std::max(st[(size_t)(j - 1) * NC + c], st[(size_t)(j - 1) * NC + c + (1 << (j - 1))]);
+                auto range_max = [&](int32_t a, int32_t b) {  // inclusive, a <= b
+                    int j = 0;
+                    while ((2 << j) <= b - a + 1) ++j;
+                    return std::max(st[(size_t)j * NC + a], st[(size_t)j * NC + b - (1 << j) + 1]);
+                };
+                int64_t *cur = wave.data() + (size_t)(k - 1) * NC;
+                for (int32_t c = 0; c < NC; ++c) {
+                    const int32_t lo4[4] = {rr[2 * c].x, rr[2 * c].z, rr[2 * c + 1].x, rr[2 * c + 1].z};
+                    const int32_t hi4[4] = {rr[2 * c].y, rr[2 * c].w, rr[2 * c + 1].y, rr[2 * c + 1].w};
+                    int64_t mx = 0;
+                    for (int q = 0; q < 4; ++q)
+                        if (hi4[q] >= lo4[q]) mx = std::max(mx, range_max(lo4[q], hi4[q]));
+                    cur[c] = mx + 2;
+                }
+            }
+        }
+        for (int32_t p = 1; p <= pmax && !batch && P->split_levels; ++p) {
+            P->unit_off[p] = (int64_t)units.size();
+            std::vector<std::pair<int64_t, int32_t>> ord;  // (wave, unit)
+            ord.reserve((size_t)p * NC);
+            for (int32_t k = 1; k <= p; ++k)
+                for (int32_t c = 0; c < NC; ++c) ord.push_back({wave[(size_t)(k - 1) * NC + c], (c << 5) | k});
+            std::sort(ord.begin(), ord.end(), [](const std::pair<int64_t, int32_t> &x, const std::pair<int64_t, int32_t> &y) {
+                if (x.first != y.first) return x.first < y.first;
+                if ((x.second & 31) != (y.second & 31)) return (x.second & 31) < (y.second & 31);
+                return x.second < y.second;
+            });
+            for (size_t j = 0; j < ord.size();) {  // one wave at a time (shuffled on request)
+                size_t e = j;
+                while (e < ord.size() && ord[e].first == ord[j].first) ++e;
+                const size_t line0 = units.size();
+                for (size_t q = j; q < e; ++q) units.push_back(ord[q].second);
+                if (o->shuffle_seed != 0)
+                    for (size_t q = units.size() - 1; q > line0; --q)
+                        std::swap(units[q], units[line0 + next_rand() % (q - line0 + 1)]);
+                j = e;
+            }
+        }
+        for (int32_t p = 1; p <= pmax && !batch && !P->split_levels; ++p) {
             P->unit_off[p] = (int64_t)units.size();
             for (int32_t d = kSlotSkew; d <= G - 1 + kSlotSkew * p; ++d) {
                 const size_t line0 = units.size();

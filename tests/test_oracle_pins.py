@@ -446,3 +446,64 @@ def test_parallel_oracle_leg_is_the_same_computation():
     Y, threads = oracle.mpk_parallel(A, X, 5)
     assert threads >= 1
     assert np.array_equal(Y.view(np.uint64), oracle.mpk(A, X, 5).view(np.uint64))
+
+
+# ----------------------------------------------------------------------------- bulky levels split
+def _star(k=4):
+    # row 0 joined to rows 1..k, every row with a diagonal: levels {0}, {1..k}
+    r = list(range(k + 1)) + [0] * k + list(range(1, k + 1))
+    c = list(range(k + 1)) + list(range(1, k + 1)) + [0] * k
+    return gen.from_coo(k + 1, r, c, np.linspace(1.0, 2.0, len(r)))
+
+
+def test_groups_split_hand_computed():
+    # row bytes (8 + 4) nnz + 4 + 16: row 0 (5 entries) 80, rows 1..4 (2 entries) 44; levels 80 and 176
+    A = _star()
+    lo, pe, ip, lp = oracle.levels(A, 0)
+    prp, _, _ = oracle.permute(A, pe, ip)
+    assert oracle.groups_split(lp, prp, 100).tolist() == [0, 1, 3, 5]   # {0} | {1,2} 88 | {3,4} 88
+    assert oracle.groups_split(lp, prp, 200).tolist() == [0, 1, 5]      # 80 + 176 > 200, 176 fits
+    assert oracle.groups_split(lp, prp, 300).tolist() == [0, 5]         # both levels in one group
+    assert oracle.groups_split(lp, prp, 50).tolist() == [0, 1, 2, 3, 4, 5]  # single rows over budget
+
+
+@pytest.mark.parametrize("budget", [2000, 20000, 60000])
+def test_groups_split_invariants(budget):
+    A = gen.laplacian_3d(14, 11, 9)
+    lo, pe, ip, lp = oracle.levels(A, 0)
+    prp, _, _ = oracle.permute(A, pe, ip)
+    gr = oracle.groups_split(lp, prp, budget)
+    rb = 12 * np.diff(prp) + 4 + 16
+    assert gr[0] == 0 and gr[-1] == A.n and np.all(np.diff(gr) > 0)
+    lev = np.searchsorted(lp, np.arange(A.n), side="right") - 1
+    for g in range(gr.size - 1):
+        rows = np.arange(gr[g], gr[g + 1])
+        ls = np.unique(lev[rows])
+        lvl_bytes = [rb[lp[l]:lp[l + 1]].sum() for l in ls]
+        if any(b > budget for b in lvl_bytes):   # a piece of a bulky level: one level, within budget
+            assert ls.size == 1 and (rb[rows].sum() <= budget or rows.size == 1)
+        else:                                     # whole levels, within budget
+            assert gr[g] in lp and gr[g + 1] in lp
+            assert rb[rows].sum() <= budget
+    # without bulky levels the rule is orc_groups'
+    big = 10 ** 9
+    assert np.array_equal(oracle.groups_split(lp, prp, big), lp[oracle.groups(lp, prp, big)])
+
+
+@pytest.mark.parametrize("budget", [50, 100, 2000, 20000])
+def test_wave_order_is_exact_where_lines_read_early(budget):
+    # split groups break the +-1 rule of levels; the wave order still gives back-to-back SpMV bit
+    # for bit, while the fixed line order g + 3k reads unfinished (NaN) inputs on the star
+    for A in (_star(6), gen.laplacian_3d(9, 8, 7), gen.banded_random(400, stream=140)):
+        lo, pe, ip, lp = oracle.levels(A, 0)
+        prp, pci, pva = oracle.permute(A, pe, ip)
+        gr = oracle.groups_split(lp, prp, budget)
+        X = gen.vector(A.n, 2, stream=141)[pe]
+        want = oracle.mpk(gen.CSR(prp, pci, pva), X, 6)
+        got = oracle.lb_mpk_waves(prp, pci, pva, X, 6, gr)
+        assert np.array_equal(got.view(np.uint64), want.view(np.uint64))
+    A = _star(6)
+    lo, pe, ip, lp = oracle.levels(A, 0)
+    prp, pci, pva = oracle.permute(A, pe, ip)
+    gr = oracle.groups_split(lp, prp, 50)
+    assert np.isnan(oracle.lb_mpk(prp, pci, pva, np.ones(A.n), 3, gr, skew=3)).any()
