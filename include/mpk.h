@@ -248,16 +248,19 @@ mpk_status mpk_apply(const mpk_plan_t *P, const double *X, int32_t p, double *Y,
  * device allocator is locked or must keep a fixed footprint, and latency-critical loops that
  * cannot afford the implicit device synchronisation of cudaMalloc/cudaFree.  The plan is
  * built beforehand and must use MPK_ORDER_PLAN (or no levels); X, p and Y are as for
- * mpk_apply.  The kernel's synchronisation state lives in one fixed array of 2^20 32-bit words
- * (4 MiB) of device memory that the library declares statically, held by every GPU that
- * loads the library until the process exits; a call needs 4 + (p+1) * num_chunks words and
- * fails with MPK_ERR_TOO_LARGE beyond that (larger chunk_rows means fewer chunks).  The
- * call allocates nothing: it clears the part of the array it uses, launches the kernel and,
- * if `status` (device int, caller-owned, may be NULL) is given, writes MPK_OK or
- * MPK_ERR_TIMEOUT there when the work completes on `stream`.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress); make that first call before
- * any stream capture.  All calls on a device share the array: calls that overlap on the
- * GPU (other streams, other threads) race and must be serialised by the caller. */
+ * mpk_apply (0 <= p <= p_max; p = 0 copies X to Y[0]).  The kernel's synchronisation state
+ * lives in one fixed array of 2^20 32-bit words (4 MiB) of device memory that the library
+ * declares statically, held by every GPU that loads the library until the process exits; a
+ * call needs 8 + (p+1) * num_chunks words (8 control words, then one completion flag per
+ * chunk and power) and fails with MPK_ERR_TOO_LARGE beyond that (larger chunk_rows means
+ * fewer chunks).  The call allocates nothing: it clears the part of the array it uses,
+ * launches the kernel and, if `status` (device int, caller-owned, may be NULL) is given,
+ * writes MPK_OK or MPK_ERR_TIMEOUT there when the work completes on `stream`.  The first
+ * call on a device looks up the array's device address (cudaGetSymbolAddress); make that
+ * first call before any stream capture.  The address is kept for the life of the process: a
+ * device reset (cudaDeviceReset) invalidates it, as it invalidates every plan.  All calls on a
+ * device share the array: calls that overlap on the GPU (other streams, other threads) race
+ * and must be serialised by the caller. */
 mpk_status mpk_apply_noalloc(const mpk_plan_t *P, const double *X, int32_t p, double *Y,
                              int32_t *status, mpk_stream stream);
 
@@ -284,9 +287,11 @@ mpk_status mpk_cheb_filter(const mpk_plan_t *P, const double *X, int32_t degree,
 
 /* The same filter in pieces, with its state in a caller-owned device buffer that can be saved
  * and restored between pieces (checkpoint/resume at any step; the natural point is a block
- * boundary of p_max steps): the ring (v_{k-1}, v_k) and the accumulator, 4 x n x nrhs float64
- * in the plan's row order, mpk_cheb_state_bytes(P) bytes.  Any split of the steps gives the
- * same bits as one mpk_cheb_filter call.
+ * boundary of p_max steps): 4 x n x nrhs float64 in the plan's row order,
+ * mpk_cheb_state_bytes(P) bytes.  Blocks 0..2 are a ring holding v_j in block j % 3 (when the
+ * state holds step k, v_k and v_{k-1} are live and the third block is scratch), block 3 is the
+ * accumulator.  Save and restore all mpk_cheb_state_bytes(P) bytes.  Any split of the steps
+ * gives the same bits as one mpk_cheb_filter call.
  *   mpk_cheb_begin:   state <- v_0 = X, acc = c_0 X (c_0 = c0_re + i c0_im on (re, im) column
  *                     pairs when complex_coeff is 1); the state holds step 0.
  *   mpk_cheb_advance: steps k_begin+1 .. k_end with coefficients coeff_re[k] (and coeff_im[k]),

@@ -366,12 +366,34 @@ class Plan:
         if X.numel() != self.n * self.nrhs:
             raise ValueError(f"X has {X.numel()} elements, plan wants n*nrhs = {self.n * self.nrhs}")
 
+    def _out_block(self, Y, X, blocks: int, name: str = "Y"):
+        """Y must hold `blocks` n x nrhs float64 blocks, contiguous, on X's device (the kernels
+        write all of them)."""
+        torch = _torch()
+        if Y.dtype != torch.float64 or not Y.is_cuda or not Y.is_contiguous():
+            raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+        if Y.device != X.device:
+            raise ValueError(f"{name} is on {Y.device}, X on {X.device}")
+        if Y.numel() < blocks * self.n * self.nrhs:
+            raise ValueError(f"{name} has {Y.numel()} elements, the call writes {blocks} x n x nrhs = "
+                             f"{blocks * self.n * self.nrhs}")
+
+    @staticmethod
+    def _status_word(status, X):
+        torch = _torch()
+        if status is None:
+            return None
+        if status.dtype != torch.int32 or not status.is_cuda or status.numel() < 1 or status.device != X.device:
+            raise TypeError("status must be an int32 CUDA tensor of at least one element on X's device")
+        return _ptr(status)
+
     def apply(self, X, p: int, Y=None, stream=None):
         """Y[k] = A^k X, k = 0..p (level-blocked).  Returns Y of shape (p+1, n, nrhs)."""
         torch = _torch()
         self._block(X)
         if Y is None:
             Y = torch.empty((p + 1, self.n, self.nrhs), dtype=torch.float64, device=X.device)
+        self._out_block(Y, X, p + 1)
         _check(self._lib.mpk_apply(self._h, _ptr(X), int(p), _ptr(Y), _stream(stream)))
         return Y
 
@@ -380,12 +402,15 @@ class Plan:
         Y must be given; status, if given, is a one-element int32 CUDA tensor that receives
         the launch's status code."""
         self._block(X)
-        _check(self._lib.mpk_apply_noalloc(self._h, _ptr(X), int(p), _ptr(Y), _ptr(status) if status is not None
-                                           else None, _stream(stream)))
+        self._out_block(Y, X, p + 1)
+        _check(self._lib.mpk_apply_noalloc(self._h, _ptr(X), int(p), _ptr(Y), self._status_word(status, X),
+                                           _stream(stream)))
         return Y
 
     def spmv_rows(self, row_begin: int, row_end: int, X, Y, stream=None):
         """Y[r] = (A X)[r] for plan-order rows r in [row_begin, row_end) (other rows untouched)."""
+        self._block(X)
+        self._out_block(Y, X, 1)
         _check(self._lib.mpk_spmv_rows(self._h, int(row_begin), int(row_end), _ptr(X), _ptr(Y), _stream(stream)))
         return Y
 
@@ -395,6 +420,7 @@ class Plan:
         self._block(X)
         if Y is None:
             Y = torch.empty((p + 1, self.n, self.nrhs), dtype=torch.float64, device=X.device)
+        self._out_block(Y, X, p + 1)
         _check(self._lib.mpk_spmv_powers(self._h, _ptr(X), int(p), _ptr(Y), _stream(stream)))
         return Y
 
@@ -410,6 +436,7 @@ class Plan:
             raise ValueError("need degree+1 coefficients")
         if out is None:
             out = torch.empty((self.n, self.nrhs), dtype=torch.float64, device=X.device)
+        self._out_block(out, X, 1, "out")
         _check(self._lib.mpk_cheb_filter(self._h, _ptr(X), int(degree), cr.ctypes.data,
                                          ci.ctypes.data if ci is not None else None, float(scale), float(shift),
                                          _ptr(out), _stream(stream)))
@@ -425,6 +452,7 @@ class Plan:
     def cheb_begin(self, X, state, c0_re: float, c0_im: float | None = None, stream=None):
         """state <- (v_0 = X, acc = c_0 X); the state then holds step 0."""
         self._block(X)
+        self._out_block(state, X, 4, "state")
         _check(self._lib.mpk_cheb_begin(self._h, _ptr(X), float(c0_re), float(c0_im or 0.0),
                                         1 if c0_im is not None else 0, _ptr(state), _stream(stream)))
         return state
@@ -433,6 +461,7 @@ class Plan:
                      shift: float = 0.0, stream=None):
         """Steps k_begin+1 .. k_end of the recurrence (absolute coefficient indices)."""
         import numpy as np
+        self._out_block(state, state, 4, "state")
         cr = np.ascontiguousarray(coeff_re, dtype=np.float64)
         ci = None if coeff_im is None else np.ascontiguousarray(coeff_im, dtype=np.float64)
         if cr.size < k_end + 1 or (ci is not None and ci.size < k_end + 1):
@@ -445,8 +474,10 @@ class Plan:
     def cheb_finish(self, state, out=None, stream=None):
         """out <- the accumulated filter (numbering as the plan's order option)."""
         torch = _torch()
+        self._out_block(state, state, 4, "state")
         if out is None:
-            out = torch.empty((self.n, self.nrhs), dtype=torch.float64, device="cuda")
+            out = torch.empty((self.n, self.nrhs), dtype=torch.float64, device=state.device)
+        self._out_block(out, state, 1, "out")
         _check(self._lib.mpk_cheb_finish(self._h, _ptr(state), _ptr(out), _stream(stream)))
         return out
 

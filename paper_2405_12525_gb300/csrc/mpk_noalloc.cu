@@ -13,8 +13,11 @@
 namespace mpk {
 
 // Scratch shared by every call on a device: kNoAllocInts 32-bit words (4 MiB).  Every GPU
-// that loads the library holds this array until the process exits.
+// that loads the library holds this array until the process exits.  A call uses
+// kNoAllocCtl control words (ticket, exit count, error epoch, error code, last epoch, padding)
+// and then (p + 1) * num_chunks completion flags.
 constexpr int64_t kNoAllocInts = int64_t(1) << 20;
+constexpr int64_t kNoAllocCtl = 8;
 static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocInts];
 
 // Host-side device address of the array, looked up once per device (the symbol's name is
@@ -55,18 +58,24 @@ extern "C" mpk_status mpk_apply_noalloc(const mpk_plan_t *Ph, const double *X, i
         if (!P.inst_row.empty()) fail(MPK_ERR_INVALID, "a batch plan runs through mpk_batch_apply");
         if (!(P.identity || P.order == MPK_ORDER_PLAN))
             fail(MPK_ERR_UNSUPPORTED, "mpk_apply_noalloc needs a plan in MPK_ORDER_PLAN (or without levels)");
-        if (p < 1 || p > P.p_max) fail(MPK_ERR_INVALID, "p = %d outside [1, p_max = %d]", p, P.p_max);
+        if (p < 0 || p > P.p_max) fail(MPK_ERR_INVALID, "p = %d outside [0, p_max = %d]", p, P.p_max);
         if (P.n > 0 && (!X || !Y)) fail(MPK_ERR_INVALID, "NULL X or Y");
+        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+        if (p == 0) {  // as mpk_apply: Y[0] = X, nothing computed, nothing allocated
+            if (P.n > 0 && Y != X)
+                MPK_CUDA(cudaMemcpyAsync(Y, X, sizeof(double) * (size_t)P.n * P.m, cudaMemcpyDeviceToDevice, s));
+            if (status) MPK_CUDA(cudaMemsetAsync(status, 0, sizeof(int32_t), s));
+            return MPK_OK;
+        }
         // scratch layout: [0..4] ticket, exit count, error epoch, error code, epoch of the last
-        // launch (zero: this launch is epoch 1); from [8] the completion flags of powers 0..p
-        // for every chunk
-        const int64_t need = 8 + (int64_t)(p + 1) * (P.num_chunks > 0 ? P.num_chunks : 1);
+        // launch (zero: this launch is epoch 1); from [kNoAllocCtl] the completion flags of
+        // powers 0..p for every chunk
+        const int64_t need = kNoAllocCtl + (int64_t)(p + 1) * (P.num_chunks > 0 ? P.num_chunks : 1);
         if (need > kNoAllocInts)
             fail(MPK_ERR_TOO_LARGE,
                  "mpk_apply_noalloc needs %lld scratch words for %d chunks and p = %d; the fixed scratch holds %lld "
                  "(use mpk_apply, or fewer chunks: larger chunk_rows)",
                  (long long)need, P.num_chunks, p, (long long)kNoAllocInts);
-        cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
         int32_t *scratch = scratch_address();
         // the previous call's flags and counters are still in the array: start from zero
         MPK_CUDA(cudaMemsetAsync(scratch, 0, sizeof(int32_t) * (size_t)need, s));
@@ -87,7 +96,7 @@ extern "C" mpk_status mpk_apply_noalloc(const mpk_plan_t *Ph, const double *X, i
             a.nchunks = P.num_chunks;
             a.units = P.units + P.unit_off[p];
             a.nunits = P.unit_off[p + 1] - P.unit_off[p];
-            a.flags = scratch + 8;
+            a.flags = scratch + kNoAllocCtl;
             a.epoch_word = reinterpret_cast<unsigned int *>(scratch + 4);
             a.ticket = reinterpret_cast<unsigned int *>(scratch);
             a.exit_count = reinterpret_cast<unsigned int *>(scratch + 1);

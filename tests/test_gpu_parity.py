@@ -356,6 +356,14 @@ def test_bad_arguments(mpk):
     P = mpk.plan(dA, L, p_max=3)
     with pytest.raises(mpk.MpkError):
         P.apply(torch.zeros(64, dtype=torch.float64, device="cuda"), 4)
+    # outputs that cannot hold what the call writes are refused by the binding
+    X = torch.zeros(64, dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        P.apply(X, 3, Y=torch.empty((3, 64, 1), dtype=torch.float64, device="cuda"))
+    with pytest.raises(TypeError):
+        P.apply(X, 2, Y=torch.empty((3, 64, 1), dtype=torch.float64))
+    with pytest.raises(ValueError):
+        P.cheb_filter(X, 3, np.ones(4), out=torch.empty(10, dtype=torch.float64, device="cuda"))
 
 
 # ----------------------------------------------------------------------------- Chebyshev (a6')

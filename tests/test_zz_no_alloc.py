@@ -56,3 +56,24 @@ def test_noalloc_rejects_too_many_chunks_and_original_order(mpk):
     with pytest.raises(mpk.MpkError) as e:
         Po.apply_noalloc(X, 2, torch.empty((3, A.n, 1), dtype=torch.float64, device="cuda"))
     assert e.value.status == 7
+
+
+def test_noalloc_p0_and_checked_outputs(mpk):
+    # p = 0 copies X into Y[0], as mpk_apply does; outputs too small for the call, or a status
+    # word that is not a device int32, are refused before anything reaches the GPU
+    A = gen.laplacian_3d(12, 10, 8)
+    dA = mpk.CsrMatrix.from_host(A, is_symmetric=True)
+    P = mpk.plan(dA, mpk.build_levels(dA, 0), p_max=4, nrhs=1, order=mpk.ORDER_PLAN)
+    X = torch.from_numpy(gen.vector(A.n, 1, stream=13)).cuda()
+    Y = torch.full((1, A.n, 1), float("nan"), dtype=torch.float64, device="cuda")
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    P.apply_noalloc(X, 0, Y, status=status)
+    torch.cuda.synchronize()
+    assert torch.equal(Y[0], X.view(A.n, 1)) and int(status.item()) == 0
+    with pytest.raises(ValueError):
+        P.apply_noalloc(X, 3, torch.empty((3, A.n, 1), dtype=torch.float64, device="cuda"))
+    with pytest.raises(TypeError):
+        P.apply_noalloc(X, 1, torch.empty((2, A.n, 1), dtype=torch.float64, device="cuda"),
+                        status=torch.zeros(1, dtype=torch.int64, device="cuda"))
+    with pytest.raises(TypeError):
+        P.apply_noalloc(X, 1, torch.empty((2, A.n, 1), dtype=torch.float32, device="cuda"))
