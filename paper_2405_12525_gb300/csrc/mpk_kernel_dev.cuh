@@ -637,6 +637,41 @@ __device__ __forceinline__ bool deps_ready(const KArgs &a, int32_t epoch, int k,
     return __all_sync(0xffffffffu, ok);
 }
 
+// Two units' dependency flags on one round trip: lanes 0..15 poll unit A's, lanes 16..31 unit
+// B's (64 flags a half per round; units of power 1 poll nothing).  Returns A's readiness in
+// bit 0 and B's in bit 1 (warp-uniform).  Every flag is loaded with acquire semantics by the
+// lane that checks it, as in deps_ready.
+__device__ __forceinline__ int deps_ready_pair(const KArgs &a, int32_t epoch, int kA, const int (&loA)[kDepRanges],
+                                               const int (&lenA)[kDepRanges], int totA, int kB,
+                                               const int (&loB)[kDepRanges], const int (&lenB)[kDepRanges],
+                                               int totB, int lane) {
+    const bool hiB = lane >= 16;
+    const int sl = lane & 15;
+    const int k = hiB ? kB : kA;
+    const int tot = (k > 1) ? (hiB ? totB : totA) : 0;
+    const int tmax = max((kA > 1) ? totA : 0, (kB > 1) ? totB : 0);
+    const int32_t *f = a.flags + (int64_t)(k - 1) * a.nchunks;
+    bool ok = true;
+    for (int v0 = 0; v0 < tmax; v0 += 64) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            int v = v0 + 16 * q + sl, idx = -1;
+            if (v < tot) {
+#pragma unroll
+                for (int r = 0; r < kDepRanges; ++r) {
+                    const int lo = hiB ? loB[r] : loA[r], len = hiB ? lenB[r] : lenA[r];
+                    if (idx < 0 && v < len) idx = lo + v;
+                    if (idx < 0) v -= len;
+                }
+            }
+            const int got = idx >= 0 ? ld_acquire(f + idx) : epoch;
+            ok = ok && got == epoch;
+        }
+    }
+    const unsigned int m = __ballot_sync(0xffffffffu, ok);
+    return ((m & 0xffffu) == 0xffffu ? 1 : 0) | ((m >> 16) == 0xffffu ? 2 : 0);
+}
+
 // dependency ranges of a chunk record (ints 8..15, shuffled from the lanes holding them)
 __device__ __forceinline__ int dep_ranges_of(int rec, int (&lo)[kDepRanges], int (&len)[kDepRanges]) {
     int total = 0;
@@ -1075,6 +1110,7 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
         u_nxt = __shfl_sync(0xffffffffu, u_nxt, 0);
         int r_cur = rec_at(u_cur);
         int r_nxt = rec_at(u_nxt);
+        bool cur_ready = false, nxt_ready = false;  // dependencies already acquired (paired poll)
         int i = 0;
         for (;; ++i) {
             if (u_cur < 0) break;  // no more work
@@ -1112,11 +1148,22 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
                 for (int o = 1; o < kXWin; o <<= 1) xbytes += __shfl_xor_sync(0xffffffffu, xbytes, o);
             }
             if (tr && lane == 0) tr_add(11, clock64() - c0);
-            // dependencies of unit i: all lanes poll its flags (acquire)
+            // dependencies of unit i, polled together with those of unit i+1 (one round trip for
+            // two units): a unit found ready this way skips its own poll in the next iteration.
+            // Its flags were acquired by lanes 16..31, whose order reaches that unit's hand-over
+            // through the warp barrier before lane 0's arrival on full[b].
             auto poll_deps = [&]() {
-                if (k > 1) {
+                const bool known = cur_ready;
+                cur_ready = false;
+                if (k > 1 && !known) {
                     const uint64_t t0 = globaltimer();
-                    while (!deps_ready(a, epoch, k, dlo, dlen, total, lane)) {
+                    int nlo[kDepRanges], nlen[kDepRanges];
+                    const int ntot = dep_ranges_of(r_nxt, nlo, nlen);
+                    const int kn = u_nxt >= 0 ? (u_nxt & 31) : 0;
+                    for (;;) {
+                        const int rd = deps_ready_pair(a, epoch, k, dlo, dlen, total, kn, nlo, nlen, ntot, lane);
+                        nxt_ready = (rd & 2) != 0 && u_nxt >= 0;
+                        if (rd & 1) break;
                         if (lane == 0) tr_add(2, 1);
                         const bool stop = ld_relaxed(a.err) == epoch || timed_out(t0, a.wait_ns);
                         if (__any_sync(0xffffffffu, stop)) {
@@ -1126,6 +1173,8 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
                         __nanosleep(32);
                     }
                     if (tr && lane == 0) tr_add(1, globaltimer() - t0);
+                } else {
+                    nxt_ready = false;
                 }
             };
             // Shape 3 polls first, while slot b may still be in use: its entries and input
@@ -1242,6 +1291,8 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
             r_nxt = r2;
             u_nn = u3;
             t = t_next;
+            cur_ready = nxt_ready;
+            nxt_ready = false;
             if (tr && lane == 0) tr_add(10, clock64() - c5);
         }
         if (lane == 0 && s_final < 0) s_final = i;  // units 0..i-1 were handed over
