@@ -247,9 +247,12 @@ __device__ __forceinline__ double to_f64(float v) { return widen_binary32(__floa
 
 // The input block the row sums of local power k read: binary64 powers, or, with binary32
 // accumulation, the binary32 shadow ring (slot j & 1 holds the binary32 rounding of step j).
+// block of the ring that holds power / step j; j < ring always for powers, so the division
+// runs only for the Chebyshev recurrence (j is the same in the whole warp)
+__device__ __forceinline__ int ring_slot(const KArgs &a, int j) { return j < a.ring ? j : j % a.ring; }
 template <int M>
 __device__ __forceinline__ const double *input_block(const KArgs &a, int k) {
-    return (k == 1 && a.k_offset == 0) ? a.x0 : a.ybase + (int64_t)((a.k_offset + k - 1) % a.ring) * a.ystride;
+    return (k == 1 && a.k_offset == 0) ? a.x0 : a.ybase + (int64_t)ring_slot(a, a.k_offset + k - 1) * a.ystride;
 }
 template <int M, class AT> struct InputAcc {
     static __device__ __forceinline__ const double *get(const KArgs &a, int k) { return input_block<M>(a, k); }
@@ -273,7 +276,7 @@ __device__ __forceinline__ void epilogue_load(const KArgs &a, int k, int64_t r, 
 #pragma unroll
         for (int i = 0; i < M; ++i) e.own[i] = xin[r * M + i];
         if (j != 1) {
-            const double *vp2 = a.ybase + (int64_t)((j - 2) % a.ring) * a.ystride + r * M;
+            const double *vp2 = a.ybase + (int64_t)ring_slot(a, j - 2) * a.ystride + r * M;
 #pragma unroll
             for (int i = 0; i < M; ++i) e.back[i] = vp2[i];
         }
@@ -296,7 +299,7 @@ __device__ __forceinline__ void row_epilogue_loaded(const KArgs &a, int k, int64
     double w[M];
 #pragma unroll
     for (int i = 0; i < M; ++i) w[i] = to_f64(wa[i]);
-    double *y = a.ybase + (int64_t)(j % a.ring) * a.ystride + r * M;
+    double *y = a.ybase + (int64_t)ring_slot(a, j) * a.ystride + r * M;
     float *sh = A32 ? a.shadow + (int64_t)(j & 1) * a.ystride + r * M : nullptr;
     if constexpr (MODE == MODE_CHEB) {
         double vn[M];
@@ -397,6 +400,20 @@ __device__ __forceinline__ int slice_width(const int (&w)[4], int q) {
     const int word = (q < 8) ? ((q < 4) ? w[0] : w[1]) : ((q < 12) ? w[2] : w[3]);  // no dynamic indexing
     return (word >> (8 * (q & 3))) & 0xff;
 }
+// padded entries of the chunk's slices 0 .. q-1 (q <= kRecSlices): the byte widths of the
+// whole words before slice q, and the low bytes of its own word, each word summed by one
+// four-way byte dot product
+__device__ __forceinline__ int slice_prefix(const int (&w)[4], int q) {
+    const int wq = q >> 2;
+    const unsigned int part = (1u << (8 * (q & 3))) - 1u;  // bytes of slices before q in word wq
+    unsigned int pre = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const unsigned int m = t < wq ? 0xffffffffu : (t == wq ? part : 0u);
+        pre = __dp4a((unsigned int)w[t] & m, 0x01010101u, pre);
+    }
+    return (int)pre;
+}
 
 // A compute warp handles a unit in two phases.  Phase A reads the column indices of the
 // warp's first row batch from shared memory and issues the x gathers; phase B runs the
@@ -404,6 +421,10 @@ __device__ __forceinline__ int slice_width(const int (&w)[4], int q) {
 // publishes the unit.  Phase B directly follows phase A of the same unit: a warp holds no
 // unit across a wait, so its lanes, which wait on the slot's mbarrier one by one, always
 // work on the same unit.
+// Padding entries of the first batch (column -1) are skipped.  Binary32 row sums keep the
+// "stored" bits that phase A derived from the columns it read; binary64 sums read the column
+// again (measured faster there: the bit mask costs the binary64 loop a register it lacks).
+template <class AT> constexpr bool kPadMask = std::is_same<AT, float>::value;
 template <int M, class AT = double> struct Prefetch {
     static constexpr int B = Batch<M>::B;
     int unit;             // -1: nothing pending
@@ -411,6 +432,7 @@ template <int M, class AT = double> struct Prefetch {
     int r;                // this lane's row in the warp's first slice, -1 if none
     int off;              // offset of that row's entries in the slot (staged units)
     int width;            // width of the warp's first slice (staged units)
+    unsigned int valid;   // binary32 sums: bit q set when entry q of the first batch is stored
     AT x[B][M];           // x values of the first batch (entries j < min(B, width))
 };
 
@@ -425,10 +447,9 @@ __device__ __forceinline__ void phase_a(const KArgs &a, const UnitInfo &u, int b
     pf.r = -1;
     pf.width = 0;
     pf.off = 0;
+    pf.valid = 0;
     if (STAGING && u.staged && cwarp < u.nsl) {  // shapes without slots never stage
-        int pre = 0;
-#pragma unroll
-        for (int q = 0; q < kRecSlices; ++q) pre += (q < cwarp) ? slice_width(u.widths, q) : 0;
+        const int pre = slice_prefix(u.widths, cwarp);
         pf.width = slice_width(u.widths, cwarp);
         pf.off = 32 * pre + lane;
         const int r = u.row0 + 32 * cwarp + lane;
@@ -437,6 +458,7 @@ __device__ __forceinline__ void phase_a(const KArgs &a, const UnitInfo &u, int b
 #pragma unroll
     for (int q = 0; q < B; ++q) {
         const int c = (pf.r >= 0 && q < pf.width) ? scol[pf.off + 32 * q] : -1;
+        if constexpr (kPadMask<AT>) pf.valid |= (c >= 0 ? 1u : 0u) << q;
 #pragma unroll
         for (int i = 0; i < M; ++i) pf.x[q][i] = (c >= 0) ? xin[(int64_t)c * M + i] : AT(0);
     }
@@ -540,7 +562,7 @@ __device__ __forceinline__ void phase_b(const KArgs &a, int32_t epoch, const Pre
         bool on[B];
 #pragma unroll
         for (int q = 0; q < B; ++q) {
-            on[q] = pf.r >= 0 && q < pf.width && scol[pf.off + 32 * q] >= 0;
+            on[q] = kPadMask<AT> ? ((pf.valid >> q) & 1u) != 0 : (pf.r >= 0 && q < pf.width && scol[pf.off + 32 * q] >= 0);
             v[q] = on[q] ? sval[pf.off + 32 * q] : AT(0);
         }
         EpiRows<M> er;
@@ -566,7 +588,7 @@ __device__ __forceinline__ void phase_b(const KArgs &a, int32_t epoch, const Pre
             for (int i = 0; i < M; ++i) w[i] = AT(0);
 #pragma unroll
             for (int q = 0; q < B; ++q) {
-                if (q < pf.width && scol[pf.off + 32 * q] >= 0) {
+                if (kPadMask<AT> ? ((pf.valid >> q) & 1u) != 0 : (q < pf.width && scol[pf.off + 32 * q] >= 0)) {
                     const AT v = sval[pf.off + 32 * q];
 #pragma unroll
                     for (int i = 0; i < M; ++i) w[i] = afma(v, pf.x[q][i], w[i]);
@@ -577,9 +599,7 @@ __device__ __forceinline__ void phase_b(const KArgs &a, int32_t epoch, const Pre
         }
         for (int sl = cwarp + kCompWarps; sl < u.nsl; sl += kCompWarps) {  // further slices (wide chunks)
             const int64_t r = (int64_t)u.row0 + 32 * sl + lane;
-            int pre = 0;
-#pragma unroll
-            for (int q = 0; q < kRecSlices; ++q) pre += (q < sl) ? slice_width(u.widths, q) : 0;
+            const int pre = slice_prefix(u.widths, sl);
             if (r >= u.row1) continue;
             AT w[M];
             row_sum<M, 2, AT>(sval, scol, 32 * pre + lane, slice_width(u.widths, sl), xacc, w);  // rare: wide chunks
@@ -738,9 +758,7 @@ __device__ __forceinline__ void phase_x(const KArgs &a, int32_t epoch, const Uni
     const double *sx = sx0 + b * Shape<SH>::XW + (((uint64_t)xin >> 3) & 1u);
     if (u.nsl <= CW && (cwarp >= u.nsl || slice_width(u.widths, cwarp) <= B)) {
         // at most one slice of at most one batch: read it, release the slot, then compute
-        int pre = 0;
-#pragma unroll
-        for (int q = 0; q < kRecSlices; ++q) pre += (q < cwarp) ? slice_width(u.widths, q) : 0;
+        const int pre = slice_prefix(u.widths, cwarp);
         const int width = cwarp < u.nsl ? slice_width(u.widths, cwarp) : 0;
         const int64_t r = (int64_t)u.row0 + 32 * cwarp + lane;
         const bool row = cwarp < u.nsl && r < u.row1;
@@ -774,9 +792,7 @@ __device__ __forceinline__ void phase_x(const KArgs &a, int32_t epoch, const Uni
         return;
     }
     for (int sl = cwarp; sl < u.nsl; sl += CW) {
-        int pre = 0;
-#pragma unroll
-        for (int q = 0; q < kRecSlices; ++q) pre += (q < sl) ? slice_width(u.widths, q) : 0;
+        const int pre = slice_prefix(u.widths, sl);
         const int width = slice_width(u.widths, sl);
         const int64_t r = (int64_t)u.row0 + 32 * sl + lane;
         if (r >= u.row1) continue;
