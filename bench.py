@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=200.0, help="mean Poisson arrival rate (requests/s)")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="length of the arrival window (s)")
     ap.add_argument("--serve-rate2", type=float, default=10.0, help="second, sustainable arrival rate")
+    ap.add_argument("--serve-rates", default="2,5,10,15,20,25,30,50",
+                    help="arrival rates (requests/s) of the throughput-latency curve ('' for none)")
     ap.add_argument("--batch-count", type=int, default=64, help="matrices of the batch workload")
     ap.add_argument("--batch-nmax", type=float, default=2e6, help="largest matrix size of the batch workload")
     ap.add_argument("--split", action="store_true",
@@ -658,26 +660,76 @@ def main_serving(args):
         for w in range(1, 9):
             pools[(name, w)] = base[:, :w].contiguous()
         del base
-    runs = {}
-    for label, rate, secs, seed in (("config", args.serve_rate, args.serve_seconds, 950),
-                                    ("sustained", args.serve_rate2, max(args.serve_seconds, 10.0), 960)):
+    def result_bytes(r):
+        m = 1 << (r.nrhs - 1).bit_length()
+        return 8 * host[r.matrix].n * m * ((r.order + 1) if r.kind == "mpk" else 1)
+
+    def serve(rate, secs, seed, sample=0):
         reqs = serving_requests(mats, rate, secs, seed)
         for r in reqs:
             r.x = pools[(r.matrix, r.nrhs)]
             r.flops = request_flops(host[r.matrix], r)
+        keep = set()
+        if sample:  # a spread of kinds and matrix families whose results fit in 1 GB
+            seen = set()
+            for r in reqs:
+                key = (r.kind, r.matrix.split("_")[0])
+                if key not in seen and result_bytes(r) <= 1 << 30 and len(keep) < sample:
+                    seen.add(key)
+                    keep.add(r.rid)
         srv = Server(GpuBackend(mats, p_max=16, cheb_block=8, streams=8), hbm_budget=150 * 10 ** 9, max_inflight=8,
-                     keep_results=False)
+                     keep_results=keep or False)
         t0 = time.perf_counter()
         srv.run(reqs)
         wall = time.perf_counter() - t0
         st = srv.stats()
         st.update(rate_rps=rate, window_s=secs, wall_s=wall, rejected=len(srv.rejected))
-        runs[label] = st
+        check = None
+        if keep:
+            # every sampled result against the same request run alone on the otherwise idle
+            # device (plan, stream and launch as the server's, nothing else in flight)
+            be = GpuBackend(mats, p_max=16, cheb_block=8, streams=1)
+            same, worst = 0, 0.0
+            kinds = []
+            for r in srv.done:
+                if r.rid not in keep:
+                    continue
+                h = be.launch(r, be.make_plan(be.plan_key(r)))
+                torch.cuda.synchronize()
+                alone = be.collect(r, h)
+                got = r.result
+                same += bool(torch.equal(got.contiguous(), alone.contiguous()))
+                den = torch.linalg.vector_norm(alone.reshape(-1, alone.shape[-1]), dim=0)
+                num = torch.linalg.vector_norm((got - alone).reshape(-1, alone.shape[-1]), dim=0)
+                worst = max(worst, float((num / den.clamp_min(1e-300)).max()))
+                kinds.append(f"{r.kind} {r.matrix} order {r.order} nrhs {r.nrhs}")
+                r.result = None
+                del h, alone, got
+            check = {"sampled": len(kinds), "bit_identical_to_alone": same, "max_rel_diff": worst,
+                     "requests": kinds,
+                     "note": "served results (concurrent, 8 streams) vs the same request alone; the GPU tests "
+                             "compare every served request of a smaller mix with the oracle, bit for bit"}
+            del be
         for r in srv.done:
             r.result = None
         del srv
         torch.cuda.synchronize()
         torch.cuda.empty_cache()
+        return st, check
+
+    runs = {}
+    check = None
+    for label, rate, secs, seed in (("config", args.serve_rate, args.serve_seconds, 950),
+                                    ("sustained", args.serve_rate2, max(args.serve_seconds, 10.0), 960)):
+        st, chk = serve(rate, secs, seed, sample=8 if label == "config" else 0)
+        runs[label] = st
+        check = check or chk
+    curve = []
+    for k, rate in enumerate(float(x) for x in args.serve_rates.split(",") if x.strip()):
+        secs = max(args.serve_seconds, min(20.0, 40.0 / rate))  # about 40 requests or more a point
+        st, _ = serve(rate, secs, 970 + 10 * k)
+        curve.append({q: st.get(q) for q in ("rate_rps", "window_s", "requests", "p50_ms", "p99_ms", "mean_ms",
+                                             "throughput_rps", "gflops", "max_inflight", "peak_bytes")})
     c = runs["config"]
     line = {
         "metric": "Serving latency p50/p99 (config 5) on 1 GB300", "value": c["p50_ms"], "unit": "ms",
@@ -688,6 +740,7 @@ def main_serving(args):
                                "HBM budget 150 GB, at most 8 requests in flight on 8 streams",
                    "matrices": {k: [v.n, v.nnz] for k, v in host.items()}},
         "serving": runs, "p99_ms": c["p99_ms"], "throughput_rps": c["throughput_rps"], "gflops": c["gflops"],
+        "throughput_latency_curve": curve, "per_request_check": check,
         "clocks": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None,
     }
     if rank == 0:

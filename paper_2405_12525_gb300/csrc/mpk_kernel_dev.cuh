@@ -975,20 +975,14 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&s_rfull[q]);
                 if (last) break;
-                const int u2 = __shfl_sync(0xffffffffu, u_nn, 0);
-                const int r2 = rec_at(u2);
-                int u3 = -1;
-                unsigned int t_next = t;
-                if (lane == 0) {
-                    u3 = unit_at(t);
-                    t_next = atomicAdd(a.ticket, 1u);
-                }
-                u_cur = u_nxt;
+                u_cur = u_nxt;  // move up, then load into the tail (as the single control warp)
                 r_cur = r_nxt;
-                u_nxt = u2;
-                r_nxt = r2;
-                u_nn = u3;
-                t = t_next;
+                u_nxt = __shfl_sync(0xffffffffu, u_nn, 0);
+                r_nxt = rec_at(u_nxt);
+                if (lane == 0) {
+                    u_nn = unit_at(t);
+                    t = atomicAdd(a.ticket, 1u);
+                }
             }
         } else {
             // ------------------------------------------------------ stage warp
@@ -1292,21 +1286,17 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
             slot_busy[b] = true;
             slot_use[b] = i / kSlots;
             // prefetch after the hand-over, so that these loads and the atomic complete during
-            // the next units' staging and polls instead of delaying this unit's fence
-            const int u2 = __shfl_sync(0xffffffffu, u_nn, 0);
-            const int r2 = rec_at(u2);
-            int u3 = -1;
-            unsigned int t_next = t;
-            if (lane == 0) {
-                u3 = unit_at(t);                   // id of unit i+3
-                t_next = atomicAdd(a.ticket, 1u);  // ticket of unit i+4, claimed whether or not it exists
-            }
+            // the next units' staging and polls instead of delaying this unit's fence.  The
+            // pipeline moves up first and the loads then land directly in its tail (r_nxt,
+            // u_nn, t): nothing in this iteration reads a value still in flight.
             u_cur = u_nxt;
             r_cur = r_nxt;
-            u_nxt = u2;
-            r_nxt = r2;
-            u_nn = u3;
-            t = t_next;
+            u_nxt = __shfl_sync(0xffffffffu, u_nn, 0);  // loaded an iteration ago
+            r_nxt = rec_at(u_nxt);
+            if (lane == 0) {
+                u_nn = unit_at(t);            // id of unit i+3
+                t = atomicAdd(a.ticket, 1u);  // ticket of unit i+4, claimed whether or not it exists
+            }
             cur_ready = nxt_ready;
             nxt_ready = false;
             if (tr && lane == 0) tr_add(10, clock64() - c5);

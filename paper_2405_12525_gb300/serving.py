@@ -56,9 +56,10 @@ class _Waiting:
 
 class Server:
     """Continuous admission under a device-memory budget (bytes), at most `max_inflight`
-    requests in flight.  `backend` provides the device work (see GpuBackend)."""
+    requests in flight.  `backend` provides the device work (see GpuBackend).  keep_results:
+    True keeps every result on its request, False none, a set of request ids those requests'."""
 
-    def __init__(self, backend, hbm_budget: int, max_inflight: int = 8, keep_results: bool = True):
+    def __init__(self, backend, hbm_budget: int, max_inflight: int = 8, keep_results=True):
         self.backend = backend
         self.keep_results = keep_results
         self.budget = int(hbm_budget)
@@ -132,7 +133,8 @@ class Server:
             if self.backend.finished(handle):
                 req.t_done = now_fn()
                 res = self.backend.collect(req, handle)  # also checks the request's device status
-                req.result = res if self.keep_results else None
+                keep = self.keep_results
+                req.result = res if (keep is True or (keep and not isinstance(keep, bool) and req.rid in keep)) else None
                 self.used -= buf
                 self.free_plans.setdefault(key, []).append(plan)
                 self.done.append(req)

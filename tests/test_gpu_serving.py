@@ -1,5 +1,6 @@
 """Serving loop on the GPU: requests arriving while others run are admitted and overlap on the
-device; every result is the same, bit for bit, as the request run alone (and as the oracle)."""
+device; every result is the same, bit for bit, as the request run alone and as the oracle
+(MPK requests: every power; Chebyshev requests: the filtered block)."""
 import numpy as np
 import pytest
 
@@ -65,5 +66,7 @@ def test_serving_mix_equals_alone(mpk):
         else:
             P = mpk.plan(A, levels[r.matrix], p_max=8, nrhs=m)
             alone = P.cheb_filter(X, r.order, r.coeffs, scale=scale, shift=shift)[..., :r.nrhs]
+            want = oracle.cheb(host[r.matrix], r.x.cpu().numpy(), r.order, r.coeffs, scale=scale, shift=shift)
+            assert np.array_equal(r.result.cpu().numpy().view(np.uint64), want.view(np.uint64))
         P.sync_status()
         assert torch.equal(r.result.contiguous(), alone.contiguous())

@@ -135,3 +135,14 @@ def test_width_buckets():
     with pytest.raises(ValueError):
         width_bucket(9)
     assert math.isnan(Request(0, 0.0, "a", "mpk", 1, 1).latency)
+
+
+@pytest.mark.parametrize("keep,kept", [(True, set(range(12))), (False, set()), ({2, 7, 11}, {2, 7, 11})])
+def test_results_kept_for_all_none_or_selected_requests(keep, kept):
+    clock = Clock()
+    be = FakeBackend(clock)
+    srv = Server(be, hbm_budget=10 ** 6, max_inflight=4, keep_results=keep)
+    done = srv.run([Request(i, 0.001 * i, "A", "mpk", 3, 1) for i in range(12)], clock=clock, sleep=clock.sleep)
+    assert len(done) == 12
+    assert {r.rid for r in done if r.result is not None} == kept
+    assert all(r.result == ("result", r.rid) for r in done if r.result is not None)
