@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--serve-rate", type=float, default=200.0, help="mean Poisson arrival rate (requests/s)")
     ap.add_argument("--serve-seconds", type=float, default=3.0, help="length of the arrival window (s)")
     ap.add_argument("--serve-rate2", type=float, default=10.0, help="second, sustainable arrival rate")
+    ap.add_argument("--serve-shape", type=int, default=-1,
+                    help="plan option `shape` of the serving plans (-1: the serving default, 0: automatic)")
     ap.add_argument("--serve-rates", default="2,5,10,15,20,25,30,50",
                     help="arrival rates (requests/s) of the throughput-latency curve ('' for none)")
     ap.add_argument("--batch-count", type=int, default=64, help="matrices of the batch workload")
@@ -641,7 +643,8 @@ def main_serving(args):
     import torch
     import gen
     import paper_2405_12525_gb300 as mpk
-    from paper_2405_12525_gb300.serving import GpuBackend, Server, request_flops
+    from paper_2405_12525_gb300.serving import SERVING_SHAPE, GpuBackend, Server, request_flops
+    shape = SERVING_SHAPE if args.serve_shape < 0 else args.serve_shape
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     mpk.build()
@@ -677,8 +680,8 @@ def main_serving(args):
                 if key not in seen and result_bytes(r) <= 1 << 30 and len(keep) < sample:
                     seen.add(key)
                     keep.add(r.rid)
-        srv = Server(GpuBackend(mats, p_max=16, cheb_block=8, streams=8), hbm_budget=150 * 10 ** 9, max_inflight=8,
-                     keep_results=keep or False)
+        srv = Server(GpuBackend(mats, p_max=16, cheb_block=8, streams=8, shape=shape),
+                     hbm_budget=150 * 10 ** 9, max_inflight=8, keep_results=keep or False)
         t0 = time.perf_counter()
         srv.run(reqs)
         wall = time.perf_counter() - t0
@@ -688,7 +691,7 @@ def main_serving(args):
         if keep:
             # every sampled result against the same request run alone on the otherwise idle
             # device (plan, stream and launch as the server's, nothing else in flight)
-            be = GpuBackend(mats, p_max=16, cheb_block=8, streams=1)
+            be = GpuBackend(mats, p_max=16, cheb_block=8, streams=1, shape=shape)
             same, worst = 0, 0.0
             kinds = []
             for r in srv.done:
@@ -738,7 +741,7 @@ def main_serving(args):
         "config": {"workload": "Poisson arrivals of MPK (p 4..16) and Chebyshev (degree 16..128) requests, 1..8 RHS, "
                                "matrices from the 256^3 Laplacian, 8 config-3 matrices and the XXZ L=24 chain, "
                                "HBM budget 150 GB, at most 8 requests in flight on 8 streams",
-                   "matrices": {k: [v.n, v.nnz] for k, v in host.items()}},
+                   "matrices": {k: [v.n, v.nnz] for k, v in host.items()}, "plan_shape_option": shape},
         "serving": runs, "p99_ms": c["p99_ms"], "throughput_rps": c["throughput_rps"], "gflops": c["gflops"],
         "throughput_latency_curve": curve, "per_request_check": check,
         "clocks": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None,

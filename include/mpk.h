@@ -402,8 +402,9 @@ mpk_status mpk_spmv_rows_multi(int32_t count, const mpk_plan_t *const *plans, co
 mpk_status mpk_copy_rows(const double *src, const int64_t *src_idx, double *dst, const int64_t *dst_idx, int64_t n,
                          int32_t m, mpk_stream stream);
 
-/* dst[r] = src[idx[r]] for r < n, m doubles a row (device arrays): the halo exchange between
- * partitions held on one device.  Asynchronous on `stream`. */
+/* dst[r] = src[idx[r]] for r < n, m doubles a row (device arrays; src and dst do not
+ * overlap): the halo exchange between partitions held on one device.  Asynchronous on
+ * `stream`. */
 mpk_status mpk_gather_rows(const double *src, const int32_t *idx, int32_t n, int32_t m, double *dst,
                            mpk_stream stream);
 

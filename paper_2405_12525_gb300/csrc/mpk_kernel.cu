@@ -310,6 +310,36 @@ __global__ void k_gather_rows(const double *src, const int32_t *perm, int32_t ba
     }
 }
 
+// k_gather_rows for m = M: a thread gathers U rows a pass (all loads issued before the stores;
+// src and dst do not overlap), no division per element
+template <int M>
+__global__ void k_gather_rows_m(const double *__restrict__ src, const int32_t *__restrict__ perm, int32_t base,
+                                double *__restrict__ dst, int32_t n) {
+    constexpr int U = M >= 4 ? 1 : 4 / M;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r0 < n; r0 += U * stride) {
+        int64_t from[U];
+        double v[U][M];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t r = r0 + u * stride;
+            from[u] = r < n ? (int64_t)((perm ? __ldg(perm + r) : (int32_t)r) - base) : -1;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int c = 0; c < M; ++c) v[u][c] = from[u] >= 0 ? __ldg(src + from[u] * M + c) : 0.0;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t r = r0 + u * stride;
+            if (r < n) {
+#pragma unroll
+                for (int c = 0; c < M; ++c) dst[r * M + c] = v[u][c];
+            }
+        }
+    }
+}
+
 // dst[i] = src[i] rounded to the nearest binary32 (ties to even): the binary32 input of the
 // first step of binary32 accumulation
 __global__ void k_round_f32(const double *src, int64_t n, float *dst) {
@@ -348,7 +378,14 @@ static int grid_rows(int64_t n) {
 void launch_gather_rows(const double *src, const int32_t *perm, double *dst, int32_t n, int32_t m, cudaStream_t s,
                         int32_t base) {
     if (n <= 0) return;
-    k_gather_rows<<<grid_rows((int64_t)n * m), 256, 0, s>>>(src, perm, base, dst, n, m);
+    const int g = grid_rows(n);
+    switch (m) {
+        case 1: k_gather_rows_m<1><<<g, 256, 0, s>>>(src, perm, base, dst, n); break;
+        case 2: k_gather_rows_m<2><<<g, 256, 0, s>>>(src, perm, base, dst, n); break;
+        case 4: k_gather_rows_m<4><<<g, 256, 0, s>>>(src, perm, base, dst, n); break;
+        case 8: k_gather_rows_m<8><<<g, 256, 0, s>>>(src, perm, base, dst, n); break;
+        default: k_gather_rows<<<grid_rows((int64_t)n * m), 256, 0, s>>>(src, perm, base, dst, n, m);
+    }
     MPK_LAUNCHED();
 }
 
@@ -360,30 +397,43 @@ void launch_scatter_rows(const double *src, const int32_t *iperm, double *dst, i
 // Y[k][i] = W[k][iperm[i]] for k = 1..p: the powers computed in plan order, written in the
 // matrix's own order.  Stores are full, coalesced rows of the output; the gathered reads
 // come from rows that neighbouring original rows map to (for a BFS order these sit a few
-// levels apart and share cache sectors with the reads of nearby original rows).  One block
-// per SM walks tiles of kScatterTile consecutive original rows, power by power, so that the
-// sectors a tile reads stay in the SM's L1 until its other rows use them.
-constexpr int kScatterBS = 1024, kScatterItems = 16, kScatterTile = kScatterBS * kScatterItems;
+// levels apart and share cache sectors with the reads of nearby original rows).  Each block
+// walks tiles of consecutive original rows, power by power, so that the sectors a tile reads
+// stay in the SM's L1 until its other rows use them.  A thread first loads all of its rows of
+// a power (16 values in flight), then stores them, streaming: the output is not read again,
+// and L2 keeps the powers still to be read.  Blocks are small (a quarter of an SM's threads
+// and registers) so that they also start beside other kernels' blocks, as in serving.
+constexpr int kScatterBS = 256, kScatterValues = 16, kScatterBlocksPerSM = 4;
 
-__global__ void __launch_bounds__(kScatterBS, 1)
-    k_scatter_powers(const double *W, int64_t w_pstride, const int32_t *__restrict__ iperm, int32_t w_row0, double *Y,
-                     int32_t n, int32_t m, int32_t p) {
-    const int64_t nm = (int64_t)n * m;
-    for (int64_t base = (int64_t)blockIdx.x * kScatterTile; base < n; base += (int64_t)gridDim.x * kScatterTile) {
-        int32_t src[kScatterItems];
+template <int M>
+__global__ void __launch_bounds__(kScatterBS, kScatterBlocksPerSM)
+    k_scatter_powers(const double *__restrict__ W, int64_t w_pstride, const int32_t *__restrict__ iperm,
+                     int32_t w_row0, double *__restrict__ Y, int32_t n, int32_t p) {
+    constexpr int IT = kScatterValues / M;  // rows of a thread in a tile
+    constexpr int64_t kTile = (int64_t)kScatterBS * IT;
+    const int64_t nm = (int64_t)n * M;
+    for (int64_t base = (int64_t)blockIdx.x * kTile; base < n; base += (int64_t)gridDim.x * kTile) {
+        int32_t src[IT];
 #pragma unroll
-        for (int q = 0; q < kScatterItems; ++q) {
+        for (int q = 0; q < IT; ++q) {
             const int64_t i = base + (int64_t)q * kScatterBS + threadIdx.x;
             src[q] = i < n ? (iperm ? __ldg(iperm + i) : w_row0 + (int32_t)i) : -1;
         }
         for (int k = 1; k <= p; ++k) {
             const double *w = W + k * w_pstride;
             double *y = Y + k * nm;
+            double v[IT][M];
 #pragma unroll
-            for (int q = 0; q < kScatterItems; ++q) {
+            for (int q = 0; q < IT; ++q)
+#pragma unroll
+                for (int c = 0; c < M; ++c) v[q][c] = src[q] >= 0 ? __ldg(w + (int64_t)src[q] * M + c) : 0.0;
+#pragma unroll
+            for (int q = 0; q < IT; ++q) {
                 const int64_t i = base + (int64_t)q * kScatterBS + threadIdx.x;
-                if (src[q] >= 0)
-                    for (int c = 0; c < m; ++c) y[i * m + c] = w[(int64_t)src[q] * m + c];
+                if (src[q] >= 0) {
+#pragma unroll
+                    for (int c = 0; c < M; ++c) __stcs(y + i * M + c, v[q][c]);
+                }
             }
         }
     }
@@ -393,7 +443,14 @@ void launch_scatter_powers(const double *W, const int32_t *iperm, double *Y, int
                            cudaStream_t s, int64_t w_pstride, int32_t base) {
     if (n <= 0 || p <= 0) return;
     if (w_pstride < 0) w_pstride = (int64_t)n * m;
-    k_scatter_powers<<<device_sms(), kScatterBS, 0, s>>>(W, w_pstride, iperm, base, Y, n, m, p);
+    const int g = device_sms() * kScatterBlocksPerSM;
+    switch (m) {
+        case 1: k_scatter_powers<1><<<g, kScatterBS, 0, s>>>(W, w_pstride, iperm, base, Y, n, p); break;
+        case 2: k_scatter_powers<2><<<g, kScatterBS, 0, s>>>(W, w_pstride, iperm, base, Y, n, p); break;
+        case 4: k_scatter_powers<4><<<g, kScatterBS, 0, s>>>(W, w_pstride, iperm, base, Y, n, p); break;
+        case 8: k_scatter_powers<8><<<g, kScatterBS, 0, s>>>(W, w_pstride, iperm, base, Y, n, p); break;
+        default: fail(MPK_ERR_UNSUPPORTED, "scatter of %d right-hand sides", m);
+    }
     MPK_LAUNCHED();
 }
 
