@@ -118,8 +118,17 @@ def load_bandwidth(nbytes: int = 1 << 30, reps: int = 5) -> float:
     buf = np.ones(nbytes // 8, np.float64)
     _L().orc_load_sum(buf, buf.size, 1)  # touch
     t0 = time.perf_counter()
-    _L().orc_load_sum(buf, buf.size, reps)
-    return reps * buf.nbytes / (time.perf_counter() - t0)
+    total = _L().orc_load_sum(buf, buf.size, reps)
+    dt = time.perf_counter() - t0
+    if total != float(reps) * buf.size:  # every element was read (the sum is exact below 2^53)
+        raise RuntimeError(f"orc_load_sum returned {total}, expected {reps * buf.size}")
+    return reps * buf.nbytes / dt
+
+
+def load_sum(buf, reps: int = 1) -> float:
+    """reps times the sum of a float64 buffer, over all threads (the load-bandwidth kernel)."""
+    b = np.ascontiguousarray(buf, np.float64)
+    return _L().orc_load_sum(b, b.size, int(reps))
 
 
 def mpk_acc32(A, X, p: int) -> np.ndarray:

@@ -310,36 +310,6 @@ __global__ void k_gather_rows(const double *src, const int32_t *perm, int32_t ba
     }
 }
 
-// k_gather_rows for m = M: a thread gathers U rows a pass (all loads issued before the stores;
-// src and dst do not overlap), no division per element
-template <int M>
-__global__ void k_gather_rows_m(const double *__restrict__ src, const int32_t *__restrict__ perm, int32_t base,
-                                double *__restrict__ dst, int32_t n) {
-    constexpr int U = M >= 4 ? 1 : 4 / M;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r0 < n; r0 += U * stride) {
-        int64_t from[U];
-        double v[U][M];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t r = r0 + u * stride;
-            from[u] = r < n ? (int64_t)((perm ? __ldg(perm + r) : (int32_t)r) - base) : -1;
-        }
-#pragma unroll
-        for (int u = 0; u < U; ++u)
-#pragma unroll
-            for (int c = 0; c < M; ++c) v[u][c] = from[u] >= 0 ? __ldg(src + from[u] * M + c) : 0.0;
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t r = r0 + u * stride;
-            if (r < n) {
-#pragma unroll
-                for (int c = 0; c < M; ++c) dst[r * M + c] = v[u][c];
-            }
-        }
-    }
-}
-
 // dst[i] = src[i] rounded to the nearest binary32 (ties to even): the binary32 input of the
 // first step of binary32 accumulation
 __global__ void k_round_f32(const double *src, int64_t n, float *dst) {
@@ -378,14 +348,7 @@ static int grid_rows(int64_t n) {
 void launch_gather_rows(const double *src, const int32_t *perm, double *dst, int32_t n, int32_t m, cudaStream_t s,
                         int32_t base) {
     if (n <= 0) return;
-    const int g = grid_rows(n);
-    switch (m) {
-        case 1: k_gather_rows_m<1><<<g, 256, 0, s>>>(src, perm, base, dst, n); break;
-        case 2: k_gather_rows_m<2><<<g, 256, 0, s>>>(src, perm, base, dst, n); break;
-        case 4: k_gather_rows_m<4><<<g, 256, 0, s>>>(src, perm, base, dst, n); break;
-        case 8: k_gather_rows_m<8><<<g, 256, 0, s>>>(src, perm, base, dst, n); break;
-        default: k_gather_rows<<<grid_rows((int64_t)n * m), 256, 0, s>>>(src, perm, base, dst, n, m);
-    }
+    k_gather_rows<<<grid_rows((int64_t)n * m), 256, 0, s>>>(src, perm, base, dst, n, m);
     MPK_LAUNCHED();
 }
 

@@ -448,6 +448,16 @@ def test_parallel_oracle_leg_is_the_same_computation():
     assert np.array_equal(Y.view(np.uint64), oracle.mpk(A, X, 5).view(np.uint64))
 
 
+def test_load_sum_reads_every_element_once():
+    # the host load-bandwidth kernel of the CPU baseline: an exact sum (integers, any thread
+    # split), so a skipped or repeated chunk of the buffer changes the result
+    buf = np.arange(1, 100001, dtype=np.float64)
+    assert oracle.load_sum(buf, 1) == 100000 * 100001 / 2
+    assert oracle.load_sum(buf, 3) == 3 * 100000 * 100001 / 2
+    assert oracle.load_sum(buf[:0], 2) == 0.0
+    assert oracle.load_bandwidth(1 << 22, 2) > 0
+
+
 # ----------------------------------------------------------------------------- bulky levels split
 def _star(k=4):
     # row 0 joined to rows 1..k, every row with a diagonal: levels {0}, {1..k}

@@ -77,3 +77,24 @@ def test_noalloc_p0_and_checked_outputs(mpk):
                         status=torch.zeros(1, dtype=torch.int64, device="cuda"))
     with pytest.raises(TypeError):
         P.apply_noalloc(X, 1, torch.empty((2, A.n, 1), dtype=torch.float32, device="cuda"))
+
+
+def test_noalloc_leaves_device_memory_unchanged(mpk):
+    # after one warm-up call (lazy module loading, the scratch address lookup), further calls
+    # take no device memory: the free bytes the driver reports stay the same
+    A = gen.laplacian_3d(48, 40, 32)
+    dA = mpk.CsrMatrix.from_host(A, is_symmetric=True)
+    L = mpk.build_levels(dA, 0)
+    P = mpk.plan(dA, L, p_max=8, nrhs=1, order=mpk.ORDER_PLAN)
+    X = torch.from_numpy(gen.vector(A.n, 1, stream=31)).cuda()
+    Y = torch.empty((9, A.n, 1), dtype=torch.float64, device="cuda")
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    P.apply_noalloc(X, 8, Y, status=status)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for p in (8, 3, 0, 8):
+        P.apply_noalloc(X, p, Y, status=status)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert int(status.item()) == 0
+    assert free1 == free0
