@@ -140,7 +140,7 @@ typedef struct {
     int32_t shape;          /* block shape of the staged engine: 0 = chosen from the mean
                                row width (2, else 3 for rows too wide to stage); 1 = 13
                                compute warps, 3072-entry slots, 3 blocks per SM; 2 = 16
-                               warps, 4608 entries, 2 blocks; 3 = 15 warps, entries read from
+                               warps, 4608 entries, 2 blocks; 3 = 14 warps, entries read from
                                global memory;
                                4 = 10 compute warps, 2304-entry slots that also hold the
                                input rows the chunk reads (at most 4 row windows, 1664

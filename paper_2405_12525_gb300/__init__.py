@@ -614,7 +614,8 @@ class BatchPlan:
 
 
 def batch_plan(mats, p_each, p_max: int = 0, nrhs: int = 1, cache_bytes: int = 0, order: int = ORDER_ORIGINAL,
-               chunk_rows: int = 0, wait_limit_ns: int = 0, mem_budget: int = 0, stream=None) -> BatchPlan:
+               chunk_rows: int = 0, wait_limit_ns: int = 0, mem_budget: int = 0, shape: int = 0,
+               stream=None) -> BatchPlan:
     """One plan and one launch for several matrices (list of CsrMatrix, powers per matrix)."""
     lib = load()
     o = _Opts()
@@ -622,6 +623,7 @@ def batch_plan(mats, p_each, p_max: int = 0, nrhs: int = 1, cache_bytes: int = 0
     o.p_max = p_max or max(p_each)
     o.nrhs, o.cache_bytes, o.order = nrhs, cache_bytes, order
     o.chunk_rows, o.wait_limit_ns, o.mem_budget = chunk_rows, wait_limit_ns, mem_budget
+    o.shape = shape
     cs = (_Csr * len(mats))(*[A._c() for A in mats])
     pe = (C.c_int32 * len(mats))(*[int(p) for p in p_each])
     h = C.c_void_p()

@@ -1,5 +1,5 @@
-"""Autotuner for plan parameters: the group budget C (cache_bytes), the rows per chunk and,
-for single plans, the unblocked sweep engine as one more candidate.
+"""Autotuner for plan parameters: the group budget C (cache_bytes), the rows per chunk, the
+kernel's block shape and, for single plans, the unblocked sweep engine as one more candidate.
 
 The paper studies p and C by hand (Sec. 6, the p x C parameter scan); here each candidate
 plan is built, timed on the device with CUDA events over a few applies of the caller's
@@ -26,9 +26,18 @@ def _time(fn, reps: int):
 
 
 def default_candidates():
-    """Group budgets of 1/4, 1/2, 1 and 2 times the L2 size; the default chunk and twice it."""
+    """Group budgets of 1/4, 1/2, 1 and 2 times the L2 size; the default chunk and 960 rows; the
+    planner's block shape, shape 0 and the unstaged shape (plan option shape = 0, 1, 3)."""
     _, l2 = device_info()
-    return {"cache_bytes": [l2 // 4, l2 // 2, l2, 2 * l2], "chunk_rows": [0, 960]}
+    return {"cache_bytes": [l2 // 4, l2 // 2, l2, 2 * l2], "chunk_rows": [0, 960], "shape": [0, 1, 3]}
+
+
+def _grid(cands):
+    """Candidate options: every budget with every chunk size at the planner's shape, and with
+    the default chunk size at each other shape (a shape fixes its own default chunk)."""
+    for sh in cands.get("shape", [0]):
+        for cb, cr in itertools.product(cands["cache_bytes"], cands["chunk_rows"] if sh == 0 else [0]):
+            yield {"cache_bytes": cb, "chunk_rows": cr, "shape": sh}
 
 
 def tune_plan(dA, levels, p: int, X, nrhs: int = 1, order: int = ORDER_PLAN, candidates=None, reps: int = 3):
@@ -37,11 +46,11 @@ def tune_plan(dA, levels, p: int, X, nrhs: int = 1, order: int = ORDER_PLAN, can
     cands = candidates or default_candidates()
     report, best = [], None
     Y = torch.empty((p + 1, dA.n, nrhs), dtype=torch.float64, device=X.device)
-    for cb, cr in itertools.product(cands["cache_bytes"], cands["chunk_rows"]):
-        P = plan(dA, levels, p_max=p, nrhs=nrhs, order=order, cache_bytes=cb, chunk_rows=cr)
+    for o in _grid(cands):
+        P = plan(dA, levels, p_max=p, nrhs=nrhs, order=order, **o)
         ms = _time(lambda: P.apply(X, p, Y=Y), reps)
         P.sync_status()
-        report.append((ms, {"cache_bytes": cb, "chunk_rows": cr}))
+        report.append((ms, o))
         if best is None or ms < best[0]:
             best = (ms, P)
         else:
@@ -60,10 +69,10 @@ def tune_batch(mats, p_each, Xs, nrhs: int = 1, order: int = ORDER_PLAN, candida
     """Best batch plan for the matrices; returns (batch plan, [(ms, options), ...])."""
     cands = candidates or default_candidates()
     report, best = [], None
-    for cb, cr in itertools.product(cands["cache_bytes"], cands["chunk_rows"]):
-        B = batch_plan(mats, p_each, nrhs=nrhs, order=order, cache_bytes=cb, chunk_rows=cr)
+    for o in _grid(cands):
+        B = batch_plan(mats, p_each, nrhs=nrhs, order=order, **o)
         ms = _time(lambda: B.apply(Xs, in_place=True), reps)
-        report.append((ms, {"cache_bytes": cb, "chunk_rows": cr}))
+        report.append((ms, o))
         if best is None or ms < best[0]:
             best = (ms, B)
         else:

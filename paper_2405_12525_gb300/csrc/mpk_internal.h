@@ -182,7 +182,7 @@ struct BlockShape {
 #endif
 constexpr BlockShape kShapes[4] = {{13, 3072, 3, 2, 0, 1},
                                    {16, 4608, 2, 2, 0, 1},
-                                   {15, 0, 2, 2, 0, 1},
+                                   {14, 0, 2, 2, 0, 1},
                                    {MPK_XS_WARPS, MPK_XS_ENTRIES, MPK_XS_BLOCKS, MPK_XS_SLOTS, MPK_XS_WORDS, MPK_XS_CTL}};
 constexpr int kNumShapes = 4;
 constexpr int kShapeX = 3;  // the shape that stages input rows

@@ -21,13 +21,18 @@ template <int SH> struct Shape {
     static constexpr int XW = kShapes[SH].x_words;  // input-row words per slot (0: not staged)
     static constexpr bool X = XW > 0;
 };
-// blocks per SM the register budget is set for (65536 registers per SM).  Shape 0 runs the
-// single-vector power kernel at three blocks of 14 warps (40 registers a thread; its two
-// 3072-entry slots, 72 KB, fit three times in an SM's shared memory); wider blocks, the
-// Chebyshev recurrence, the traced kernel and shape 1 keep 64 registers at two blocks.
+// blocks per SM the register budget is set for (65536 registers per SM).  The single-vector
+// power kernel runs at the shape's own block count (shape 0: three blocks of 15 warps, 40
+// registers a thread; shape 1: two of 18, 56 registers).  Wider blocks, the Chebyshev
+// recurrence and the traced kernel run two blocks; the unstaged shape with 4 or more
+// right-hand sides runs one block of 96 registers, whose rows of 4-8 columns would spill at
+// two (measured: 27-point stencil 100^3, bfloat16, 8 columns, p = 8: 3.88 against 4.88 ms;
+// the staged shapes lose at one block: 6.74 against 4.94 ms).
 template <int M, int MODE, bool TRACE, int SH> struct MpkOcc {
     static constexpr int blocks = Shape<SH>::X ? kShapes[SH].blocks
-                                               : ((M == 1 && MODE == 0 && !TRACE) ? kShapes[SH].blocks : 2);
+                                  : (M == 1 && MODE == 0 && !TRACE) ? kShapes[SH].blocks
+                                  : (Shape<SH>::SE == 0 && M >= 4) ? 1
+                                                                    : 2;
 };
 constexpr int kSpmvBS = 256;        // threads per block of the plain SpMV kernel
 // Staging slots (Shape::SL): the control warp fills one while the compute warps work on another.
@@ -69,6 +74,10 @@ __device__ __forceinline__ int ld_acquire(const int32_t *p) {
 #define MPK_ACQ_POLL 1
 #endif
 constexpr bool kAcquirePoll = MPK_ACQ_POLL != 0;
+#ifndef MPK_DIRECT_PUBLISH
+#define MPK_DIRECT_PUBLISH 0
+#endif
+constexpr bool kDirectPublish = MPK_DIRECT_PUBLISH != 0;
 __device__ __forceinline__ void st_relaxed(int32_t *p, int v) {
     asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -492,13 +501,17 @@ __device__ __forceinline__ void publish_unit(const KArgs &a, int32_t epoch, int 
     __syncwarp();
     if (lane == 0) {
         __threadfence_block();  // this warp's stores before the count (block scope)
-        atomicAdd(&s_done[seq % kDoneRing], 1);
+        const int old = atomicAdd(&s_done[seq % kDoneRing], 1);
+        if (kDirectPublish && old == CW * (seq / kDoneRing + 1) - 1) {  // the unit's last warp
+            fence_acq_rel_gpu();
+            if (unit != a.drop_unit) st_relaxed(a.flags + (int64_t)(unit & 31) * a.nchunks + (unit >> 5), epoch);
+        }
     }
 }
 // The control warp may record sequence number i in the ring only once the publisher is past
 // i - kDoneRing (normally at once; bounded: false if the publisher made no progress in time).
 __device__ __forceinline__ bool useq_slot_free(volatile int *s_published, int i, int64_t limit) {
-    if (i - *s_published < kDoneRing) return true;
+    if (kDirectPublish || i - *s_published < kDoneRing) return true;
     const uint64_t t0 = globaltimer();
     while (i - *s_published >= kDoneRing)
         if (timed_out(t0, limit)) return false;
@@ -515,6 +528,7 @@ __device__ __forceinline__ int ld_relaxed_cta_shared(const int *p) {
 template <int CW>
 __device__ __forceinline__ void publisher_loop(const KArgs &a, int32_t epoch, const int *s_done, const int *s_useq,
                                                volatile int *s_final, volatile int *s_published, int lane) {
+    if constexpr (kDirectPublish) return;
     int j = 0;
     uint64_t t_idle = globaltimer();
     for (;;) {

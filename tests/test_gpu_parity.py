@@ -437,7 +437,7 @@ def test_apply_replays_from_cuda_graph(mpk):
                                   "disconnected", "single"])
 def test_apply_every_block_shape(mpk, shape, name):
     # the block shapes of the staged kernel (13 warps with 3072-entry slots, 16 warps with
-    # 4608, 15 warps reading entries from global memory, and input rows staged as well) give
+    # 4608, 14 warps reading entries from global memory, and input rows staged as well) give
     # the same bits; shape 3 refuses a plan whose chunks read input rows beyond a slot
     make, sym = MATRICES[name]
     A = make()
@@ -511,7 +511,7 @@ def test_automatic_block_shape(mpk):
         dA = _dev(A, mpk, True)
         P = mpk.plan(dA, mpk.build_levels(dA, 0), p_max=4)
         d = P.describe()
-        assert d["shape"] == want and d["engine"] == 0 and d["chunk_rows"] == 32 * (16 if want == 1 else 15)
+        assert d["shape"] == want and d["engine"] == 0 and d["chunk_rows"] == 32 * (16 if want == 1 else 14)
 
 
 @pytest.mark.parametrize("seed", [1, 2, 0x5EED])
