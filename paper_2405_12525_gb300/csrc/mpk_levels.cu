@@ -2,9 +2,13 @@
 // BFS permutation (Sec. 3, level definition, prose and Fig. 1).
 #include "mpk_internal.h"
 
+#include <cooperative_groups.h>
+
+#include <algorithm>
 #include <climits>
 
 namespace mpk {
+namespace cg = cooperative_groups;
 
 // err[0]: bad row pointer, err[1]: column out of range
 __global__ void k_validate(int32_t n, int32_t nnz, const int32_t *rp, const int32_t *ci, int32_t *err) {
@@ -60,38 +64,147 @@ __global__ void k_tfill(int32_t n, const int32_t *rp, const int32_t *ci, int32_t
             if (ci[e] != i) tci[atomicAdd(&pos[ci[e]], 1)] = (int32_t)i;
 }
 
-// ----------------------------------------------------------------------------- BFS
-// One frontier vertex per thread; neighbours from A's row and (if given) A^T's row.
-// A vertex joins the next level by winning the CAS from -1 (levels are BFS distances,
-// so the outcome does not depend on which thread wins).
-__global__ void k_bfs_expand(const int32_t *front, int32_t fsize, const int32_t *rp, const int32_t *ci,
-                             const int32_t *tp, const int32_t *tci, int32_t *level_of, int32_t next_level,
-                             int32_t *next, int32_t *next_count) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < fsize; t += stride) {
-        const int32_t v = front[t];
-        for (int32_t e = rp[v]; e < rp[v + 1]; ++e) {
-            const int32_t u = ci[e];
-            if (u != v && level_of[u] < 0 && atomicCAS(&level_of[u], -1, next_level) == -1)
-                next[atomicAdd(next_count, 1)] = u;
-        }
-        if (tp)
-            for (int32_t e = tp[v]; e < tp[v + 1]; ++e) {
-                const int32_t u = tci[e];
-                if (level_of[u] < 0 && atomicCAS(&level_of[u], -1, next_level) == -1)
-                    next[atomicAdd(next_count, 1)] = u;
+// ----------------------------------------------------------------------------- BFS on the device
+// The whole level-synchronous BFS in one cooperative launch (every block resident): per level the
+// blocks expand the frontier queue[head, tail) into level lev + 1 (appending at queue[tail + ..]),
+// meet at a grid barrier and all read the number found, so every block advances head, tail and
+// lev identically.  The counters rotate through three slots: phase q adds to slot q % 3 and
+// resets slot (q + 1) % 3, whose last readers (after barrier q - 2) have all passed barrier q - 1.
+// A graph whose search runs dry before every vertex is reached continues from the smallest
+// untouched vertex (a grid-wide minimum, one barrier), which opens the next level (one more
+// barrier to publish it).  Every barrier wait is bounded; on expiry the kernel records the
+// failure and all blocks leave.
+constexpr int64_t kBfsWaitNs = 2000000000LL;  // bound of one grid-barrier wait (2 s)
+struct BfsState {
+    unsigned int bar_count;  // arrivals at grid barriers, all rounds
+    int32_t cnt[3];    // vertices found per phase
+    int32_t minv[3];   // smallest untouched vertex per phase (INT_MAX: none)
+    int32_t levels;    // number of levels (written at the end)
+    int32_t err;       // 1: a barrier wait expired, 2: the search lost track of untouched vertices
+};
+
+__device__ __forceinline__ uint64_t bfs_clock() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// all blocks of the grid, barrier number `round` (counted by the caller, the same in every
+// block): the arrivals only grow, and barrier r is passed once r * gridDim.x blocks arrived.
+// Thread 0 arrives with an acquire-release add (the block's writes, ordered before it by the
+// block barrier, are released; the earlier arrivals acquired) and polls with acquire loads.
+// False when the wait expired (recorded in st->err).
+__device__ __forceinline__ bool bfs_grid_barrier(BfsState *st, unsigned int round, int64_t limit_ns) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int target = round * gridDim.x;
+        unsigned int v;
+        asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(v) : "l"(&st->bar_count) : "memory");
+        s_ok = 1;
+        if (v + 1 < target) {
+            const uint64_t t0 = bfs_clock();
+            for (;;) {
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(&st->bar_count) : "memory");
+                if (v >= target) break;
+                if (bfs_clock() - t0 > (uint64_t)limit_ns) {
+                    atomicCAS(&st->err, 0, 1);
+                    s_ok = 0;
+                    break;
+                }
+                __nanosleep(32);
             }
+        }
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// appends u at queue[tail + *cnt++]; the lanes of a warp that append together (a coalesced
+// group) share one atomic, each writing at its rank in the group
+__device__ __forceinline__ void bfs_append(int32_t *queue, int64_t tail, int32_t *cnt, int32_t u) {
+    cg::coalesced_group g = cg::coalesced_threads();
+    int32_t base = 0;
+    if (g.thread_rank() == 0) base = atomicAdd(cnt, (int32_t)g.size());
+    base = g.shfl(base, 0);
+    queue[tail + base + (int64_t)g.thread_rank()] = u;
+}
+
+// neighbours ci[e0 .. e1) of v join level `next` unless reached (CAS from -1), eight at a time:
+// their columns, then their levels, then the claims, so that a vertex's work is a few memory
+// round trips instead of two per neighbour
+__device__ __forceinline__ void bfs_visit(const int32_t *ci, int32_t e0, int32_t e1, int32_t v, int32_t *level_of,
+                                          int32_t next, int32_t *queue, int64_t tail, int32_t *cnt) {
+    for (int32_t eb = e0; eb < e1; eb += 8) {
+        int32_t u[8], l[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) u[q] = (eb + q < e1) ? ci[eb + q] : v;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) l[q] = (u[q] != v) ? level_of[u[q]] : 0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (l[q] < 0 && atomicCAS(&level_of[u[q]], -1, next) == -1) bfs_append(queue, tail, cnt, u[q]);
     }
 }
 
-// smallest index >= from with level_of < 0, searched in [from, to)
-__global__ void k_first_unvisited(const int32_t *level_of, int64_t from, int64_t to, int32_t *out) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = from + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < to; i += stride)
-        if (level_of[i] < 0) {
-            atomicMin(out, (int32_t)i);
+__global__ void __launch_bounds__(256) k_bfs_all(const int32_t *rp, const int32_t *ci, const int32_t *tp,
+                                                 const int32_t *tci, int32_t *level_of, int32_t *queue, int32_t n,
+                                                 int32_t head0, int32_t tail0, BfsState *st, int64_t limit_ns) {
+    const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
+    int64_t head = head0, tail = tail0, cursor = 0;
+    int32_t lev = 0;
+    int q = 0;               // phase
+    unsigned int round = 0;  // grid barriers passed
+    for (;;) {
+        // expand level lev
+        if (gtid == 0) {
+            st->cnt[(q + 1) % 3] = 0;
+            st->minv[(q + 1) % 3] = INT_MAX;
+        }
+        int32_t *cnt = &st->cnt[q % 3];
+        for (int64_t t = head + gtid; t < tail; t += gstride) {
+            const int32_t v = queue[t];
+            bfs_visit(ci, rp[v], rp[v + 1], v, level_of, lev + 1, queue, tail, cnt);
+            if (tp) bfs_visit(tci, tp[v], tp[v + 1], v, level_of, lev + 1, queue, tail, cnt);
+        }
+        if (!bfs_grid_barrier(st, ++round, limit_ns)) return;
+        const int32_t found = *(volatile int32_t *)cnt;
+        ++q;
+        head = tail;
+        tail += found;
+        if (found > 0) {
+            ++lev;
+            continue;
+        }
+        if (tail >= n) break;
+        // the search ran dry: the smallest untouched vertex (all below cursor are reached)
+        int32_t *mn = &st->minv[q % 3];
+        for (int64_t i = cursor + gtid; i < n; i += gstride)
+            if (level_of[i] < 0) {
+                atomicMin(mn, (int32_t)i);
+                break;
+            }
+        if (gtid == 0) {
+            st->cnt[(q + 1) % 3] = 0;
+            st->minv[(q + 1) % 3] = INT_MAX;
+        }
+        if (!bfs_grid_barrier(st, ++round, limit_ns)) return;
+        const int32_t v = *(volatile int32_t *)mn;
+        ++q;
+        if (v == INT_MAX) {
+            if (gtid == 0) atomicCAS(&st->err, 0, 2);
             return;
         }
+        cursor = v;
+        ++lev;
+        if (gtid == 0) {
+            level_of[v] = lev;
+            queue[tail] = v;
+        }
+        tail += 1;
+        if (!bfs_grid_barrier(st, ++round, limit_ns)) return;  // the new root before its expansion
+    }
+    if (gtid == 0) st->levels = lev + 1;
 }
 
 __global__ void k_set_root(int32_t *level_of, int32_t *queue_slot, int32_t v, int32_t level) {
@@ -174,15 +287,8 @@ Levels *build_levels(const mpk_csr *A, int32_t root, cudaStream_t s, const std::
         }
         // level-synchronous BFS; queue holds the levels back to back
         Tmp<int32_t> queue(n);
-        Tmp<int32_t> dcount(2);
-        int32_t *h = nullptr;
-        MPK_CUDA(cudaMallocHost(&h, 2 * sizeof(int32_t)));
-        struct HostFree {
-            int32_t *p;
-            ~HostFree() { cudaFreeHost(p); }
-        } hf{h};
         MPK_CUDA(cudaMemsetAsync(L->level_of, 0xff, sizeof(int32_t) * (size_t)n, s));
-        int64_t head = 0, tail = 1, cursor = 0;
+        int64_t head = 0, tail = 1;
         if (roots) {
             const int32_t nr = (int32_t)roots->size();
             Tmp<int32_t> d_roots(nr);
@@ -195,47 +301,31 @@ Levels *build_levels(const mpk_csr *A, int32_t root, cudaStream_t s, const std::
             k_set_root<<<1, 1, 0, s>>>(L->level_of, queue.p, root, 0);
             MPK_LAUNCHED();
         }
-        int32_t lev = 0;
-        while (true) {
-            if (tail > head) {
-                MPK_CUDA(cudaMemsetAsync(dcount.p, 0, sizeof(int32_t), s));
-                k_bfs_expand<<<grid_n(tail - head), 256, 0, s>>>(queue.p + head, (int32_t)(tail - head), A->row_ptr,
-                                                                 A->col, A->is_symmetric ? nullptr : tp.p,
-                                                                 tci.p, L->level_of, lev + 1, queue.p + tail,
-                                                                 dcount.p);
-                MPK_LAUNCHED();
-                MPK_CUDA(cudaMemcpyAsync(h, dcount.p, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-                MPK_CUDA(cudaStreamSynchronize(s));
-                const int32_t found = h[0];
-                head = tail;
-                tail += found;
-                if (found > 0) {
-                    ++lev;
-                    continue;
-                }
-            }
-            if (tail >= n) break;
-            // disconnected: the smallest untouched vertex opens level lev + 1
-            int32_t v = INT_MAX;
-            while (v == INT_MAX && cursor < n) {
-                const int64_t window = (int64_t)1 << 20;
-                const int64_t to = (cursor + window < (int64_t)n) ? cursor + window : (int64_t)n;
-                fill_i32(dcount.p + 1, INT_MAX, 1, s);
-                k_first_unvisited<<<grid_n(to - cursor), 256, 0, s>>>(L->level_of, cursor, to, dcount.p + 1);
-                MPK_LAUNCHED();
-                MPK_CUDA(cudaMemcpyAsync(h + 1, dcount.p + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
-                MPK_CUDA(cudaStreamSynchronize(s));
-                v = h[1];
-                if (v == INT_MAX) cursor = to;
-            }
-            if (v == INT_MAX) fail(MPK_ERR_CUDA, "BFS lost track of unvisited vertices");
-            cursor = v;
-            ++lev;
-            k_set_root<<<1, 1, 0, s>>>(L->level_of, queue.p + tail, v, lev);
-            MPK_LAUNCHED();
-            head = tail;
-            tail += 1;
-        }
+        // the levels, in one cooperative launch (every block resident)
+        Tmp<BfsState> st(1);
+        MPK_CUDA(cudaMemsetAsync(st.p, 0, sizeof(BfsState), s));
+        int per_sm = 0;
+        MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs_all, 256, 0));
+        if (per_sm < 1) fail(MPK_ERR_CUDA, "the BFS kernel does not fit an SM");
+        // two blocks per SM: enough threads for the widest frontiers, few arrivals per barrier
+        const int grid = std::min(per_sm, 2) * device_sms();
+        const int32_t *rpp = A->row_ptr, *cip = A->col;
+        const int32_t *tpp = A->is_symmetric ? nullptr : tp.p;
+        const int32_t *tcip = tci.p;
+        int32_t *lvl = L->level_of, *qp = queue.p;
+        int32_t nn = n, h0 = (int32_t)head, t0 = (int32_t)tail;
+        BfsState *stp = st.p;
+        int64_t limit = kBfsWaitNs;
+        void *args[] = {(void *)&rpp, (void *)&cip, (void *)&tpp, (void *)&tcip, (void *)&lvl, (void *)&qp,
+                        (void *)&nn, (void *)&h0, (void *)&t0, (void *)&stp, (void *)&limit};
+        MPK_CUDA(cudaLaunchCooperativeKernel((const void *)k_bfs_all, dim3(grid), dim3(256), args, 0, s));
+        MPK_LAUNCHED();
+        BfsState hs;
+        MPK_CUDA(cudaMemcpyAsync(&hs, st.p, sizeof(BfsState), cudaMemcpyDeviceToHost, s));
+        MPK_CUDA(cudaStreamSynchronize(s));
+        if (hs.err == 1) fail(MPK_ERR_TIMEOUT, "BFS: a grid barrier wait expired");
+        if (hs.err != 0) fail(MPK_ERR_CUDA, "BFS lost track of unvisited vertices");
+        const int32_t lev = hs.levels - 1;
         const int32_t nl = lev + 1;
         L->num_levels = nl;
         // permutation: stable sort of (level, id) pairs with ids ascending as input order
