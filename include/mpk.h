@@ -255,12 +255,12 @@ mpk_status mpk_apply(const mpk_plan_t *P, const double *X, int32_t p, double *Y,
  * chunk and power) and fails with MPK_ERR_TOO_LARGE beyond that (larger chunk_rows means
  * fewer chunks).  The call allocates nothing: it clears the part of the array it uses,
  * launches the kernel and, if `status` (device int, caller-owned, may be NULL) is given,
- * writes MPK_OK or MPK_ERR_TIMEOUT there when the work completes on `stream`.  The first
- * call on a device looks up the array's device address (cudaGetSymbolAddress); make that
- * first call before any stream capture.  The address is kept for the life of the process: a
- * device reset (cudaDeviceReset) invalidates it, as it invalidates every plan.  All calls on a
- * device share the array: calls that overlap on the GPU (other streams, other threads) race
- * and must be serialised by the caller. */
+ * writes MPK_OK or MPK_ERR_TIMEOUT there when the work completes on `stream`.  Every call
+ * looks up the array's device address in the current context (cudaGetSymbolAddress, which
+ * allocates nothing), so the address follows a device reset (plans do not survive one); the
+ * first call on a device loads the array's module: make it before any stream capture.  All
+ * calls on a device share the array: calls that overlap on the GPU (other streams, other
+ * threads) race and must be serialised by the caller. */
 mpk_status mpk_apply_noalloc(const mpk_plan_t *P, const double *X, int32_t p, double *Y,
                              int32_t *status, mpk_stream stream);
 

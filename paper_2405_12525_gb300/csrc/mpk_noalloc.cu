@@ -8,7 +8,6 @@
 #include "mpk_internal.h"
 
 #include <cstring>
-#include <mutex>
 
 namespace mpk {
 
@@ -20,25 +19,15 @@ constexpr int64_t kNoAllocInts = int64_t(1) << 20;
 constexpr int64_t kNoAllocCtl = 8;
 static __device__ __align__(256) int32_t g_noalloc_scratch[kNoAllocInts];
 
-// Host-side device address of the array, looked up once per device (the symbol's name is
-// only a host-side stand-in and must not be passed to a kernel).
-constexpr int kMaxDevices = 64;
-static int32_t *g_scratch_addr[kMaxDevices] = {};
-static std::mutex g_scratch_mutex;
-
+// Device address of the array in the current context, looked up on every call (no device
+// memory is allocated by the lookup): a cached address could outlive its context, e.g. after
+// cudaDeviceReset, when the module is loaded again elsewhere.
 static int32_t *scratch_address() {
-    int dev = 0;
-    MPK_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) fail(MPK_ERR_UNSUPPORTED, "device index %d beyond %d", dev, kMaxDevices);
-    std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *ptr = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess || !ptr)
-            fail(MPK_ERR_CUDA, "cudaGetSymbolAddress of the no-allocation scratch failed: %s", cudaGetErrorString(e));
-        g_scratch_addr[dev] = static_cast<int32_t *>(ptr);
-    }
-    return g_scratch_addr[dev];
+    void *ptr = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr)
+        fail(MPK_ERR_CUDA, "cudaGetSymbolAddress of the no-allocation scratch failed: %s", cudaGetErrorString(e));
+    return static_cast<int32_t *>(ptr);
 }
 
 // copies the launch's error code (0 or MPK_ERR_TIMEOUT) to the caller's status word
