@@ -74,10 +74,6 @@ __device__ __forceinline__ int ld_acquire(const int32_t *p) {
 #define MPK_ACQ_POLL 1
 #endif
 constexpr bool kAcquirePoll = MPK_ACQ_POLL != 0;
-#ifndef MPK_DIRECT_PUBLISH
-#define MPK_DIRECT_PUBLISH 0
-#endif
-constexpr bool kDirectPublish = MPK_DIRECT_PUBLISH != 0;
 __device__ __forceinline__ void st_relaxed(int32_t *p, int v) {
     asm volatile("st.relaxed.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -501,17 +497,13 @@ __device__ __forceinline__ void publish_unit(const KArgs &a, int32_t epoch, int 
     __syncwarp();
     if (lane == 0) {
         __threadfence_block();  // this warp's stores before the count (block scope)
-        const int old = atomicAdd(&s_done[seq % kDoneRing], 1);
-        if (kDirectPublish && old == CW * (seq / kDoneRing + 1) - 1) {  // the unit's last warp
-            fence_acq_rel_gpu();
-            if (unit != a.drop_unit) st_relaxed(a.flags + (int64_t)(unit & 31) * a.nchunks + (unit >> 5), epoch);
-        }
+        atomicAdd(&s_done[seq % kDoneRing], 1);
     }
 }
 // The control warp may record sequence number i in the ring only once the publisher is past
 // i - kDoneRing (normally at once; bounded: false if the publisher made no progress in time).
 __device__ __forceinline__ bool useq_slot_free(volatile int *s_published, int i, int64_t limit) {
-    if (kDirectPublish || i - *s_published < kDoneRing) return true;
+    if (i - *s_published < kDoneRing) return true;
     const uint64_t t0 = globaltimer();
     while (i - *s_published >= kDoneRing)
         if (timed_out(t0, limit)) return false;
@@ -528,7 +520,6 @@ __device__ __forceinline__ int ld_relaxed_cta_shared(const int *p) {
 template <int CW>
 __device__ __forceinline__ void publisher_loop(const KArgs &a, int32_t epoch, const int *s_done, const int *s_useq,
                                                volatile int *s_final, volatile int *s_published, int lane) {
-    if constexpr (kDirectPublish) return;
     int j = 0;
     uint64_t t_idle = globaltimer();
     for (;;) {
