@@ -123,7 +123,9 @@ void mpk_levels_destroy(mpk_levels *L);
  * ------------------------------------------------------------------------------------- */
 typedef struct {
     int32_t p_max;          /* largest power mpk_apply may request (1..31)                 */
-    int32_t nrhs;           /* m: 1, 2, 4 or 8 right-hand sides per call                    */
+    int32_t nrhs;           /* m: 1, 2, 4, 8 or 16 right-hand sides per call; 16 runs on the
+                               unstaged block shape (shape 0 or 3) of the staged or the sweep
+                               engine, else MPK_ERR_UNSUPPORTED                              */
     int64_t cache_bytes;    /* C in bytes; 0 = three quarters of the device L2            */
     int32_t order;          /* mpk_order of X, Y and the Chebyshev input/output             */
     int32_t chunk_rows;     /* rows per work unit (multiple of 32); 0 = 416 (13 slices)     */

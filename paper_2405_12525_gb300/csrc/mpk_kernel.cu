@@ -183,7 +183,7 @@ template <class VT> static void *select_sweep_vt(int mode, int m, bool a32) {
         }                                                                                                    \
         return mode == MODE_POWERS ? (void *)k_sweep<MM, MODE_POWERS, VT> : (void *)k_sweep<MM, MODE_CHEB, VT>; \
     }
-    SEL(1) SEL(2) SEL(4) SEL(8)
+    SEL(1) SEL(2) SEL(4) SEL(8) SEL(16)
 #undef SEL
     fail(MPK_ERR_UNSUPPORTED, "nrhs %d", m);
 }
@@ -237,7 +237,7 @@ static void launch_spmv_rows_vt(const RowSegs &segs, int m, cudaStream_t s) {
             k_spmv_rows<MM, VT, false><<<grid, kSpmvBS, 0, s>>>(segs);             \
         break;
     switch (m) {
-        L(1) L(2) L(4) L(8) default : fail(MPK_ERR_UNSUPPORTED, "nrhs %d", m);
+        L(1) L(2) L(4) L(8) L(16) default : fail(MPK_ERR_UNSUPPORTED, "nrhs %d", m);
     }
 #undef L
     MPK_LAUNCHED();
@@ -412,6 +412,7 @@ void launch_scatter_powers(const double *W, const int32_t *iperm, double *Y, int
         case 2: k_scatter_powers<2><<<g, kScatterBS, 0, s>>>(W, w_pstride, iperm, base, Y, n, p); break;
         case 4: k_scatter_powers<4><<<g, kScatterBS, 0, s>>>(W, w_pstride, iperm, base, Y, n, p); break;
         case 8: k_scatter_powers<8><<<g, kScatterBS, 0, s>>>(W, w_pstride, iperm, base, Y, n, p); break;
+        case 16: k_scatter_powers<16><<<g, kScatterBS, 0, s>>>(W, w_pstride, iperm, base, Y, n, p); break;
         default: fail(MPK_ERR_UNSUPPORTED, "scatter of %d right-hand sides", m);
     }
     MPK_LAUNCHED();

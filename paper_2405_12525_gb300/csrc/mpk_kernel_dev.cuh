@@ -1422,8 +1422,11 @@ template <class VT, int SH> static void *select_mpk_vs(int mode, int m, bool tra
         return mpk_fn<MM, MODE_CHEB, VT, SH>(trace, a32);                                 \
     }
     SEL(1) SEL(2) SEL(4) SEL(8)
+    if constexpr (Shape<SH>::SE == 0 && !Shape<SH>::X) {  // 16 columns: the unstaged shape only
+        SEL(16)
+    }
 #undef SEL
-    fail(MPK_ERR_UNSUPPORTED, "nrhs %d", m);
+    fail(MPK_ERR_UNSUPPORTED, "nrhs %d on this block shape", m);
 }
 
 // k_mpk of block shape SH for (mode, nrhs, trace, value type, accumulator), and its dynamic shared memory

@@ -324,8 +324,13 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
     if (!o) fail(MPK_ERR_INVALID, "options are NULL");
     validate_csr(A, s);
     if (o->p_max < 1 || o->p_max > kMaxP) fail(MPK_ERR_INVALID, "p_max must be in [1, %d]", kMaxP);
-    if (!(o->nrhs == 1 || o->nrhs == 2 || o->nrhs == 4 || o->nrhs == 8))
-        fail(MPK_ERR_UNSUPPORTED, "nrhs must be 1, 2, 4 or 8 (got %d)", o->nrhs);
+    if (!(o->nrhs == 1 || o->nrhs == 2 || o->nrhs == 4 || o->nrhs == 8 || o->nrhs == 16))
+        fail(MPK_ERR_UNSUPPORTED, "nrhs must be 1, 2, 4, 8 or 16 (got %d)", o->nrhs);
+    // 16 right-hand sides: a row's 16 x values and sums need the registers of the unstaged
+    // shape at one block per SM; the staged shapes and the warp engine would spill
+    if (o->nrhs == 16 && ((o->shape > 0 && o->shape != 3) || o->engine == MPK_ENGINE_WARP))
+        fail(MPK_ERR_UNSUPPORTED, "16 right-hand sides run on the unstaged block shape (plan option shape 0 or 3) "
+                                  "of the staged or the sweep engine");
     if (o->order != MPK_ORDER_ORIGINAL && o->order != MPK_ORDER_PLAN) fail(MPK_ERR_INVALID, "bad order");
     int32_t chunk_rows = o->chunk_rows;  // 0: 32 rows per compute warp of the block shape
     if (chunk_rows != 0 && (chunk_rows < 32 || chunk_rows > 8192 || chunk_rows % 32))
@@ -547,7 +552,7 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
             auto fits = [&](int sh, int slices) {
                 return (int64_t)slices * P->padded <= (int64_t)kShapes[sh].stage_entries * std::max(NS, 1);
             };
-            fallback_shape = fits(1, 6) ? 1 : 2;  // up to 24 entries a row on average
+            fallback_shape = (o->nrhs < 16 && fits(1, 6)) ? 1 : 2;  // up to 24 entries a row on average
             try_x = false;
         }
         const bool x_forced = o->shape - 1 == kShapeX;
