@@ -126,9 +126,11 @@ typedef struct {
     int32_t nrhs;           /* m: 1, 2, 4, 8 or 16 right-hand sides per call; 16 runs on the
                                unstaged block shape (shape 0 or 3) of the staged or the sweep
                                engine, else MPK_ERR_UNSUPPORTED                              */
-    int64_t cache_bytes;    /* C in bytes; 0 = three quarters of the device L2            */
+    int64_t cache_bytes;    /* C in bytes; 0 = three quarters of the device L2 (five
+                               quarters with two slices a warp, shape 5 below)               */
     int32_t order;          /* mpk_order of X, Y and the Chebyshev input/output             */
-    int32_t chunk_rows;     /* rows per work unit (multiple of 32); 0 = 416 (13 slices)     */
+    int32_t chunk_rows;     /* rows per work unit (multiple of 32); 0 = 32 per compute warp
+                               and slice of the block shape (512 for shape 2, 1024 for 5)     */
     int64_t wait_limit_ns;  /* bound on every device-side wait; 0 = 2 s                     */
     int64_t mem_budget;     /* bytes the plan may allocate on the device; 0 = no limit     */
     int32_t trace;          /* 1: the level-blocked kernel accumulates timing counters      */
@@ -139,8 +141,10 @@ typedef struct {
                                Needs levels and MPK_ORDER_PLAN (else MPK_ERR_INVALID);
                                mpk_cheb_filter rejects such a plan                           */
     int32_t engine;         /* MPK_ENGINE_STAGED (0, default) or MPK_ENGINE_WARP (1), below  */
-    int32_t shape;          /* block shape of the staged engine: 0 = chosen from the mean
-                               row width (2, else 3 for rows too wide to stage); 1 = 13
+    int32_t shape;          /* block shape of the staged engine: 0 = chosen: 5 for binary32
+                               sums over 2-byte values, one RHS and rows of at most 10
+                               entries, else from the mean row width (2, else 3 for rows too
+                               wide to stage); 1 = 13
                                compute warps, 3072-entry slots, 3 blocks per SM; 2 = 16
                                warps, 4608 entries, 2 blocks; 3 = 14 warps, entries read from
                                global memory;
@@ -148,7 +152,10 @@ typedef struct {
                                input rows the chunk reads (at most 4 row windows, 1664
                                doubles), 3 blocks per SM: the compute warps read only shared
                                memory.  Shape 4 is never chosen automatically; mpk_plan fails
-                               with MPK_ERR_UNSUPPORTED when a chunk's windows do not fit    */
+                               with MPK_ERR_UNSUPPORTED when a chunk's windows do not fit;
+                               5 = 16 compute warps taking two 32-row slices each of a unit,
+                               9216-entry slots, 2 blocks per SM (1 with 4-byte or wider
+                               values, whose slots take the shared memory of two)          */
     int64_t shuffle_seed;   /* race-detection aid: non-zero permutes the staged engine's work
                                units inside every line of the schedule (a valid order whose
                                results must be the same bits); 0 = the natural order         */

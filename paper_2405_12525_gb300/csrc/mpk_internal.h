@@ -161,6 +161,7 @@ constexpr int kMaxP = 31;
 // shape 2, unless the plan options name a shape (0 or 3 included).
 struct BlockShape {
     int comp_warps, stage_entries, blocks, slots, x_words, ctrl_warps;
+    int slices_per_warp;  // 32-row slices a compute warp takes per unit (0: one)
 };
 #ifndef MPK_XS_WARPS
 #define MPK_XS_WARPS 10
@@ -180,11 +181,12 @@ struct BlockShape {
 #ifndef MPK_XS_CTL
 #define MPK_XS_CTL 1
 #endif
-constexpr BlockShape kShapes[4] = {{13, 3072, 3, 2, 0, 1},
+constexpr BlockShape kShapes[5] = {{13, 3072, 3, 2, 0, 1},
                                    {16, 4608, 2, 2, 0, 1},
                                    {14, 0, 2, 2, 0, 1},
-                                   {MPK_XS_WARPS, MPK_XS_ENTRIES, MPK_XS_BLOCKS, MPK_XS_SLOTS, MPK_XS_WORDS, MPK_XS_CTL}};
-constexpr int kNumShapes = 4;
+                                   {MPK_XS_WARPS, MPK_XS_ENTRIES, MPK_XS_BLOCKS, MPK_XS_SLOTS, MPK_XS_WORDS, MPK_XS_CTL},
+                                   {16, 9216, 2, 2, 0, 1, 2}};
+constexpr int kNumShapes = 5;
 constexpr int kShapeX = 3;  // the shape that stages input rows
 // input-row windows of a chunk (shape 3): one per dependency range
 constexpr int kXWin = 4;
@@ -206,11 +208,14 @@ constexpr int kTraceShared = MPK_TRACE_COUNTERS - 1;
 constexpr int kSlotSkew = 3;
 // chunk record: 8 ints of chunk data, 2 * kDepRanges ints of dependency ranges, the
 // widths of up to kRecSlices slices as bytes (only staged chunks use them) and, for shape 3,
-// kXWin input-row windows as (first row, rows, position in the slot's window area in rows)
-constexpr int kRecSlices = 16;
+// kXWin input-row windows as (first row, rows, position in the slot's window area in rows);
+// the other shapes keep the widths of slices 16..31 in the first 4 window words
+constexpr int kRecSlices = 16;      // shape 3 (its windows follow the widths)
+constexpr int kRecSlicesWide = 32;  // the other shapes: the window words hold 16 more widths
 constexpr int kRecWin = 8 + 2 * kDepRanges + kRecSlices / 4;  // first int of the windows
 constexpr int kRecInts = kRecWin + 3 * kXWin;
 static_assert(kRecInts <= 32, "a chunk record is read by one lane per int");
+static_assert(kRecWin + kRecSlicesWide / 4 - kRecSlices / 4 <= kRecInts, "wide widths in the window words");
 struct KArgs {
     // sliced matrix copy (plan order)
     const void *val;  // values of the matrix's value type (Plan::val_type)

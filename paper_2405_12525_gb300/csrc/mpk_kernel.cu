@@ -436,7 +436,8 @@ static void *select_mpk(int mode, int m, bool trace, int vtype, int shape, bool 
     if (shape == 0) return select_mpk_shape0(mode, m, trace, vtype, a32);
     if (shape == 1) return select_mpk_shape1(mode, m, trace, vtype, a32);
     if (shape == 2) return select_mpk_shape2(mode, m, trace, vtype, a32);
-    return select_mpk_shape3(mode, m, trace, vtype, a32);
+    if (shape == 3) return select_mpk_shape3(mode, m, trace, vtype, a32);
+    return select_mpk_shape4(mode, m, trace, vtype, a32);
 }
 
 static int mpk_smem_bytes(int vtype, int shape) {
@@ -444,7 +445,8 @@ static int mpk_smem_bytes(int vtype, int shape) {
         case 0: return smem_bytes_shape<0>(vtype);
         case 1: return smem_bytes_shape<1>(vtype);
         case 2: return smem_bytes_shape<2>(vtype);
-        default: return smem_bytes_shape<3>(vtype);
+        case 3: return smem_bytes_shape<3>(vtype);
+        default: return smem_bytes_shape<4>(vtype);
     }
 }
 
@@ -453,15 +455,17 @@ static int mpk_block_size(int shape) {
         case 0: return Shape<0>::BS;
         case 1: return Shape<1>::BS;
         case 2: return Shape<2>::BS;
-        default: return Shape<3>::BS;
+        case 3: return Shape<3>::BS;
+        default: return Shape<4>::BS;
     }
 }
 
 int occupancy_grid(int mode, int m, bool trace, int vtype, int shape, bool a32) {
-    static int cache[3][2][2][9][kNumShapes][2] = {};
+    static int cache[3][2][2][5][kNumShapes][2] = {};  // width index: log2 of m (1 .. 16)
     if (vtype < 0 || vtype > 2) fail(MPK_ERR_UNSUPPORTED, "value type %d", vtype);
     if (shape < 0 || shape >= kNumShapes) fail(MPK_ERR_UNSUPPORTED, "block shape %d", shape);
-    int &c = cache[vtype][mode][trace ? 1 : 0][m][shape][a32 ? 1 : 0];
+    if (m < 1 || m > 16 || (m & (m - 1))) fail(MPK_ERR_UNSUPPORTED, "nrhs %d", m);
+    int &c = cache[vtype][mode][trace ? 1 : 0][__builtin_ctz((unsigned)m)][shape][a32 ? 1 : 0];
     if (c) return c;
     void *fn = select_mpk(mode, m, trace, vtype, shape, a32);
     const int smem = mpk_smem_bytes(vtype, shape);

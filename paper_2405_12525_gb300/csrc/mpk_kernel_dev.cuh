@@ -20,6 +20,7 @@ template <int SH> struct Shape {
     static constexpr int CTL = kShapes[SH].ctrl_warps;  // control warps: 1, or 2 (poll + stage)
     static constexpr int XW = kShapes[SH].x_words;  // input-row words per slot (0: not staged)
     static constexpr bool X = XW > 0;
+    static constexpr int SPW = kShapes[SH].slices_per_warp > 1 ? kShapes[SH].slices_per_warp : 1;
 };
 // blocks per SM the register budget is set for (65536 registers per SM).  The single-vector
 // power kernel runs at the shape's own block count (shape 0: three blocks of 15 warps, 40
@@ -395,25 +396,30 @@ struct UnitInfo {
     int ecount;       // padded entries of the chunk
     int staged;       // entries were copied to the slot's shared buffer
     int nsl;          // slices of the chunk
-    int widths[4];    // staged chunks: width of slice q in byte q of the 16 bytes
+    int widths[8];    // staged chunks: width of slice q in byte q of the 32 bytes (16 for shape 3)
     long long ebase;  // first entry of the chunk in the sliced copy
 };
 
 __device__ __forceinline__ bool timed_out(uint64_t t0, int64_t limit) { return globaltimer() - t0 > (uint64_t)limit; }
 
-__device__ __forceinline__ int slice_width(const int (&w)[4], int q) {
-    const int word = (q < 8) ? ((q < 4) ? w[0] : w[1]) : ((q < 12) ? w[2] : w[3]);  // no dynamic indexing
+// NW: the width words a shape uses (8 for two slices a warp, else 4: at most 16 slices)
+template <int NW = 4>
+__device__ __forceinline__ int slice_width(const int (&w)[8], int q) {
+    int word = w[0];
+#pragma unroll
+    for (int t = 1; t < NW; ++t) word = (q >> 2) == t ? w[t] : word;  // no dynamic indexing
     return (word >> (8 * (q & 3))) & 0xff;
 }
-// padded entries of the chunk's slices 0 .. q-1 (q <= kRecSlices): the byte widths of the
+// padded entries of the chunk's slices 0 .. q-1 (q <= kRecSlicesWide): the byte widths of the
 // whole words before slice q, and the low bytes of its own word, each word summed by one
 // four-way byte dot product
-__device__ __forceinline__ int slice_prefix(const int (&w)[4], int q) {
+template <int NW = 4>
+__device__ __forceinline__ int slice_prefix(const int (&w)[8], int q) {
     const int wq = q >> 2;
     const unsigned int part = (1u << (8 * (q & 3))) - 1u;  // bytes of slices before q in word wq
     unsigned int pre = 0;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
+    for (int t = 0; t < NW; ++t) {
         const unsigned int m = t < wq ? 0xffffffffu : (t == wq ? part : 0u);
         pre = __dp4a((unsigned int)w[t] & m, 0x01010101u, pre);
     }
@@ -442,7 +448,7 @@ template <int M, class AT = double> struct Prefetch {
 };
 
 // phase A: request the x values of the warp's first batch of unit u (slot b)
-template <int M, bool STAGING, class AT>
+template <int M, bool STAGING, class AT, int NW = 4>
 __device__ __forceinline__ void phase_a(const KArgs &a, const UnitInfo &u, int b, const int32_t *scol, int cwarp,
                                         int lane, Prefetch<M, AT> &pf) {
     constexpr int B = Batch<M>::B;
@@ -454,8 +460,8 @@ __device__ __forceinline__ void phase_a(const KArgs &a, const UnitInfo &u, int b
     pf.off = 0;
     pf.valid = 0;
     if (STAGING && u.staged && cwarp < u.nsl) {  // shapes without slots never stage
-        const int pre = slice_prefix(u.widths, cwarp);
-        pf.width = slice_width(u.widths, cwarp);
+        const int pre = slice_prefix<NW>(u.widths, cwarp);
+        pf.width = slice_width<NW>(u.widths, cwarp);
         pf.off = 32 * pre + lane;
         const int r = u.row0 + 32 * cwarp + lane;
         if (r < u.row1) pf.r = r;
@@ -604,10 +610,13 @@ __device__ __forceinline__ void phase_b(const KArgs &a, int32_t epoch, const Pre
         }
         for (int sl = cwarp + kCompWarps; sl < u.nsl; sl += kCompWarps) {  // further slices (wide chunks)
             const int64_t r = (int64_t)u.row0 + 32 * sl + lane;
-            const int pre = slice_prefix(u.widths, sl);
+            const int pre = slice_prefix<Shape<SH>::SPW * 4>(u.widths, sl);
             if (r >= u.row1) continue;
             AT w[M];
-            row_sum<M, 2, AT>(sval, scol, 32 * pre + lane, slice_width(u.widths, sl), xacc, w);  // rare: wide chunks
+            // a second slice of the warp (shapes of two slices a warp: all gathers of a batch at
+            // once) or, on the other shapes, the rare chunk wider than the block
+            constexpr int BS2 = Shape<SH>::SPW > 1 ? B : 2;
+            row_sum<M, BS2, AT>(sval, scol, 32 * pre + lane, slice_width<Shape<SH>::SPW * 4>(u.widths, sl), xacc, w);
             row_epilogue<M, MODE, AT>(a, k, r, w, xin);
         }
     } else {  // entries in global memory (chunk too large to stage): the slot holds nothing
@@ -1023,7 +1032,7 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
                 u.staged = __shfl_sync(0xffffffffu, r_cur, 6);
                 u.nsl = __shfl_sync(0xffffffffu, r_cur, 7);
 #pragma unroll
-                for (int w = 0; w < 4; ++w) u.widths[w] = __shfl_sync(0xffffffffu, r_cur, 16 + w);
+                for (int w = 0; w < 4 * Shape<SH>::SPW; ++w) u.widths[w] = __shfl_sync(0xffffffffu, r_cur, 16 + w);
                 const int k = un & 31;
                 XCopy xc{0, 0, 0, 0, 0};
                 uint32_t xbytes = 0;
@@ -1143,7 +1152,7 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
             u.staged = __shfl_sync(0xffffffffu, r_cur, 6);
             u.nsl = __shfl_sync(0xffffffffu, r_cur, 7);
 #pragma unroll
-            for (int q = 0; q < 4; ++q) u.widths[q] = __shfl_sync(0xffffffffu, r_cur, 16 + q);
+            for (int q = 0; q < 4 * Shape<SH>::SPW; ++q) u.widths[q] = __shfl_sync(0xffffffffu, r_cur, 16 + q);
             int dlo[kDepRanges], dlen[kDepRanges];
             const int total = dep_ranges_of(r_cur, dlo, dlen);
             const int k = u.unit & 31;
@@ -1357,7 +1366,7 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
                 if (tr && lane == 0) tr_add(13, clock64() - c1);
             } else {
                 const long long c0 = tr ? clock64() : 0;
-                phase_a<M, (kStageEntries > 0), AT>(a, s_u[b], b,
+                phase_a<M, (kStageEntries > 0), AT, Shape<SH>::SPW * 4>(a, s_u[b], b,
                                                      kStageCol ? scol0 + b * kStageEntries : a.col + s_u[b].ebase, cw,
                                                      lane, pf);
                 if (tr) {  // wait for the gathers (integer ops only) to split the unit time
@@ -1447,5 +1456,6 @@ void *select_mpk_shape0(int mode, int m, bool trace, int vtype, bool a32);
 void *select_mpk_shape1(int mode, int m, bool trace, int vtype, bool a32);
 void *select_mpk_shape2(int mode, int m, bool trace, int vtype, bool a32);
 void *select_mpk_shape3(int mode, int m, bool trace, int vtype, bool a32);
+void *select_mpk_shape4(int mode, int m, bool trace, int vtype, bool a32);
 
 }  // namespace mpk

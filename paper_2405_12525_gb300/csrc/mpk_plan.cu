@@ -234,12 +234,12 @@ __global__ void k_lcol(int32_t n, const int32_t *rowlen, const int32_t *chunk_ro
 // shared memory when its entries fit a buffer and its widths fit the record.
 __global__ void k_chunk_records(int32_t nchunks, const int32_t *chunk_row, const int32_t *chunk_slice,
                                 const int64_t *slice_ptr, const int4 *ranges, int32_t stage_entries, const int32_t *win,
-                                int32_t *rec) {
+                                int32_t max_slices, int32_t *rec) {
     for (int32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < nchunks; c += gridDim.x * blockDim.x) {
         const int32_t sl0 = chunk_slice[c], sl1 = chunk_slice[c + 1], nsl = sl1 - sl0;
         const int64_t e0 = slice_ptr[sl0], e1 = slice_ptr[sl1];
         const int32_t cnt = (int32_t)(e1 - e0);
-        const int staged = kStageChunks && cnt > 0 && cnt <= stage_entries && nsl <= kRecSlices;
+        const int staged = kStageChunks && cnt > 0 && cnt <= stage_entries && nsl <= max_slices;
         int32_t *o = rec + (int64_t)kRecInts * c;
         o[0] = chunk_row[c];
         o[1] = chunk_row[c + 1];
@@ -252,14 +252,15 @@ __global__ void k_chunk_records(int32_t nchunks, const int32_t *chunk_row, const
         const int4 r0 = ranges[2 * c], r1 = ranges[2 * c + 1];
         o[8] = r0.x; o[9] = r0.y; o[10] = r0.z; o[11] = r0.w;
         o[12] = r1.x; o[13] = r1.y; o[14] = r1.z; o[15] = r1.w;
-        uint32_t wb[kRecSlices / 4] = {0, 0, 0, 0};
+        uint32_t wb[kRecSlicesWide / 4] = {0, 0, 0, 0, 0, 0, 0, 0};
         if (staged)
             for (int32_t q = 0; q < nsl; ++q) {
                 const uint32_t w = (uint32_t)((slice_ptr[sl0 + q + 1] - slice_ptr[sl0 + q]) >> 5);
                 wb[q >> 2] |= (w & 0xffu) << (8 * (q & 3));
             }
-        for (int q = 0; q < kRecSlices / 4; ++q) o[16 + q] = (int32_t)wb[q];
         for (int q = 0; q < 3 * kXWin; ++q) o[kRecWin + q] = win ? win[3 * kXWin * (int64_t)c + q] : 0;
+        // widths of slices 0..15, then (shapes without windows) of slices 16..31 over the windows
+        for (int q = 0; q < (win ? kRecSlices : kRecSlicesWide) / 4; ++q) o[16 + q] = (int32_t)wb[q];
     }
 }
 
@@ -364,7 +365,14 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         P->order = o->order;
         P->identity = (L == nullptr);
         P->chunk_rows = chunk_rows;
-        P->cache_bytes = o->cache_bytes ? o->cache_bytes : device_l2_bytes() / 4 * 3;
+        // Units of two slices a warp (block shape 4) are the planner's choice for binary32 sums
+        // over 2-byte values, one right-hand side and short rows (decided here from the mean row
+        // length, since the budget shapes the groups the slices are cut from); they want larger
+        // groups: measured at 256^3, p = 8, 1.575 / 1.486 / 1.459 / 1.468 ms at C = 96 / 128 /
+        // 160 / 192 MB.  Every other plan: three quarters of L2.
+        const bool two_slices = o->shape == 5 || (o->shape == 0 && o->accum == MPK_F32 && P->val_bytes == 2 &&
+                                                  o->nrhs == 1 && A->nnz <= 10 * (int64_t)A->n);
+        P->cache_bytes = o->cache_bytes ? o->cache_bytes : device_l2_bytes() / 4 * (two_slices ? 5 : 3);
         P->window = kSlotSkew * pmax + 1;
         P->group_budget = P->cache_bytes / P->window;
         P->wait_ns = o->wait_limit_ns ? o->wait_limit_ns : 2000000000LL;
@@ -540,8 +548,10 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         //      width, else unstaged (measured: 27-point stencils run 1.7x
         //      faster unstaged).  Shape 1's fewer, larger units beat shape 0 on the 3-D
         //      Laplacian (2.20 ms against 2.58 ms at 256^3, p = 8), since the per-unit work of
-        //      the control warp sets the pace; shapes 0 and 3 (input rows staged too) are taken
-        //      only when the options name them.
+        //      the control warp sets the pace; for the same reason binary32 sums over 2-byte
+        //      values take shape 4 (two slices a warp) when its slot holds 24 slices of the
+        //      mean width (1.459 against 1.622 ms at their best budgets); shapes 0 and 3 (input
+        //      rows staged too) are taken only when the options name them.
         if (o->shape < 0 || o->shape > kNumShapes) fail(MPK_ERR_INVALID, "shape must be in [0, %d]", kNumShapes);
         int fallback_shape = 0;
         bool try_x = false;
@@ -553,6 +563,7 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
                 return (int64_t)slices * P->padded <= (int64_t)kShapes[sh].stage_entries * std::max(NS, 1);
             };
             fallback_shape = (o->nrhs < 16 && fits(1, 6)) ? 1 : 2;  // up to 24 entries a row on average
+            if (two_slices && fits(4, 24)) fallback_shape = 4;      // up to 12 entries a row
             try_x = false;
         }
         const bool x_forced = o->shape - 1 == kShapeX;
@@ -581,7 +592,8 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
             if (attempt > 0 && P->shape == kShapeX) fail(MPK_ERR_UNSUPPORTED, "block shape 3 does not fit this plan");
             stage_entries = kShapes[P->shape].stage_entries;
             const int64_t chunk_entries = stage_entries > 0 ? stage_entries : INT64_MAX;
-            chunk_rows = o->chunk_rows ? o->chunk_rows : 32 * kShapes[P->shape].comp_warps;
+            chunk_rows = o->chunk_rows ? o->chunk_rows
+                                       : 32 * kShapes[P->shape].comp_warps * std::max(1, kShapes[P->shape].slices_per_warp);
             P->chunk_rows = chunk_rows;
 
             // ---- chunks: consecutive slices of one group, at most chunk_rows rows and at most
@@ -750,6 +762,9 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
                                          s));
             k_chunk_records<<<grid_n(NC), 256, 0, s>>>(NC, P->chunk_row, P->chunk_slice, P->slice_ptr, P->dep_ranges,
                                                       stage_entries, d_win.p,
+                                                      // slices a staged chunk may have: what the shape's
+                                                      // compute warps read widths for
+                                                      kShapes[P->shape].slices_per_warp > 1 ? kRecSlicesWide : kRecSlices,
                                                       reinterpret_cast<int32_t *>(P->chunk_rec));
             MPK_LAUNCHED();
             MPK_CUDA(cudaStreamSynchronize(s));

@@ -50,7 +50,7 @@ MATS = {
 
 @pytest.mark.parametrize("name", sorted(MATS))
 @pytest.mark.parametrize("vtype", ["f32", "bf16"])
-@pytest.mark.parametrize("engine,shape", [(0, 0), (0, 1), (0, 2), (0, 3), (2, 0)])
+@pytest.mark.parametrize("engine,shape", [(0, 0), (0, 1), (0, 2), (0, 3), (0, 5), (2, 0)])
 def test_powers_bit_exact(mpk, name, vtype, engine, shape):
     A = MATS[name]()
     vt = {"f32": mpk.MPK_F32, "bf16": mpk.MPK_BF16}[vtype]
@@ -174,3 +174,22 @@ def test_rejected_combinations(mpk):
     with pytest.raises(mpk.MpkError) as e:
         P.spmv_powers(torch.zeros((A.n, 1), dtype=torch.float64, device="cuda"), 2)
     assert e.value.status == 7
+
+
+def test_automatic_two_slice_shape_for_bfloat16(mpk):
+    # binary32 sums over bfloat16 values, one right-hand side, rows of 7 entries: the planner
+    # takes two slices a warp (shape index 4, 1024-row chunks) and a budget of 5/4 of L2; with
+    # float32 values it keeps shape 1; the powers equal the oracle's binary32 path
+    A = gen.laplacian_3d(40, 36, 30)
+    _, l2 = mpk.device_info()
+    for vt, shape, rows, frac in ((mpk.MPK_BF16, 4, 1024, 5), (mpk.MPK_F32, 1, 512, 3)):
+        dA = mpk.CsrMatrix.from_host(A, is_symmetric=True, value_type=vt)
+        L = mpk.build_levels(dA, 0)
+        P = mpk.plan(dA, L, p_max=8, order=mpk.ORDER_PLAN, accum=mpk.MPK_F32)
+        d = P.describe()
+        assert d["shape"] == shape and d["chunk_rows"] == rows and d["cache_bytes"] == l2 // 4 * frac
+        pe = L.perm.cpu().numpy()
+        X = gen.vector(A.n, 1, stream=409)
+        Y = P.apply(torch.from_numpy(np.ascontiguousarray(X[pe])).cuda(), 8, Y=_poisoned((9, A.n, 1)))
+        P.sync_status()
+        assert _bits_equal(Y.cpu().numpy(), oracle.mpk_acc32(_widened(dA), X, 8)[:, pe, :])

@@ -432,13 +432,14 @@ def test_apply_replays_from_cuda_graph(mpk):
         _check_powers(Ys, oracle.mpk(A, X, 6)[:, pe, :])
 
 
-@pytest.mark.parametrize("shape", [1, 2, 3, 4])
+@pytest.mark.parametrize("shape", [1, 2, 3, 4, 5])
 @pytest.mark.parametrize("name", ["lap3d_17x9x6", "lap2d_64", "band_3000", "int_nonsym_500", "xxz_10", "empty_rows",
                                   "disconnected", "single"])
 def test_apply_every_block_shape(mpk, shape, name):
     # the block shapes of the staged kernel (13 warps with 3072-entry slots, 16 warps with
-    # 4608, 14 warps reading entries from global memory, and input rows staged as well) give
-    # the same bits; shape 3 refuses a plan whose chunks read input rows beyond a slot
+    # 4608, 14 warps reading entries from global memory, input rows staged as well, and two
+    # slices a warp in 9216-entry slots) give the same bits; shape 3 refuses a plan whose
+    # chunks read input rows beyond a slot
     make, sym = MATRICES[name]
     A = make()
     dA = _dev(A, mpk, sym)
@@ -454,7 +455,28 @@ def test_apply_every_block_shape(mpk, shape, name):
     P.sync_status()
     _check_powers(Y, oracle.mpk(A, X, 7))
     with pytest.raises(mpk.MpkError):
-        mpk.plan(dA, L, p_max=3, shape=5)
+        mpk.plan(dA, L, p_max=3, shape=6)
+
+
+@pytest.mark.parametrize("m", [1, 2])
+@pytest.mark.parametrize("order", [0, 1])
+def test_two_slices_a_warp(mpk, m, order):
+    # block shape 4 (plan option 5): 1024-row chunks of up to 32 slices, two slices for each of
+    # the 16 compute warps, on matrices whose groups hold full chunks and ragged last ones
+    for A in (gen.laplacian_3d(40, 40, 40), gen.banded_random(60000, stream=176), gen.laplacian_2d(300, 211)):
+        dA = _dev(A, mpk, True)
+        L = mpk.build_levels(dA, 0)
+        pe = L.perm.cpu().numpy()
+        X = gen.vector(A.n, m, stream=177)
+        for cache, cr in ((0, 0), (2000000, 0), (0, 800)):
+            P = mpk.plan(dA, L, p_max=8, nrhs=m, cache_bytes=cache, order=order, chunk_rows=cr, shape=5)
+            d = P.describe()
+            assert d["shape"] == 4 and d["chunk_rows"] == (cr or 1024)
+            Xin = X if order == 0 else np.ascontiguousarray(X[pe])
+            Y = P.apply(torch.from_numpy(Xin).cuda(), 8, Y=_poisoned((9, A.n, m)))
+            P.sync_status()
+            Yo = oracle.mpk(A, X, 8)
+            _check_powers(Y, Yo if order == 0 else Yo[:, pe, :])
 
 
 @pytest.mark.parametrize("m", [1, 2])
