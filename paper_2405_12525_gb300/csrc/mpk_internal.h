@@ -181,11 +181,21 @@ struct BlockShape {
 #ifndef MPK_XS_CTL
 #define MPK_XS_CTL 1
 #endif
+// shape 4: compute warps, slot entries and slices a warp takes per unit (at most 32 slices a unit)
+#ifndef MPK_S4_WARPS
+#define MPK_S4_WARPS 16
+#endif
+#ifndef MPK_S4_ENTRIES
+#define MPK_S4_ENTRIES 9216
+#endif
+#ifndef MPK_S4_SPW
+#define MPK_S4_SPW 2
+#endif
 constexpr BlockShape kShapes[5] = {{13, 3072, 3, 2, 0, 1},
                                    {16, 4608, 2, 2, 0, 1},
                                    {14, 0, 2, 2, 0, 1},
                                    {MPK_XS_WARPS, MPK_XS_ENTRIES, MPK_XS_BLOCKS, MPK_XS_SLOTS, MPK_XS_WORDS, MPK_XS_CTL},
-                                   {16, 9216, 2, 2, 0, 1, 2}};
+                                   {MPK_S4_WARPS, MPK_S4_ENTRIES, 2, 2, 0, 1, MPK_S4_SPW}};
 constexpr int kNumShapes = 5;
 constexpr int kShapeX = 3;  // the shape that stages input rows
 // input-row windows of a chunk (shape 3): one per dependency range
@@ -216,6 +226,7 @@ constexpr int kRecWin = 8 + 2 * kDepRanges + kRecSlices / 4;  // first int of th
 constexpr int kRecInts = kRecWin + 3 * kXWin;
 static_assert(kRecInts <= 32, "a chunk record is read by one lane per int");
 static_assert(kRecWin + kRecSlicesWide / 4 - kRecSlices / 4 <= kRecInts, "wide widths in the window words");
+static_assert(MPK_S4_WARPS * MPK_S4_SPW <= kRecSlicesWide, "a unit of shape 4 has at most 32 slices");
 struct KArgs {
     // sliced matrix copy (plan order)
     const void *val;  // values of the matrix's value type (Plan::val_type)

@@ -21,6 +21,7 @@ template <int SH> struct Shape {
     static constexpr int XW = kShapes[SH].x_words;  // input-row words per slot (0: not staged)
     static constexpr bool X = XW > 0;
     static constexpr int SPW = kShapes[SH].slices_per_warp > 1 ? kShapes[SH].slices_per_warp : 1;
+    static constexpr int NW = SPW > 1 ? 8 : 4;  // width words of the chunk record it reads
 };
 // blocks per SM the register budget is set for (65536 registers per SM).  The single-vector
 // power kernel runs at the shape's own block count (shape 0: three blocks of 15 warps, 40
@@ -610,13 +611,13 @@ __device__ __forceinline__ void phase_b(const KArgs &a, int32_t epoch, const Pre
         }
         for (int sl = cwarp + kCompWarps; sl < u.nsl; sl += kCompWarps) {  // further slices (wide chunks)
             const int64_t r = (int64_t)u.row0 + 32 * sl + lane;
-            const int pre = slice_prefix<Shape<SH>::SPW * 4>(u.widths, sl);
+            const int pre = slice_prefix<Shape<SH>::NW>(u.widths, sl);
             if (r >= u.row1) continue;
             AT w[M];
             // a second slice of the warp (shapes of two slices a warp: all gathers of a batch at
             // once) or, on the other shapes, the rare chunk wider than the block
             constexpr int BS2 = Shape<SH>::SPW > 1 ? B : 2;
-            row_sum<M, BS2, AT>(sval, scol, 32 * pre + lane, slice_width<Shape<SH>::SPW * 4>(u.widths, sl), xacc, w);
+            row_sum<M, BS2, AT>(sval, scol, 32 * pre + lane, slice_width<Shape<SH>::NW>(u.widths, sl), xacc, w);
             row_epilogue<M, MODE, AT>(a, k, r, w, xin);
         }
     } else {  // entries in global memory (chunk too large to stage): the slot holds nothing
@@ -1032,7 +1033,7 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
                 u.staged = __shfl_sync(0xffffffffu, r_cur, 6);
                 u.nsl = __shfl_sync(0xffffffffu, r_cur, 7);
 #pragma unroll
-                for (int w = 0; w < 4 * Shape<SH>::SPW; ++w) u.widths[w] = __shfl_sync(0xffffffffu, r_cur, 16 + w);
+                for (int w = 0; w < Shape<SH>::NW; ++w) u.widths[w] = __shfl_sync(0xffffffffu, r_cur, 16 + w);
                 const int k = un & 31;
                 XCopy xc{0, 0, 0, 0, 0};
                 uint32_t xbytes = 0;
@@ -1152,7 +1153,7 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
             u.staged = __shfl_sync(0xffffffffu, r_cur, 6);
             u.nsl = __shfl_sync(0xffffffffu, r_cur, 7);
 #pragma unroll
-            for (int q = 0; q < 4 * Shape<SH>::SPW; ++q) u.widths[q] = __shfl_sync(0xffffffffu, r_cur, 16 + q);
+            for (int q = 0; q < Shape<SH>::NW; ++q) u.widths[q] = __shfl_sync(0xffffffffu, r_cur, 16 + q);
             int dlo[kDepRanges], dlen[kDepRanges];
             const int total = dep_ranges_of(r_cur, dlo, dlen);
             const int k = u.unit & 31;
@@ -1366,7 +1367,7 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
                 if (tr && lane == 0) tr_add(13, clock64() - c1);
             } else {
                 const long long c0 = tr ? clock64() : 0;
-                phase_a<M, (kStageEntries > 0), AT, Shape<SH>::SPW * 4>(a, s_u[b], b,
+                phase_a<M, (kStageEntries > 0), AT, Shape<SH>::NW>(a, s_u[b], b,
                                                      kStageCol ? scol0 + b * kStageEntries : a.col + s_u[b].ebase, cw,
                                                      lane, pf);
                 if (tr) {  // wait for the gathers (integer ops only) to split the unit time
