@@ -68,8 +68,8 @@ extern "C" mpk_status mpk_batch_plan(const mpk_csr *mats, int32_t count, const i
     const int32_t N = inst_row.back();
     const int64_t NNZ = nnz_off.back();
     // the direct sum in CSR: row pointers and columns shifted by each block's offsets
-    Tmp<int32_t> rp((int64_t)N + 1), ci(std::max<int64_t>(NNZ, 1));
-    Tmp<unsigned char> va(std::max<int64_t>(NNZ * vb, 1));
+    Tmp<int32_t> rp((int64_t)N + 1, s), ci(std::max<int64_t>(NNZ, 1), s);
+    Tmp<unsigned char> va(std::max<int64_t>(NNZ * vb, 1), s);
     for (int32_t i = 0; i < count; ++i) {
         const mpk_csr &A = mats[i];
         if (A.n > 0)

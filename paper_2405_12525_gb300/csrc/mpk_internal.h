@@ -64,14 +64,16 @@ struct Arena {
     void release();
 };
 
-// Temporary device buffer freed on scope exit (not counted in a plan).
+// Temporary device buffer, allocated and freed in the order of stream s (stream-ordered pool:
+// no device-wide synchronisation as with cudaFree), freed on scope exit (not counted in a plan).
 template <class T> struct Tmp {
     T *p = nullptr;
-    explicit Tmp(int64_t n) {
-        if (n > 0) MPK_CUDA(cudaMalloc(&p, (size_t)n * sizeof(T)));
+    cudaStream_t s = nullptr;
+    Tmp(int64_t n, cudaStream_t stream) : s(stream) {
+        if (n > 0) MPK_CUDA(cudaMallocAsync(reinterpret_cast<void **>(&p), (size_t)n * sizeof(T), s));
     }
     ~Tmp() {
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, s);
     }
     Tmp(const Tmp &) = delete;
     Tmp &operator=(const Tmp &) = delete;

@@ -37,7 +37,7 @@ void validate_csr(const mpk_csr *A, cudaStream_t s) {
     if (A->n == 0) return;
     if (!A->row_ptr || (A->nnz > 0 && (!A->col || !A->val)))
         fail(MPK_ERR_INVALID, "NULL CSR array");
-    Tmp<int32_t> err(2);
+    Tmp<int32_t> err(2, s);
     MPK_CUDA(cudaMemsetAsync(err.p, 0, 2 * sizeof(int32_t), s));
     int g = (int)((A->n + 255) / 256);
     if (g > device_sms() * 16) g = device_sms() * 16;
@@ -272,10 +272,10 @@ Levels *build_levels(const mpk_csr *A, int32_t root, cudaStream_t s, const std::
             return L;
         }
         // pattern of A^T without the diagonal, only when A is not declared symmetric
-        Tmp<int32_t> tp(A->is_symmetric ? 0 : (int64_t)n + 1);
-        Tmp<int32_t> tci(A->is_symmetric ? 0 : (int64_t)A->nnz);
+        Tmp<int32_t> tp(A->is_symmetric ? 0 : (int64_t)n + 1, s);
+        Tmp<int32_t> tci(A->is_symmetric ? 0 : (int64_t)A->nnz, s);
         if (!A->is_symmetric) {
-            Tmp<int32_t> cnt((int64_t)n + 1);
+            Tmp<int32_t> cnt((int64_t)n + 1, s);
             MPK_CUDA(cudaMemsetAsync(cnt.p, 0, sizeof(int32_t) * ((size_t)n + 1), s));
             k_tcount<<<grid_n(n), 256, 0, s>>>(n, A->row_ptr, A->col, cnt.p);
             MPK_LAUNCHED();
@@ -286,12 +286,12 @@ Levels *build_levels(const mpk_csr *A, int32_t root, cudaStream_t s, const std::
             MPK_CUDA(cudaStreamSynchronize(s));
         }
         // level-synchronous BFS; queue holds the levels back to back
-        Tmp<int32_t> queue(n);
+        Tmp<int32_t> queue(n, s);
         MPK_CUDA(cudaMemsetAsync(L->level_of, 0xff, sizeof(int32_t) * (size_t)n, s));
         int64_t head = 0, tail = 1;
         if (roots) {
             const int32_t nr = (int32_t)roots->size();
-            Tmp<int32_t> d_roots(nr);
+            Tmp<int32_t> d_roots(nr, s);
             MPK_CUDA(cudaMemcpyAsync(d_roots.p, roots->data(), sizeof(int32_t) * (size_t)nr, cudaMemcpyHostToDevice, s));
             k_set_roots<<<grid_n(nr), 256, 0, s>>>(L->level_of, queue.p, d_roots.p, nr);
             MPK_LAUNCHED();
@@ -302,7 +302,7 @@ Levels *build_levels(const mpk_csr *A, int32_t root, cudaStream_t s, const std::
             MPK_LAUNCHED();
         }
         // the levels, in one cooperative launch (every block resident)
-        Tmp<BfsState> st(1);
+        Tmp<BfsState> st(1, s);
         MPK_CUDA(cudaMemsetAsync(st.p, 0, sizeof(BfsState), s));
         int per_sm = 0;
         MPK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs_all, 256, 0));
@@ -329,7 +329,7 @@ Levels *build_levels(const mpk_csr *A, int32_t root, cudaStream_t s, const std::
         const int32_t nl = lev + 1;
         L->num_levels = nl;
         // permutation: stable sort of (level, id) pairs with ids ascending as input order
-        Tmp<uint32_t> k0(n), v0(n), k1(n), v1(n);
+        Tmp<uint32_t> k0(n, s), v0(n, s), k1(n, s), v1(n, s);
         MPK_CUDA(cudaMemcpyAsync(k0.p, L->level_of, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToDevice, s));
         iota_i32(reinterpret_cast<int32_t *>(v0.p), n, s);
         int bits = 0;

@@ -303,7 +303,7 @@ void export_csr(const Plan &P, int32_t *rp, int32_t *ci, double *va, cudaStream_
     if (!rp || (P.nnz > 0 && (!ci || !va))) fail(MPK_ERR_INVALID, "NULL output array");
     exclusive_scan(P.rowlen, rp, P.n, s);
     if (P.n == 0) return;
-    Tmp<int32_t> cor(P.n);
+    Tmp<int32_t> cor(P.n, s);
     k_chunk_of_row<<<grid_n(P.num_chunks * 256), 256, 0, s>>>(P.chunk_row, P.num_chunks, cor.p);
     MPK_LAUNCHED();
 #define EXPORT(T)                                                                                              \
@@ -411,9 +411,9 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
             g_row = {0, n};
         } else if (n > 0) {
             const int32_t NL = L->num_levels;
-            Tmp<int32_t> prp((int64_t)n + 1);
+            Tmp<int32_t> prp((int64_t)n + 1, s);
             exclusive_scan(P->rowlen, prp.p, n, s);
-            Tmp<int32_t> lvl_nnz((int64_t)NL + 1);
+            Tmp<int32_t> lvl_nnz((int64_t)NL + 1, s);
             k_gather_i32<<<grid_n(NL + 1), 256, 0, s>>>(prp.p, L->level_ptr, NL + 1, lvl_nnz.p);
             MPK_LAUNCHED();
             std::vector<int32_t> h_nz((size_t)NL + 1);
@@ -529,8 +529,8 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         g_slice.push_back((int32_t)s_row.size() - 1);
         const int32_t NS = (int32_t)s_row.size() - 1;
         P->num_slices = NS;
-        Tmp<int32_t> d_srow((int64_t)NS + 1);
-        Tmp<int32_t> d_width(NS);
+        Tmp<int32_t> d_srow((int64_t)NS + 1, s);
+        Tmp<int32_t> d_width(NS, s);
         MPK_CUDA(cudaMemcpyAsync(d_srow.p, s_row.data(), sizeof(int32_t) * ((size_t)NS + 1), cudaMemcpyHostToDevice, s));
         if (NS > 0) {
             k_slice_width<<<grid_n(NS), 256, 0, s>>>(d_srow.p, NS, P->rowlen, d_width.p);
@@ -578,7 +578,7 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
         }
         P->slice_ptr = P->arena.alloc_n<int64_t>((int64_t)NS + 1);
         MPK_CUDA(cudaMemcpyAsync(P->slice_ptr, sptr.data(), sizeof(int64_t) * ((size_t)NS + 1), cudaMemcpyHostToDevice, s));
-        Tmp<int32_t> cor(n);
+        Tmp<int32_t> cor(n, s);
         P->val = P->arena.alloc((P->padded + 32) * P->val_bytes);
         P->col = P->arena.alloc_n<int32_t>(P->padded + 32);
         MPK_CUDA(cudaMemsetAsync(P->val, 0, (size_t)P->val_bytes * (size_t)(P->padded + 32), s));  // +0 in every type
@@ -636,7 +636,7 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
     k_fill<T><<<grid_n(n), 256, 0, s>>>(n, A->row_ptr, A->col, static_cast<const T *>(A->val), P->perm,    \
                                         P->iperm, P->chunk_row, P->chunk_slice, cor.p, P->slice_ptr,         \
                                         static_cast<T *>(P->val), P->col, P->dep, A->is_symmetric ? 1 : 0, special.p)
-                Tmp<int32_t> special(1);
+                Tmp<int32_t> special(1, s);
                 MPK_CUDA(cudaMemsetAsync(special.p, 0, sizeof(int32_t), s));
                 if (P->val_type == MPK_F64)
                     FILL(double);
@@ -664,8 +664,8 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
                 for (int32_t c = 0; c < NC; ++c) woff[c + 1] = woff[c] + (hull[c].y - hull[c].x + 32) / 32;
                 const int64_t words = woff[NC];
                 if (words <= ((int64_t)1 << 27)) {
-                    Tmp<int64_t> d_woff((int64_t)NC + 1);
-                    Tmp<uint32_t> d_bits(words);
+                    Tmp<int64_t> d_woff((int64_t)NC + 1, s);
+                    Tmp<uint32_t> d_bits(words, s);
                     MPK_CUDA(cudaMemcpyAsync(d_woff.p, woff.data(), sizeof(int64_t) * ((size_t)NC + 1),
                                              cudaMemcpyHostToDevice, s));
                     MPK_CUDA(cudaMemsetAsync(d_bits.p, 0, sizeof(uint32_t) * (size_t)words, s));
@@ -694,7 +694,7 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
                 bool ok = NC > 0;
                 h_win.assign((size_t)3 * kXWin * std::max(NC, 1), 0);
                 if (ok) {
-                    Tmp<int2> d_xw((int64_t)kXWin * NC);
+                    Tmp<int2> d_xw((int64_t)kXWin * NC, s);
                     std::vector<int2> xw((size_t)kXWin * NC, make_int2(INT_MAX, -1));
                     MPK_CUDA(cudaMemcpyAsync(d_xw.p, xw.data(), sizeof(int2) * xw.size(), cudaMemcpyHostToDevice, s));
                     k_xwin<<<grid_n(n), 256, 0, s>>>(n, P->rowlen, P->chunk_row, P->chunk_slice, cor.p, P->slice_ptr,
@@ -741,7 +741,7 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
                     h_win.clear();
                     continue;
                 }
-                Tmp<int32_t> d_win((int64_t)h_win.size());
+                Tmp<int32_t> d_win((int64_t)h_win.size(), s);
                 MPK_CUDA(cudaMemcpyAsync(d_win.p, h_win.data(), sizeof(int32_t) * h_win.size(), cudaMemcpyHostToDevice,
                                          s));
                 P->lcol = P->arena.alloc_n<uint16_t>(P->padded + 32);
@@ -756,7 +756,7 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
 
         P->chunk_rec = reinterpret_cast<int4 *>(P->arena.alloc_n<int32_t>((int64_t)kRecInts * (NC > 0 ? NC : 1)));
         if (NC > 0) {
-            Tmp<int32_t> d_win(P->shape == kShapeX ? (int64_t)h_win.size() : 0);
+            Tmp<int32_t> d_win(P->shape == kShapeX ? (int64_t)h_win.size() : 0, s);
             if (P->shape == kShapeX)
                 MPK_CUDA(cudaMemcpyAsync(d_win.p, h_win.data(), sizeof(int32_t) * h_win.size(), cudaMemcpyHostToDevice,
                                          s));

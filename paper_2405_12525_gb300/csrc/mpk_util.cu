@@ -179,7 +179,7 @@ template <class T> static void scan_impl(const T *in, T *out, int64_t n, cudaStr
         MPK_LAUNCHED();
         return;
     }
-    Tmp<T> totals(tiles + 1);
+    Tmp<T> totals(tiles + 1, s);
     k_scan_totals<T><<<(unsigned)tiles, SCAN_BS, 0, s>>>(in, n, totals.p);
     MPK_LAUNCHED();
     scan_impl<T>(totals.p, totals.p, tiles, s);
@@ -265,7 +265,7 @@ void radix_sort_pairs(uint32_t *keys, uint32_t *vals, uint32_t *keys_tmp, uint32
     if (n > 0 && key_bits > 0) {
         const int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
         if (ntiles * 256 >= (int64_t)1 << 31) fail(MPK_ERR_TOO_LARGE, "radix sort: too many tiles");
-        Tmp<int32_t> counts(ntiles * 256 + 1);
+        Tmp<int32_t> counts(ntiles * 256 + 1, s);
         for (int shift = 0; shift < key_bits; shift += 8) {
             k_radix_hist<<<(unsigned)ntiles, RS_BS, 0, s>>>(ka, n, shift, counts.p, ntiles);
             MPK_LAUNCHED();
