@@ -37,17 +37,17 @@ sys.path.insert(0, ROOT)
 METRIC = "Level-blocked MPK Gflop/s vs p×CSR SpMV on 1 GB300; serving p50/p99 latency"
 DFMA_LANES_PER_CLK_PER_SM = 2  # GB300's FP64 FMA issue rate per SM (unit count of the roof)
 SM_MAX_MHZ_FALLBACK = 2070.0   # used only if nvidia-smi gives no clock
-# L2 hit rate of the level-blocked kernel from the committed ncu capture (context only)
-L2_PROFILE = os.path.join(ROOT, "profiles", "k_mpk_128cube_full.md")
 # the level-blocked kernel, its tunables and the planner that cuts its chunks
 KERNEL_SOURCES = [os.path.join(ROOT, "paper_2405_12525_gb300", "csrc", f)
                   for f in ("mpk_kernel_dev.cuh", "mpk_internal.h", "mpk_plan.cu")]
 TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "k_mpk_traffic.json")
 
 
-def measured_traffic(side: int):
-    """DRAM bytes per launch of the level-blocked kernel from the committed ncu record, or None
-    when the record is missing, was taken on another workload, or the kernel source changed."""
+def measured_profile(side: int, accum: str):
+    """The committed ncu record of the level-blocked kernel for one accumulation ("f64": binary64
+    sums over binary64 values; "f32": binary32 sums over bfloat16 values): DRAM bytes per launch
+    and L2 hit rate.  None when the record is missing, was taken on another workload, or the
+    kernel source changed since."""
     try:
         rec = json.load(open(TRAFFIC_RECORD))
         h = hashlib.sha256()
@@ -56,9 +56,10 @@ def measured_traffic(side: int):
         sha = h.hexdigest()
     except (OSError, ValueError):
         return None
-    if rec.get("kernel_source_sha256") != sha or rec.get("side") != side:
+    case = rec.get("records", {}).get(accum)
+    if rec.get("kernel_source_sha256") != sha or not case or case.get("side") != side:
         return None
-    return rec.get("dram_bytes_per_launch")
+    return case
 
 
 def parse():
@@ -251,16 +252,6 @@ def device_roofs(mpk, torch):
         del buf
     torch.cuda.empty_cache()
     return out
-
-
-def l2_hit_rate_from_profile():
-    try:
-        for ln in open(L2_PROFILE):
-            if "lts__t_sector_hit_rate" in ln:
-                return float(ln.split("|")[2].strip().rstrip("%").split()[0]) / 100.0
-    except (OSError, ValueError, IndexError):
-        return None
-    return None
 
 
 def cheb_workload(L: int, degree: int):
@@ -1028,9 +1019,15 @@ def main():
     roof_blocked_ms = max(t_hbm, t_l2) * 1e3
     plain_bytes = p * (a_bytes + (4.0 if acc32 else 8.0) * A.n + out_row * A.n)
     peak_nominal = roofs["sms"] * DFMA_LANES_PER_CLK_PER_SM * 2 * mhz * 1e6 / 1e12  # TFLOP/s
+    # DRAM bytes per launch from one ncu capture of this kernel source (null once it has changed)
+    prof = measured_profile(args.side, "f32" if acc32 else "f64")
+    if prof and (prof.get("values") != args.values or prof.get("shape") != desc["shape"] or args.cache_mb
+                 or args.split or args.p != prof.get("p")):
+        prof = None  # the capture was taken on the default plan of this workload only
+    traffic = prof.get("dram_bytes_per_launch") if prof else None
     if not acc32:
         roofline = {"bound": "alu", "achieved": achieved, "peak": peak_nominal, "unit": "TFLOP/s",
-                    "frac": achieved / peak_nominal, "traffic": measured_traffic(args.side),
+                    "frac": achieved / peak_nominal, "traffic": traffic,
                     "peak_note": f"{roofs['sms']} SMs x {DFMA_LANES_PER_CLK_PER_SM} FP64 FMA lanes/clk x 2 flop x "
                                  f"{mhz:.0f} MHz (median SM clock sampled during the timed region)",
                     "measured_fp64_peak": roofs["fp64_fma_tflops_measured"],
@@ -1040,7 +1037,7 @@ def main():
     else:
         achieved_gbs = hbm_bytes / (ms * 1e-3) / 1e9
         roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": roofs["hbm_load_gbs"], "unit": "GB/s",
-                    "frac": achieved_gbs / roofs["hbm_load_gbs"], "traffic": None,
+                    "frac": achieved_gbs / roofs["hbm_load_gbs"], "traffic": traffic,
                     "peak_note": "load bandwidth from HBM measured in this process (mpk_probe_load, 2 GiB)",
                     "achieved_note": "algorithmic HBM bytes of one apply (A once, X once, p binary64 powers and "
                                      "their binary32 copies written) / kernel time"}
@@ -1055,7 +1052,7 @@ def main():
         "effective_bandwidth_gbs": p * a_bytes / (ms * 1e-3) / 1e9,
         "effective_bandwidth_note": "p x matrix bytes / kernel time",
         "algorithmic_hbm_bytes": hbm_bytes, "algorithmic_l2_bytes": l2_bytes,
-        "l2_hit_rate_profile": l2_hit_rate_from_profile(),
+        "l2_hit_rate_profile": prof.get("l2_hit_rate") if prof else None,
         "device": roofs})
     if rank == 0:
         line = {

@@ -359,8 +359,8 @@ Plan *build_plan(const mpk_csr *A, const Levels *L, const mpk_plan_opts *o, cuda
             if (o->engine == MPK_ENGINE_WARP || o->trace || o->level_capped || inst_row != nullptr ||
                 o->shape - 1 == kShapeX)
                 fail(MPK_ERR_UNSUPPORTED,
-                     "binary32 accumulation runs on the staged engine (shapes 0-2) or the sweep engine, without "
-                     "trace, level caps or batching");
+                     "binary32 accumulation runs on the staged engine (any shape but the X-staged one) or the "
+                     "sweep engine, without trace, level caps or batching");
         }
         P->order = o->order;
         P->identity = (L == nullptr);

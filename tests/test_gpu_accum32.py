@@ -193,3 +193,55 @@ def test_automatic_two_slice_shape_for_bfloat16(mpk):
         Y = P.apply(torch.from_numpy(np.ascontiguousarray(X[pe])).cuda(), 8, Y=_poisoned((9, A.n, 1)))
         P.sync_status()
         assert _bits_equal(Y.cpu().numpy(), oracle.mpk_acc32(_widened(dA), X, 8)[:, pe, :])
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_two_slice_shape_on_every_path(mpk, order):
+    # the planner's two-slice shape (bfloat16 values, binary32 sums): powers with split levels,
+    # the Chebyshev recurrence (real and complex coefficients, the second slice of a warp
+    # through the recurrence's epilogue), in both orders, against the oracle's binary32 path
+    A = gen.laplacian_3d(40, 36, 30)
+    dA = mpk.CsrMatrix.from_host(A, is_symmetric=True, value_type=mpk.MPK_BF16)
+    Aw = _widened(dA)
+    L = mpk.build_levels(dA, 0)
+    _, pe, ip, _ = oracle.levels(A, 0)
+    X = gen.vector(A.n, 2, stream=411)
+    Xin = torch.from_numpy(np.ascontiguousarray(X if order == 0 else X[pe])).cuda()
+    for split in (False, True):
+        P = mpk.plan(dA, L, p_max=8, nrhs=1, order=order, accum=mpk.MPK_F32, split_levels=split, shape=5,
+                     cache_bytes=0 if not split else 4 << 20)
+        assert P.describe()["shape"] == 4
+        Y = P.apply(Xin[:, :1].contiguous(), 8, Y=_poisoned((9, A.n, 1)))
+        P.sync_status()
+        want = oracle.mpk_acc32(Aw, X[:, :1], 8)
+        assert _bits_equal(Y.cpu().numpy(), want if order == 0 else want[:, pe, :])
+    lo, hi = gen.gershgorin_bounds(A)
+    scale, shift = (hi - lo) / 2 * 1.01, (hi + lo) / 2
+    P = mpk.plan(dA, L, p_max=8, nrhs=2, order=order, accum=mpk.MPK_F32, shape=5)
+    assert P.describe()["shape"] == 4
+    deg = 21
+    cr = gen.uniform(gen.derive_seed(412), deg + 1)
+    ci = gen.uniform(gen.derive_seed(413), deg + 1)
+    for cim in (None, ci):
+        got = P.cheb_filter(Xin, deg, cr, cim, scale=scale, shift=shift).cpu().numpy()
+        P.sync_status()
+        want = oracle.cheb_acc32(Aw, X, deg, cr, cim, scale=scale, shift=shift)
+        assert _bits_equal(got[ip] if order == 1 else got, want)
+
+
+def test_two_slice_shape_without_allocation(mpk):
+    A = gen.laplacian_3d(40, 36, 30)
+    dA = mpk.CsrMatrix.from_host(A, is_symmetric=True, value_type=mpk.MPK_BF16)
+    L = mpk.build_levels(dA, 0)
+    P = mpk.plan(dA, L, p_max=8, order=mpk.ORDER_PLAN, accum=mpk.MPK_F32)
+    assert P.describe()["shape"] == 4
+    pe = L.perm.cpu().numpy()
+    X = gen.vector(A.n, 1, stream=414)
+    Xp = torch.from_numpy(np.ascontiguousarray(X[pe])).cuda()
+    want = P.apply(Xp, 8)
+    P.sync_status()
+    Y = _poisoned((9, A.n, 1))
+    status = torch.full((1,), -1, dtype=torch.int32, device="cuda")
+    P.apply_noalloc(Xp, 8, Y, status=status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == 0 and torch.equal(Y, want)
