@@ -124,6 +124,21 @@ __device__ __forceinline__ void bulk_g2s_addr(uint32_t dst, uint64_t src, uint32
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
     bulk_g2s_addr(smem_u32(dst), (uint64_t)src, bytes, bar);
 }
+// The same copy with an L2 priority: evict_first marks the lines the first to leave L2 (the
+// last use of data inside a launch); otherwise the default priority
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar, bool evict_first) {
+    if (!evict_first) {
+        bulk_g2s(dst, src, bytes, bar);
+        return;
+    }
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            smem_u32(dst)),
+        "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
+        : "memory");
+}
 
 // Entries whose x loads are issued together before their FMAs.
 template <int M> struct Batch {
@@ -342,8 +357,16 @@ __device__ __forceinline__ void row_epilogue_loaded(const KArgs &a, int k, int64
             }
         }
     } else {
+        if (!A32 && k == a.p_launch) {
+            // the launch's last power is not read again here: streaming stores, so that it does
+            // not push out of L2 the groups still in their reuse window (measured at 256^3,
+            // p = 8: 0.8 % faster with binary64 sums, 3 % slower with binary32 sums)
 #pragma unroll
-        for (int i = 0; i < M; ++i) y[i] = w[i];
+            for (int i = 0; i < M; ++i) __stcs(y + i, w[i]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < M; ++i) y[i] = w[i];
+        }
         if constexpr (A32) {
 #pragma unroll
             for (int i = 0; i < M; ++i) sh[i] = (float)wa[i];
@@ -1066,12 +1089,16 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                         constexpr uint32_t cb = XS ? 2u : (kStageCol ? 4u : 0u);
                         mbar_expect_tx_only(&s_full[b], (uint32_t)u.ecount * (uint32_t)(sizeof(T) + cb) + xbytes);
+                        // the launch's last power is the last use of the unit's entries
+                        const bool last_use = (u.unit & 31) == a.p_launch;
                         bulk_g2s(sval0 + b * kStageEntries, static_cast<const T *>(a.val) + u.ebase,
-                                 (uint32_t)(u.ecount * sizeof(T)), &s_full[b]);
+                                 (uint32_t)(u.ecount * sizeof(T)), &s_full[b], last_use);
                         if constexpr (XS)
-                            bulk_g2s(slc0 + b * kStageEntries, a.lcol + u.ebase, (uint32_t)u.ecount * 2u, &s_full[b]);
+                            bulk_g2s(slc0 + b * kStageEntries, a.lcol + u.ebase, (uint32_t)u.ecount * 2u, &s_full[b],
+                                     last_use);
                         else if (kStageCol)
-                            bulk_g2s(scol0 + b * kStageEntries, a.col + u.ebase, (uint32_t)u.ecount * 4u, &s_full[b]);
+                            bulk_g2s(scol0 + b * kStageEntries, a.col + u.ebase, (uint32_t)u.ecount * 4u, &s_full[b],
+                                     last_use);
                     }
                 }
                 if constexpr (XS) {
@@ -1235,12 +1262,19 @@ __global__ void __launch_bounds__(Shape<SH>::BS, (MpkOcc<M, MODE, TRACE, SH>::bl
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     constexpr uint32_t cb = XS ? 2u : (kStageCol ? 4u : 0u);
                     mbar_expect_tx_only(&s_full[b], (uint32_t)u.ecount * (uint32_t)(sizeof(T) + cb) + xbytes);
+                    // the launch's last power is the last use of the unit's entries: they are
+                    // copied with the evict_first priority, so that the groups still in their
+                    // reuse window keep their L2 lines (measured at 256^3, p = 8: 1.1 % faster
+                    // with binary64 sums, 0.6 % with binary32 sums)
+                    const bool last_use = (u.unit & 31) == a.p_launch;
                     bulk_g2s(sval0 + b * kStageEntries, static_cast<const T *>(a.val) + u.ebase,
-                             (uint32_t)(u.ecount * sizeof(T)), &s_full[b]);
+                             (uint32_t)(u.ecount * sizeof(T)), &s_full[b], last_use);
                     if constexpr (XS)
-                        bulk_g2s(slc0 + b * kStageEntries, a.lcol + u.ebase, (uint32_t)u.ecount * 2u, &s_full[b]);
+                        bulk_g2s(slc0 + b * kStageEntries, a.lcol + u.ebase, (uint32_t)u.ecount * 2u, &s_full[b],
+                                 last_use);
                     else if (kStageCol)
-                        bulk_g2s(scol0 + b * kStageEntries, a.col + u.ebase, (uint32_t)u.ecount * 4u, &s_full[b]);
+                        bulk_g2s(scol0 + b * kStageEntries, a.col + u.ebase, (uint32_t)u.ecount * 4u, &s_full[b],
+                                 last_use);
                 }
             }
             if (tr && lane == 0) tr_add(8, clock64() - c2);
