@@ -252,6 +252,22 @@ void mpk_plan_destroy(mpk_plan_t *P);
  * ------------------------------------------------------------------------------------- */
 mpk_status mpk_apply(const mpk_plan_t *P, const double *X, int32_t p, double *Y, mpk_stream stream);
 
+/* mpk_apply_host: mpk_apply with X and Y in host memory (Sec. 3's powers, the same bits as
+ * mpk_apply).  X_host: n x m doubles (host, any host memory; pinned memory keeps the copy
+ * asynchronous); Y_host: (p+1) x n x m doubles (host, page-locked: cudaHostAlloc or
+ * cudaHostRegister, else MPK_ERR_INVALID), in the plan's order; 0 <= p <= p_max.  One copy
+ * takes X to the device (the plan's workspace, no allocation).  With MPK_ORDER_PLAN (or no
+ * levels), the staged engine and nrhs 1, the kernel stores every power's rows into Y_host as
+ * its units finish, so the transfer to the host overlaps the wavefront; other plan-order plans
+ * compute on the device and copy the p+1 blocks afterwards (level-capped plans need the first
+ * case, else MPK_ERR_UNSUPPORTED).  With MPK_ORDER_ORIGINAL the powers are written through
+ * the permutation straight into Y_host after the kernel (a temporary device copy of X is
+ * allocated in stream order).  Asynchronous on `stream`: Y_host is complete when the stream
+ * is.  Y_host must not overlap X_host.  Not for batch plans (MPK_ERR_INVALID); not safe to run
+ * concurrently with another call on the same plan. */
+mpk_status mpk_apply_host(const mpk_plan_t *P, const double *X_host, int32_t p, double *Y_host,
+                          mpk_stream stream);
+
 /* mpk_apply_noalloc: mpk_apply for callers that must not allocate device memory while the
  * call runs (the paper has no counterpart).  Such callers include code running while a
  * device allocator is locked or must keep a fixed footprint, and latency-critical loops that

@@ -38,7 +38,7 @@ EXPORTED_SYMBOLS = [
     "mpk_status_string", "mpk_last_error", "mpk_debug_drop_release", "mpk_read_trace", "mpk_apply_noalloc",
     "mpk_widen_values", "mpk_batch_plan", "mpk_batch_apply", "mpk_batch_describe", "mpk_batch_workspace",
     "mpk_build_levels_from", "mpk_spmv_rows", "mpk_gather_rows", "mpk_spmv_rows_multi", "mpk_copy_rows",
-    "mpk_cheb_state_bytes", "mpk_cheb_begin", "mpk_cheb_advance", "mpk_cheb_finish",
+    "mpk_cheb_state_bytes", "mpk_cheb_begin", "mpk_cheb_advance", "mpk_cheb_finish", "mpk_apply_host",
 ]
 MAX_ROW_SEGMENTS = 32
 
@@ -100,6 +100,7 @@ def load():
         "mpk_plan_describe": [vp, C.POINTER(_Desc)],
         "mpk_plan_export_csr": [vp, vp, vp, vp, vp],
         "mpk_apply": [vp, vp, i32, vp, vp],
+        "mpk_apply_host": [vp, vp, i32, vp, vp],
         "mpk_spmv_powers": [vp, vp, i32, vp, vp],
         "mpk_cheb_filter": [vp, vp, i32, vp, vp, dbl, dbl, vp, vp],
         "mpk_sync_status": [vp, vp],
@@ -395,6 +396,25 @@ class Plan:
             Y = torch.empty((p + 1, self.n, self.nrhs), dtype=torch.float64, device=X.device)
         self._out_block(Y, X, p + 1)
         _check(self._lib.mpk_apply(self._h, _ptr(X), int(p), _ptr(Y), _stream(stream)))
+        return Y
+
+    def apply_host(self, X, p: int, Y=None, stream=None):
+        """mpk_apply with X and Y in host memory: X an n x nrhs float64 CPU tensor, Y a
+        (p+1) x n x nrhs float64 pinned CPU tensor (allocated pinned if not given), in the
+        plan's order.  Asynchronous on the stream: Y is complete when the stream is."""
+        torch = _torch()
+        if X.dtype != torch.float64 or X.is_cuda or not X.is_contiguous():
+            raise TypeError("X must be a contiguous float64 CPU tensor")
+        if X.numel() != self.n * self.nrhs:
+            raise ValueError(f"X has {X.numel()} elements, plan wants n*nrhs = {self.n * self.nrhs}")
+        if Y is None:
+            Y = torch.empty((p + 1, self.n, self.nrhs), dtype=torch.float64).pin_memory()
+        if Y.dtype != torch.float64 or Y.is_cuda or not Y.is_contiguous() or not Y.is_pinned():
+            raise TypeError("Y must be a contiguous float64 pinned CPU tensor")
+        if Y.numel() < (p + 1) * self.n * self.nrhs:
+            raise ValueError(f"Y has {Y.numel()} elements, the call writes {p + 1} x n x nrhs = "
+                             f"{(p + 1) * self.n * self.nrhs}")
+        _check(self._lib.mpk_apply_host(self._h, _ptr(X), int(p), _ptr(Y), _stream(stream)))
         return Y
 
     def apply_noalloc(self, X, p: int, Y, status=None, stream=None):

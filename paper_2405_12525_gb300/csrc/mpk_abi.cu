@@ -235,6 +235,73 @@ extern "C" mpk_status mpk_apply(const mpk_plan_t *Ph, const double *X, int32_t p
     MPK_GUARD_END
 }
 
+extern "C" mpk_status mpk_apply_host(const mpk_plan_t *Ph, const double *X_host, int32_t p, double *Y_host,
+                                     mpk_stream stream) {
+    MPK_GUARD_BEGIN
+    check_apply_args(Ph, X_host, p, Y_host);
+    Plan &P = *const_cast<Plan *>(Ph->impl);
+    cudaStream_t s = as_stream(stream);
+    const int64_t nm = (int64_t)P.n * P.m;
+    if (P.n == 0) return MPK_OK;
+    // the output is written by kernels: it must be page-locked host memory with a device address
+    cudaPointerAttributes at{};
+    MPK_CUDA(cudaPointerGetAttributes(&at, Y_host));
+    if (at.type != cudaMemoryTypeHost || at.devicePointer == nullptr)
+        fail(MPK_ERR_INVALID, "Y_host must be page-locked host memory (cudaHostAlloc or cudaHostRegister)");
+    double *yh = static_cast<double *>(at.devicePointer);
+    const size_t xbytes = sizeof(double) * (size_t)nm;
+    if ((const char *)Y_host < (const char *)X_host + xbytes &&
+        (const char *)X_host < (const char *)Y_host + xbytes * (size_t)(p + 1))
+        fail(MPK_ERR_INVALID, "Y_host overlaps X_host");
+    if (p == 0) {
+        MPK_CUDA(cudaMemcpyAsync(Y_host, X_host, xbytes, cudaMemcpyHostToHost, s));
+        return MPK_OK;
+    }
+    if (P.identity || P.order == MPK_ORDER_PLAN) {
+        // X into power block 0 of the workspace.  The staged engine with one right-hand side
+        // runs the host-output kernel: power-1 units copy X's rows to Y_host[0] and every power's
+        // rows go to Y_host as their units finish.  Other plans compute into the workspace and
+        // copy the p+1 blocks to Y_host afterwards.
+        MPK_CUDA(cudaMemcpyAsync(P.work, X_host, xbytes, cudaMemcpyHostToDevice, s));
+        next_epoch(P, s);
+        KArgs a = base_args(P, p);
+        a.ring = p + 1;
+        a.x0 = P.work;
+        a.ybase = P.work;
+        const bool fused = P.engine == MPK_ENGINE_STAGED && P.m == 1 && a.trace == nullptr;
+        if (P.level_capped && !fused)
+            fail(MPK_ERR_UNSUPPORTED, "host output of a level-capped plan needs nrhs 1 and the staged engine");
+        if (P.accum == MPK_F32) launch_round_f32(P.work, nm, P.shadow, s);
+        if (fused) {
+            a.y0copy = yh;
+            a.yhost = yh;
+            if (P.level0_rows > 0)  // level 0 of a level-capped plan has no units
+                MPK_CUDA(cudaMemcpyAsync(Y_host, X_host, sizeof(double) * (size_t)P.level0_rows * P.m,
+                                         cudaMemcpyHostToHost, s));
+            launch_mpk(P, a, 2, s);  // MODE_HOST
+        } else {
+            launch_mpk(P, a, 0, s);
+            MPK_CUDA(cudaMemcpyAsync(Y_host, P.work, xbytes * (size_t)(p + 1), cudaMemcpyDeviceToHost, s));
+        }
+    } else {
+        // X to the device, gathered into plan order, every power in the workspace, then all
+        // powers (0..p) written through the permutation into Y_host
+        Tmp<double> xd(nm, s);
+        MPK_CUDA(cudaMemcpyAsync(xd.p, X_host, xbytes, cudaMemcpyHostToDevice, s));
+        launch_gather_rows(xd.p, P.perm, P.work, P.n, P.m, s);
+        next_epoch(P, s);
+        KArgs a = base_args(P, p);
+        a.ring = p + 1;
+        a.x0 = P.work;
+        a.ybase = P.work;
+        if (P.accum == MPK_F32) launch_round_f32(P.work, nm, P.shadow, s);
+        launch_mpk(P, a, 0, s);
+        launch_scatter_powers(P.work, P.iperm, yh, P.n, P.m, p, s, -1, 0, 0);
+    }
+    return MPK_OK;
+    MPK_GUARD_END
+}
+
 extern "C" mpk_status mpk_spmv_powers(const mpk_plan_t *Ph, const double *X, int32_t p, double *Y,
                                       mpk_stream stream) {
     MPK_GUARD_BEGIN

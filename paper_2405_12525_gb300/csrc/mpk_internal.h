@@ -260,6 +260,8 @@ struct KArgs {
     int64_t ystride;
     int32_t ring;
     double *y0copy;    // if set, units of power 1 copy their rows of x0 here
+    double *yhost = nullptr;  // if set, every power's rows are stored here too (pinned host memory,
+                              // device-mapped, plan order, ystride apart): output overlaps compute
     float *shadow;     // binary32 accumulation: ring of 2 blocks (ystride floats apart); slot j & 1
                        // holds the binary32 rounding of step j, the input of step j + 1
     int32_t k_offset;  // absolute index of local power 0 (Chebyshev blocks)
@@ -370,10 +372,11 @@ void launch_spmv_rows(const Plan *const *plans, const int32_t *lo, const int32_t
                       double *const *y, int count, cudaStream_t s);
 void launch_copy_rows(const double *src, const int64_t *src_idx, double *dst, const int64_t *dst_idx, int64_t n,
                       int32_t m, cudaStream_t s);
-// Y[k][i] = W[k][iperm[i]] (iperm NULL: W[k][base + i]) for k = 1..p, i < n; W's powers are
-// w_pstride doubles apart (< 0: n * m), Y's n * m
+// Y[k][i] = W[k][iperm[i]] (iperm NULL: W[k][base + i]) for k = k0..p, i < n; W's powers are
+// w_pstride doubles apart (< 0: n * m), Y's n * m; Y may be device-mapped host memory (the
+// writes of a thread block are whole consecutive rows)
 void launch_scatter_powers(const double *W, const int32_t *iperm, double *Y, int32_t n, int32_t m, int32_t p,
-                           cudaStream_t s, int64_t w_pstride = -1, int32_t base = 0);
+                           cudaStream_t s, int64_t w_pstride = -1, int32_t base = 0, int32_t k0 = 1);
 // dst[r] = src[perm[r] - base] for r < n (m values a row; perm NULL: the identity)
 void launch_gather_rows(const double *src, const int32_t *perm, double *dst, int32_t n, int32_t m,
                         cudaStream_t s, int32_t base = 0);

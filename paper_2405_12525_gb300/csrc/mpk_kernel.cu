@@ -357,8 +357,8 @@ void launch_scatter_rows(const double *src, const int32_t *iperm, double *dst, i
     launch_gather_rows(src, iperm, dst, n, m, s);
 }
 
-// Y[k][i] = W[k][iperm[i]] for k = 1..p: the powers computed in plan order, written in the
-// matrix's own order.  Stores are full, coalesced rows of the output; the gathered reads
+// Y[k][i] = W[k][iperm[i]] for k = k0..p: the powers computed in plan order, written in the
+// matrix's own order (Y in device memory, or device-mapped pinned host memory).  Stores are full, coalesced rows of the output; the gathered reads
 // come from rows that neighbouring original rows map to (for a BFS order these sit a few
 // levels apart and share cache sectors with the reads of nearby original rows).  Each block
 // walks tiles of consecutive original rows, power by power, so that the sectors a tile reads
@@ -371,7 +371,7 @@ constexpr int kScatterBS = 256, kScatterValues = 16, kScatterBlocksPerSM = 4;
 template <int M>
 __global__ void __launch_bounds__(kScatterBS, kScatterBlocksPerSM)
     k_scatter_powers(const double *__restrict__ W, int64_t w_pstride, const int32_t *__restrict__ iperm,
-                     int32_t w_row0, double *__restrict__ Y, int32_t n, int32_t p) {
+                     int32_t w_row0, double *__restrict__ Y, int32_t n, int32_t p, int32_t k0) {
     constexpr int IT = kScatterValues / M;  // rows of a thread in a tile
     constexpr int64_t kTile = (int64_t)kScatterBS * IT;
     const int64_t nm = (int64_t)n * M;
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(kScatterBS, kScatterBlocksPerSM)
             const int64_t i = base + (int64_t)q * kScatterBS + threadIdx.x;
             src[q] = i < n ? (iperm ? __ldg(iperm + i) : w_row0 + (int32_t)i) : -1;
         }
-        for (int k = 1; k <= p; ++k) {
+        for (int k = k0; k <= p; ++k) {
             const double *w = W + k * w_pstride;
             double *y = Y + k * nm;
             double v[IT][M];
@@ -403,16 +403,16 @@ __global__ void __launch_bounds__(kScatterBS, kScatterBlocksPerSM)
 }
 
 void launch_scatter_powers(const double *W, const int32_t *iperm, double *Y, int32_t n, int32_t m, int32_t p,
-                           cudaStream_t s, int64_t w_pstride, int32_t base) {
-    if (n <= 0 || p <= 0) return;
+                           cudaStream_t s, int64_t w_pstride, int32_t base, int32_t k0) {
+    if (n <= 0 || p < k0) return;
     if (w_pstride < 0) w_pstride = (int64_t)n * m;
     const int g = device_sms() * kScatterBlocksPerSM;
     switch (m) {
-        case 1: k_scatter_powers<1><<<g, kScatterBS, 0, s>>>(W, w_pstride, iperm, base, Y, n, p); break;
-        case 2: k_scatter_powers<2><<<g, kScatterBS, 0, s>>>(W, w_pstride, iperm, base, Y, n, p); break;
-        case 4: k_scatter_powers<4><<<g, kScatterBS, 0, s>>>(W, w_pstride, iperm, base, Y, n, p); break;
-        case 8: k_scatter_powers<8><<<g, kScatterBS, 0, s>>>(W, w_pstride, iperm, base, Y, n, p); break;
-        case 16: k_scatter_powers<16><<<g, kScatterBS, 0, s>>>(W, w_pstride, iperm, base, Y, n, p); break;
+        case 1: k_scatter_powers<1><<<g, kScatterBS, 0, s>>>(W, w_pstride, iperm, base, Y, n, p, k0); break;
+        case 2: k_scatter_powers<2><<<g, kScatterBS, 0, s>>>(W, w_pstride, iperm, base, Y, n, p, k0); break;
+        case 4: k_scatter_powers<4><<<g, kScatterBS, 0, s>>>(W, w_pstride, iperm, base, Y, n, p, k0); break;
+        case 8: k_scatter_powers<8><<<g, kScatterBS, 0, s>>>(W, w_pstride, iperm, base, Y, n, p, k0); break;
+        case 16: k_scatter_powers<16><<<g, kScatterBS, 0, s>>>(W, w_pstride, iperm, base, Y, n, p, k0); break;
         default: fail(MPK_ERR_UNSUPPORTED, "scatter of %d right-hand sides", m);
     }
     MPK_LAUNCHED();
@@ -461,8 +461,9 @@ static int mpk_block_size(int shape) {
 }
 
 int occupancy_grid(int mode, int m, bool trace, int vtype, int shape, bool a32) {
-    static int cache[3][2][2][5][kNumShapes][2] = {};  // width index: log2 of m (1 .. 16)
+    static int cache[3][3][2][5][kNumShapes][2] = {};  // width index: log2 of m (1 .. 16)
     if (vtype < 0 || vtype > 2) fail(MPK_ERR_UNSUPPORTED, "value type %d", vtype);
+    if (mode < 0 || mode > 2) fail(MPK_ERR_INVALID, "kernel mode %d", mode);
     if (shape < 0 || shape >= kNumShapes) fail(MPK_ERR_UNSUPPORTED, "block shape %d", shape);
     if (m < 1 || m > 16 || (m & (m - 1))) fail(MPK_ERR_UNSUPPORTED, "nrhs %d", m);
     int &c = cache[vtype][mode][trace ? 1 : 0][__builtin_ctz((unsigned)m)][shape][a32 ? 1 : 0];

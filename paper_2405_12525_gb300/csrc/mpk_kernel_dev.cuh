@@ -32,7 +32,7 @@ template <int SH> struct Shape {
 // the staged shapes lose at one block: 6.74 against 4.94 ms).
 template <int M, int MODE, bool TRACE, int SH> struct MpkOcc {
     static constexpr int blocks = Shape<SH>::X ? kShapes[SH].blocks
-                                  : (M == 1 && MODE == 0 && !TRACE) ? kShapes[SH].blocks
+                                  : (M == 1 && MODE != 1 /* not the recurrence */ && !TRACE) ? kShapes[SH].blocks
                                   : (Shape<SH>::SE == 0 && M >= 4) ? 1
                                                                     : 2;
 };
@@ -53,7 +53,8 @@ template <class VT, int SH> constexpr int smem_bytes() {
                         : Shape<SH>::SL * Shape<SH>::SE * (int)(sizeof(typename VT::T) + (kStageCol ? 4 : 0));
 }
 
-enum Mode { MODE_POWERS = 0, MODE_CHEB = 1 };
+// MODE_HOST: the powers, each row also stored into host memory (a.yhost) as its unit finishes
+enum Mode { MODE_POWERS = 0, MODE_CHEB = 1, MODE_HOST = 2 };
 
 
 __device__ __forceinline__ int ld_relaxed(const int32_t *p) {
@@ -370,6 +371,11 @@ __device__ __forceinline__ void row_epilogue_loaded(const KArgs &a, int k, int64
         if constexpr (A32) {
 #pragma unroll
             for (int i = 0; i < M; ++i) sh[i] = (float)wa[i];
+        }
+        if constexpr (MODE == MODE_HOST) {  // the power's rows in host memory too (never read here)
+            double *yh = a.yhost + (int64_t)j * a.ystride + r * M;
+#pragma unroll
+            for (int i = 0; i < M; ++i) __stcs(yh + i, w[i]);
         }
         if (k == 1 && a.y0copy) {
 #pragma unroll
@@ -1459,7 +1465,23 @@ template <int M, int MODE, class VT, int SH> static void *mpk_fn(bool trace, boo
     return trace ? (void *)k_mpk<M, MODE, true, VT, SH> : (void *)k_mpk<M, MODE, false, VT, SH>;
 }
 
+// the host-output kernel: one right-hand side, no trace counters
+template <class VT, int SH> static void *mpk_fn_host(bool a32) {
+    if (a32) {
+        if constexpr (Shape<SH>::X || std::is_same<VT, ValF64>::value) {
+            fail(MPK_ERR_UNSUPPORTED, "binary32 accumulation needs float32 or bfloat16 values and a shape other than 3");
+        } else {
+            return (void *)k_mpk<1, MODE_HOST, false, VT, SH, true>;
+        }
+    }
+    return (void *)k_mpk<1, MODE_HOST, false, VT, SH>;
+}
+
 template <class VT, int SH> static void *select_mpk_vs(int mode, int m, bool trace, bool a32) {
+    if (mode == MODE_HOST) {
+        if (m != 1 || trace) fail(MPK_ERR_UNSUPPORTED, "host output needs nrhs 1 and no trace counters");
+        return mpk_fn_host<VT, SH>(a32);
+    }
 #define SEL(MM)                                                                           \
     if (m == MM) {                                                                        \
         if (mode == MODE_POWERS) return mpk_fn<MM, MODE_POWERS, VT, SH>(trace, a32);      \
