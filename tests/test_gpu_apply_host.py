@@ -32,10 +32,11 @@ def _pinned_nan(shape):
     return torch.full(shape, float("nan"), dtype=torch.float64).pin_memory()
 
 
+@pytest.mark.parametrize("pin", [False, True])
 @pytest.mark.parametrize("engine", [0, 1, 2])
 @pytest.mark.parametrize("m", [1, 2])
 @pytest.mark.parametrize("order", [0, 1])
-def test_host_buffers_equal_oracle_and_device_apply(mpk, order, m, engine):
+def test_host_buffers_equal_oracle_and_device_apply(mpk, order, m, engine, pin):
     A = gen.laplacian_3d(21, 13, 11)
     dA = mpk.CsrMatrix.from_host(A, is_symmetric=True)
     L = mpk.build_levels(dA, 0)
@@ -43,8 +44,9 @@ def test_host_buffers_equal_oracle_and_device_apply(mpk, order, m, engine):
     _, pe, _, _ = oracle.levels(A, 0)
     X = gen.vector(A.n, m, stream=501)
     Xin = np.ascontiguousarray(X if order == 0 else X[pe])
+    Xh = torch.from_numpy(Xin).pin_memory() if pin else torch.from_numpy(Xin)
     Yh = _pinned_nan((8, A.n, m))
-    P.apply_host(torch.from_numpy(Xin), 7, Yh)
+    P.apply_host(Xh, 7, Yh)
     torch.cuda.synchronize()
     P.sync_status()
     want = oracle.mpk(A, X, 7)
@@ -54,21 +56,40 @@ def test_host_buffers_equal_oracle_and_device_apply(mpk, order, m, engine):
     assert _bits(Yd.cpu().numpy(), Yh.numpy())
 
 
+@pytest.mark.parametrize("shape", [0, 2])
 @pytest.mark.parametrize("order", [0, 1])
-def test_host_buffers_binary32_two_slice_shape(mpk, order):
+def test_host_buffers_binary32(mpk, order, shape):
+    # plan option shape 0: the planner's choice (two slices a warp, index 4); 2: index 1
     A = gen.laplacian_3d(40, 36, 30)
     dA = mpk.CsrMatrix.from_host(A, is_symmetric=True, value_type=mpk.MPK_BF16)
     Aw = gen.CSR(dA.row_ptr.cpu().numpy(), dA.col.cpu().numpy(), dA.val.double().cpu().numpy())
     L = mpk.build_levels(dA, 0)
-    P = mpk.plan(dA, L, p_max=8, order=order, accum=mpk.MPK_F32)
-    assert P.describe()["shape"] == 4
+    P = mpk.plan(dA, L, p_max=8, order=order, accum=mpk.MPK_F32, shape=shape)
+    assert P.describe()["shape"] == (4 if shape == 0 else 1)
     _, pe, _, _ = oracle.levels(A, 0)
     X = gen.vector(A.n, 1, stream=502)
     Xin = np.ascontiguousarray(X if order == 0 else X[pe])
-    Yh = P.apply_host(torch.from_numpy(Xin), 8, _pinned_nan((9, A.n, 1)))
+    Yh = P.apply_host(torch.from_numpy(Xin).pin_memory(), 8, _pinned_nan((9, A.n, 1)))
     torch.cuda.synchronize()
     P.sync_status()
     want = oracle.mpk_acc32(Aw, X, 8)
+    assert _bits(Yh.numpy(), want if order == 0 else want[:, pe, :])
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_host_buffers_x_staged_shape(mpk, order):
+    # the shape that stages input rows with bulk copies (plan option 4) through the host-output mode
+    A = gen.laplacian_3d(21, 13, 11)
+    dA = mpk.CsrMatrix.from_host(A, is_symmetric=True)
+    P = mpk.plan(dA, mpk.build_levels(dA, 0), p_max=6, order=order, cache_bytes=60000, shape=4)
+    assert P.describe()["shape"] == 3
+    _, pe, _, _ = oracle.levels(A, 0)
+    X = gen.vector(A.n, 1, stream=507)
+    Xin = np.ascontiguousarray(X if order == 0 else X[pe])
+    Yh = P.apply_host(torch.from_numpy(Xin).pin_memory(), 6, _pinned_nan((7, A.n, 1)))
+    torch.cuda.synchronize()
+    P.sync_status()
+    want = oracle.mpk(A, X, 6)
     assert _bits(Yh.numpy(), want if order == 0 else want[:, pe, :])
 
 
