@@ -262,15 +262,15 @@ extern "C" mpk_status mpk_apply_host(const mpk_plan_t *Ph, const double *X_host,
         // runs the host-output kernel: power-1 units copy X's rows to Y_host[0] and every power's
         // rows go to Y_host as their units finish.  Other plans compute into the workspace and
         // copy the p+1 blocks to Y_host afterwards.
+        const bool fused = P.engine == MPK_ENGINE_STAGED && P.m == 1 && P.trace == nullptr;
+        if (P.level_capped && !fused)
+            fail(MPK_ERR_UNSUPPORTED, "host output of a level-capped plan needs nrhs 1 and the staged engine");
         MPK_CUDA(cudaMemcpyAsync(P.work, X_host, xbytes, cudaMemcpyHostToDevice, s));
         next_epoch(P, s);
         KArgs a = base_args(P, p);
         a.ring = p + 1;
         a.x0 = P.work;
         a.ybase = P.work;
-        const bool fused = P.engine == MPK_ENGINE_STAGED && P.m == 1 && a.trace == nullptr;
-        if (P.level_capped && !fused)
-            fail(MPK_ERR_UNSUPPORTED, "host output of a level-capped plan needs nrhs 1 and the staged engine");
         if (P.accum == MPK_F32) launch_round_f32(P.work, nm, P.shadow, s);
         if (fused) {
             a.y0copy = yh;
