@@ -895,6 +895,16 @@ def main():
     # headline: one kernel launch per apply, vectors in the plan's (BFS) numbering
     P = mpk.plan(dA, L, p_max=p, nrhs=1, order=mpk.ORDER_PLAN, cache_bytes=cb, accum=accum, split_levels=args.split)
     t_plan = time.perf_counter() - t0
+    # the same preprocessing once more: the first calls of a process also load the library's kernel
+    # modules (a one-time cost); the second pair is the cost per matrix
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    L2 = mpk.build_levels(dA, 0)
+    t_levels_warm = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    P2 = mpk.plan(dA, L2, p_max=p, nrhs=1, order=mpk.ORDER_PLAN, cache_bytes=cb, accum=accum, split_levels=args.split)
+    t_plan_warm = time.perf_counter() - t0
+    del P2, L2
     Po = mpk.plan(dA, L, p_max=p, nrhs=1, order=mpk.ORDER_ORIGINAL, cache_bytes=cb, accum=accum,
                   split_levels=args.split)
     desc = P.describe()
@@ -1087,8 +1097,12 @@ def main():
                                               "is the fastest" + ("; binary32 accumulation in every comparator"
                                                                   if acc32 else ""),
                            "vendor_csr": csr},
-            "preprocess": {"levels_ms": t_levels * 1e3, "plan_ms": t_plan * 1e3,
-                           "spmv_equivalents": (t_levels + t_plan) * 1e3 / (best_plain / p)},
+            "preprocess": {"levels_ms": t_levels_warm * 1e3, "plan_ms": t_plan_warm * 1e3,
+                           "spmv_equivalents": (t_levels_warm + t_plan_warm) * 1e3 / (best_plain / p),
+                           "first_call": {"levels_ms": t_levels * 1e3, "plan_ms": t_plan * 1e3,
+                                          "spmv_equivalents": (t_levels + t_plan) * 1e3 / (best_plain / p)},
+                           "note": "levels and plan of the same matrix built twice in one process; the first "
+                                   "calls also load the library's kernel modules"},
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": args.steps * (2 if acc32 else 1),
         }
