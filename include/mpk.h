@@ -394,8 +394,8 @@ mpk_status mpk_debug_drop_release(mpk_plan_t *P, int32_t chunk, int32_t k);
 
 /* ---------------------------------------------------------------------------------------
  * Measurement aids (the analogue of the paper's load-only bandwidth kernel, Sec. 6).
- * mpk_probe_load: `reps` passes of 16-byte loads over buf[0..bytes) (bytes a multiple of
- * 16) by ctas_per_sm * #SM blocks of 512 threads; sink is a device int that is written
+ * mpk_probe_load: `reps` passes of 16-byte loads over buf[0..bytes) (buf 16-byte aligned,
+ * bytes a multiple of 16, else MPK_ERR_INVALID) by ctas_per_sm * #SM blocks of 512 threads; sink is a device int that is written
  * only if a checksum matches a constant.  mpk_probe_dfma: blocks * 256 threads each run
  * `iters` x 8 independent FP64 FMAs; sink as above.
  * ------------------------------------------------------------------------------------- */

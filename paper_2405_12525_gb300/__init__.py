@@ -165,6 +165,27 @@ def _ptr(t) -> int:
     return int(t.data_ptr()) if t is not None and t.numel() > 0 else 0
 
 
+def _rows_f64(t, name: str) -> int:
+    """Check a contiguous float64 CUDA tensor of rows; returns its row width (last dimension,
+    1 for a vector)."""
+    torch = _torch()
+    if t.dtype != torch.float64 or not t.is_cuda or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    return int(t.shape[-1]) if t.dim() > 1 else 1
+
+
+def _index(t, dtype, name: str):
+    """Check a contiguous CUDA index tensor of the given integer dtype."""
+    if t.dtype != dtype or not t.is_cuda or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous {dtype} CUDA tensor")
+
+
+def _same_device(*ts):
+    devs = {t.device for t in ts}
+    if len(devs) > 1:
+        raise ValueError(f"tensors on several devices: {sorted(str(d) for d in devs)}")
+
+
 def _value_type(t) -> int:
     torch = _torch()
     types = {torch.float64: MPK_F64, torch.float32: MPK_F32, torch.bfloat16: MPK_BF16}
@@ -283,8 +304,16 @@ def build_levels_from(A: CsrMatrix, roots, stream=None) -> Levels:
 
 
 def gather_rows(src, idx, out, stream=None):
-    """out[r] = src[idx[r]] (rows of m doubles; CUDA tensors, idx int32)."""
-    m = int(src.shape[-1]) if src.dim() > 1 else 1
+    """out[r] = src[idx[r]] (rows of m doubles; CUDA tensors, idx int32).  The values of idx
+    must be row numbers of src; they are not checked (that would need a device pass)."""
+    torch = _torch()
+    m = _rows_f64(src, "src")
+    if _rows_f64(out, "out") != m:
+        raise ValueError("src and out need rows of the same width")
+    _index(idx, torch.int32, "idx")
+    _same_device(src, idx, out)
+    if out.numel() < idx.numel() * m:
+        raise ValueError(f"out has {out.numel()} elements, the call writes {idx.numel()} rows of {m}")
     _check(load().mpk_gather_rows(_ptr(src), _ptr(idx), int(idx.numel()), m, _ptr(out), _stream(stream)))
     return out
 
@@ -295,6 +324,10 @@ def spmv_rows_multi(plans, row_begin, row_end, Xs, Ys, stream=None):
     n = len(plans)
     if not (len(row_begin) == len(row_end) == len(Xs) == len(Ys) == n):
         raise ValueError("one row range, X and Y per plan")
+    for P, lo, hi, X, Y in zip(plans, row_begin, row_end, Xs, Ys):
+        if int(hi) > int(lo):  # the library reads X and Y of non-empty segments only
+            P._block(X)
+            P._out_block(Y, X, 1)
     hs = (C.c_void_p * max(n, 1))(*[P._h for P in plans])
     lo = (C.c_int32 * max(n, 1))(*[int(v) for v in row_begin])
     hi = (C.c_int32 * max(n, 1))(*[int(v) for v in row_end])
@@ -304,8 +337,16 @@ def spmv_rows_multi(plans, row_begin, row_end, Xs, Ys, stream=None):
 
 
 def copy_rows(src, src_idx, dst, dst_idx, stream=None):
-    """dst[dst_idx[t]] = src[src_idx[t]] (rows of m doubles, int64 CUDA index tensors)."""
-    m = int(src.shape[-1]) if src.dim() > 1 else 1
+    """dst[dst_idx[t]] = src[src_idx[t]] (rows of m doubles, int64 CUDA index tensors).  The
+    index values must be row numbers of src and dst, the destinations distinct; they are not
+    checked (that would need a device pass)."""
+    torch = _torch()
+    m = _rows_f64(src, "src")
+    if _rows_f64(dst, "dst") != m:
+        raise ValueError("src and dst need rows of the same width")
+    _index(src_idx, torch.int64, "src_idx")
+    _index(dst_idx, torch.int64, "dst_idx")
+    _same_device(src, src_idx, dst, dst_idx)
     if src_idx.numel() != dst_idx.numel():
         raise ValueError("one destination per source row")
     _check(load().mpk_copy_rows(_ptr(src), _ptr(src_idx), _ptr(dst), _ptr(dst_idx), int(src_idx.numel()), m,
@@ -423,8 +464,8 @@ class Plan:
         the launch's status code."""
         self._block(X)
         self._out_block(Y, X, p + 1)
-        _check(self._lib.mpk_apply_noalloc(self._h, _ptr(X), int(p), _ptr(Y), self._status_word(status, X),
-                                           _stream(stream)))
+        st = self._status_word(status, X)
+        _check(self._lib.mpk_apply_noalloc(self._h, _ptr(X), int(p), _ptr(Y), st, _stream(stream)))
         return Y
 
     def spmv_rows(self, row_begin: int, row_end: int, X, Y, stream=None):
@@ -550,11 +591,19 @@ def plan(A: CsrMatrix, levels: Levels | None = None, p_max: int = 8, nrhs: int =
 
 
 def probe_load(buf, reps: int, ctas_per_sm: int, sink, stream=None):
+    """reps passes of 16-byte loads over buf (a contiguous CUDA tensor, 16-byte aligned, a
+    multiple of 16 bytes); sink is an int32 CUDA tensor."""
+    torch = _torch()
+    if not buf.is_cuda or not buf.is_contiguous() or buf.data_ptr() % 16:
+        raise TypeError("buf must be a contiguous, 16-byte aligned CUDA tensor")
+    _index(sink, torch.int32, "sink")
     _check(load().mpk_probe_load(_ptr(buf), buf.numel() * buf.element_size(), reps, ctas_per_sm, _ptr(sink),
                                  _stream(stream)))
 
 
 def probe_dfma(blocks: int, iters: int, sink, stream=None):
+    """blocks x 256 threads of iters x 8 independent FP64 FMAs; sink is a float64 CUDA tensor."""
+    _rows_f64(sink, "sink")
     _check(load().mpk_probe_dfma(blocks, iters, _ptr(sink), _stream(stream)))
 
 
@@ -621,12 +670,20 @@ class BatchPlan:
             _check(self._lib.mpk_batch_apply(self._h, C.cast(xp, C.c_void_p), C.cast(yp, C.c_void_p),
                                              _stream(stream)))
             return self.views()
-        if Ys is None:
-            Ys = [torch.empty((p + 1, n, self.nrhs), dtype=torch.float64, device=X.device)
-                  for X, n, p in zip(Xs, self.sizes, self.p_each)]
         for X, n in zip(Xs, self.sizes):
             if X.dtype != torch.float64 or not X.is_cuda or not X.is_contiguous() or X.numel() != n * self.nrhs:
                 raise TypeError("each X must be a contiguous float64 CUDA tensor of n x nrhs")
+        if Ys is None:
+            Ys = [torch.empty((p + 1, n, self.nrhs), dtype=torch.float64, device=X.device)
+                  for X, n, p in zip(Xs, self.sizes, self.p_each)]
+        if len(Ys) != len(self.sizes):
+            raise ValueError("one Y per matrix")
+        for X, Y, n, p in zip(Xs, Ys, self.sizes, self.p_each):
+            _rows_f64(Y, "each Y")
+            _same_device(X, Y)
+            if Y.numel() < (p + 1) * n * self.nrhs:
+                raise ValueError(f"a Y has {Y.numel()} elements, its block writes (p+1) x n x nrhs = "
+                                 f"{(p + 1) * n * self.nrhs}")
         xp = (C.c_void_p * len(Xs))(*[_ptr(X) for X in Xs])
         yp = (C.c_void_p * len(Ys))(*[_ptr(Y) for Y in Ys])
         _check(self._lib.mpk_batch_apply(self._h, C.cast(xp, C.c_void_p), C.cast(yp, C.c_void_p), _stream(stream)))

@@ -575,6 +575,7 @@ __global__ void k_probe_dfma(int iters, double *sink) {
 void probe_load(const void *buf, int64_t bytes, int reps, int ctas_per_sm, int32_t *sink, cudaStream_t s) {
     if (!buf || !sink || bytes <= 0 || bytes % 16 || reps < 1 || ctas_per_sm < 1 || ctas_per_sm > 64)
         fail(MPK_ERR_INVALID, "probe_load: bad arguments");
+    if (reinterpret_cast<uintptr_t>(buf) % 16) fail(MPK_ERR_INVALID, "probe_load: buf is not 16-byte aligned");
     k_probe_load<<<device_sms() * ctas_per_sm, 512, 0, s>>>(static_cast<const int4 *>(buf), bytes / 16, reps, sink);
     MPK_LAUNCHED();
 }
