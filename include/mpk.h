@@ -24,7 +24,8 @@
  *  - Every function returns an mpk_status and never throws; mpk_last_error() gives a
  *    thread-local message for the last failure on the calling thread.
  *  - Indices are int32: n, nnz < 2^31.  Floating point is IEEE binary64; each row sum is
- *    evaluated in the row's stored order with one fused multiply-add per entry.
+ *    evaluated in the row's stored order with one fused multiply-add per entry (in binary32
+ *    for plans built with opts.accum = MPK_F32, over binary64 vectors).
  */
 #ifndef MPK_H
 #define MPK_H
@@ -63,8 +64,9 @@ typedef void *mpk_stream;
  * Precision: a plan stores the values in val_type (8, 4 or 2 bytes an entry) and every
  * kernel widens each value to float64 exactly before its FMA; vectors and accumulation are
  * float64.  The results are those of the float64 computation on the widened values, bit for
- * bit; values exactly representable in the narrow type (e.g. the {6, -1} or {26, -1}
- * stencil coefficients in bfloat16) therefore give the float64 results unchanged.  In the
+ * bit (unless the plan asks for binary32 row sums, opts.accum); values exactly
+ * representable in the narrow type (e.g. the {6, -1} or {26, -1} stencil coefficients in
+ * bfloat16) therefore give the float64 results unchanged.  In the
  * narrow types every value must be zero or a normal number: mpk_plan fails with
  * MPK_ERR_UNSUPPORTED on a subnormal, infinite or NaN value. */
 typedef struct {
@@ -222,8 +224,8 @@ typedef struct {
     const int32_t *group_row_ptr_dev;   /* num_groups+1 row offsets                        */
     const int32_t *chunk_row_ptr_dev;   /* num_chunks+1 row offsets                        */
     const int32_t *perm_dev;            /* new -> old (NULL: identity)                     */
-    int32_t shape;                /* block shape of the staged engine (0..3, opts.shape - 1) */
-    int32_t engine;               /* MPK_ENGINE_STAGED or MPK_ENGINE_WARP                 */
+    int32_t shape;                /* block shape of the staged engine (0..4, opts.shape - 1) */
+    int32_t engine;               /* MPK_ENGINE_STAGED, MPK_ENGINE_WARP or MPK_ENGINE_SWEEP */
     int32_t chunk_rows;           /* rows per chunk limit in effect                      */
     int32_t accum;                /* MPK_F64 or MPK_F32 (opts.accum)                     */
     int32_t split_levels;         /* opts.split_levels; group_level_ptr then holds the level
@@ -246,9 +248,10 @@ void mpk_plan_destroy(mpk_plan_t *P);
  * plan's order (opts.order).  1 <= p <= p_max (p = 0 only copies X).  X must not overlap
  * Y[1..p].  One persistent kernel executes the Lp-diagram cells (group g, power k) in
  * diagonal order, split into row chunks; each chunk waits on the completion flags of the
- * chunks its rows read at power k-1.  With MPK_ORDER_ORIGINAL a gather kernel runs first
- * and the kernel writes Y through the permutation.  Results equal back-to-back SpMV bit
- * for bit.  Not safe to run concurrently with another call on the same plan.
+ * chunks its rows read at power k-1.  With MPK_ORDER_ORIGINAL a gather kernel first takes
+ * X into plan order in the plan's workspace, the kernel computes every power there, and a
+ * last pass writes Y[1..p] through the permutation (one gather per output row).  Results
+ * equal back-to-back SpMV bit for bit.  Not safe to run concurrently with another call on the same plan.
  * ------------------------------------------------------------------------------------- */
 mpk_status mpk_apply(const mpk_plan_t *P, const double *X, int32_t p, double *Y, mpk_stream stream);
 
