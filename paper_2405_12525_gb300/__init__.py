@@ -420,6 +420,13 @@ class Plan:
             raise ValueError(f"{name} has {Y.numel()} elements, the call writes {blocks} x n x nrhs = "
                              f"{blocks * self.n * self.nrhs}")
 
+    def _x_clear_of_powers(self, X, Y, p: int):
+        """X may be Y[0] but must not overlap Y[1..p], which the call writes while it reads X."""
+        blk = 8 * self.n * self.nrhs
+        x0, y1 = X.data_ptr(), Y.data_ptr() + blk
+        if p > 0 and x0 < y1 + p * blk and y1 < x0 + 8 * X.numel():
+            raise ValueError("X overlaps Y[1..p]")
+
     @staticmethod
     def _status_word(status, X):
         torch = _torch()
@@ -436,6 +443,7 @@ class Plan:
         if Y is None:
             Y = torch.empty((p + 1, self.n, self.nrhs), dtype=torch.float64, device=X.device)
         self._out_block(Y, X, p + 1)
+        self._x_clear_of_powers(X, Y, p)
         _check(self._lib.mpk_apply(self._h, _ptr(X), int(p), _ptr(Y), _stream(stream)))
         return Y
 
@@ -464,6 +472,7 @@ class Plan:
         the launch's status code."""
         self._block(X)
         self._out_block(Y, X, p + 1)
+        self._x_clear_of_powers(X, Y, p)
         st = self._status_word(status, X)
         _check(self._lib.mpk_apply_noalloc(self._h, _ptr(X), int(p), _ptr(Y), st, _stream(stream)))
         return Y
@@ -482,6 +491,7 @@ class Plan:
         if Y is None:
             Y = torch.empty((p + 1, self.n, self.nrhs), dtype=torch.float64, device=X.device)
         self._out_block(Y, X, p + 1)
+        self._x_clear_of_powers(X, Y, p)
         _check(self._lib.mpk_spmv_powers(self._h, _ptr(X), int(p), _ptr(Y), _stream(stream)))
         return Y
 

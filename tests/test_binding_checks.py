@@ -124,3 +124,17 @@ def test_probe_checks():
         mpk.probe_load(FakeCuda(torch.zeros(64, dtype=torch.uint8)), 1, 1, idx(1, torch.int64))
     with pytest.raises(TypeError):
         mpk.probe_dfma(1, 1, idx(1, torch.int32))
+
+
+def test_x_may_be_y0_but_not_a_later_power():
+    P = fake_plan(10, 1)
+    Y = torch.zeros(4, 10, 1, dtype=torch.float64)
+    with pytest.raises(ValueError, match="overlaps"):
+        P.apply(FakeCuda(Y[1]), 3, Y=FakeCuda(Y))
+    with pytest.raises(ValueError, match="overlaps"):
+        P.spmv_powers(FakeCuda(Y[3]), 3, Y=FakeCuda(Y))
+    with pytest.raises(ValueError, match="overlaps"):
+        P.apply_noalloc(FakeCuda(Y.view(-1)[5:15]), 3, FakeCuda(Y))
+    # X = Y[0] passes every check and reaches the library call, which the stand-in plan lacks
+    with pytest.raises(AttributeError, match="_lib"):
+        P.apply(FakeCuda(Y[0]), 3, Y=FakeCuda(Y))
