@@ -60,8 +60,10 @@ def tune_plan(dA, levels, p: int, X, nrhs: int = 1, order: int = ORDER_PLAN, can
         ms = _time(lambda: P.apply(X, p, Y=Y), reps)
         P.sync_status()
         report.append((ms, {"engine": "sweep"}))
-        if ms < best[0]:
+        if best is None or ms < best[0]:
             best = (ms, P)
+    if best is None:
+        raise ValueError("no candidate plan: the candidate lists are empty and the sweep is off")
     return best[1], sorted(report, key=lambda t: t[0])
 
 
@@ -77,4 +79,6 @@ def tune_batch(mats, p_each, Xs, nrhs: int = 1, order: int = ORDER_PLAN, candida
             best = (ms, B)
         else:
             del B
+    if best is None:
+        raise ValueError("no candidate batch plan: the candidate lists are empty")
     return best[1], sorted(report, key=lambda t: t[0])
