@@ -175,6 +175,21 @@ def algorithmic(A, p: int, m: int = 1):
     return flops, a_bytes, v_bytes
 
 
+def memory_roofs(a_bytes: float, n: int, p: int, acc32: bool, hbm_gbs: float, l2_gbs: float) -> dict:
+    """Memory roofs of one apply with one right-hand side (Sec. 6 roofline reasoning on this
+    device's measured bandwidths).  Level-blocked, from HBM: A once, X once and every power
+    written once; from L2: p passes over A and the two vectors of a power; the L2-blocked roof is
+    the larger of the two times.  The plain p x SpMV moves the L2 bytes through HBM.  With
+    binary32 accumulation a power also writes its binary32 copy (4 B a row) and reads the
+    previous one instead of the binary64 power."""
+    out_row = 8.0 + (4.0 if acc32 else 0.0)
+    hbm = a_bytes + 8.0 * n + p * out_row * n
+    l2 = p * (a_bytes + (4.0 if acc32 else 8.0) * n + out_row * n)
+    t_hbm, t_l2 = hbm / (hbm_gbs * 1e9), l2 / (l2_gbs * 1e9)
+    return {"hbm_bytes": hbm, "l2_bytes": l2, "plain_bytes": l2, "t_hbm_s": t_hbm, "t_l2_s": t_l2,
+            "l2_blocked_roof_ms": max(t_hbm, t_l2) * 1e3, "plain_hbm_roof_ms": l2 / (hbm_gbs * 1e9) * 1e3}
+
+
 def host_cores():
     """Logical CPUs of the host (os.cpu_count) and lscpu's model line, for the record."""
     model = None
@@ -1018,17 +1033,10 @@ def main():
     achieved = flops / (ms * 1e-3) / 1e12
     best_name = min(comps, key=comps.get)
     best_plain = comps[best_name]
-    # memory roofs of one apply (Sec. 6 roofline reasoning on this device's measured bandwidths):
-    # A once, X once and every power written once from / to HBM; p passes over A and the two
-    # vectors of a power from L2.  With binary32 accumulation a power also writes its binary32
-    # copy (4 B a row) and reads the previous one.
-    out_row = 8.0 + (4.0 if acc32 else 0.0)
-    hbm_bytes = a_bytes + 8.0 * A.n + p * out_row * A.n
-    l2_bytes = p * (a_bytes + (4.0 if acc32 else 8.0) * A.n + out_row * A.n)
-    bw_h, bw_l2 = roofs["hbm_load_gbs"] * 1e9, roofs["l2_load_gbs"] * 1e9
-    t_hbm, t_l2 = hbm_bytes / bw_h, l2_bytes / bw_l2
-    roof_blocked_ms = max(t_hbm, t_l2) * 1e3
-    plain_bytes = p * (a_bytes + (4.0 if acc32 else 8.0) * A.n + out_row * A.n)
+    mr = memory_roofs(a_bytes, A.n, p, acc32, roofs["hbm_load_gbs"], roofs["l2_load_gbs"])
+    hbm_bytes, l2_bytes, plain_bytes = mr["hbm_bytes"], mr["l2_bytes"], mr["plain_bytes"]
+    t_hbm, t_l2, roof_blocked_ms = mr["t_hbm_s"], mr["t_l2_s"], mr["l2_blocked_roof_ms"]
+    bw_h = roofs["hbm_load_gbs"] * 1e9
     peak_nominal = roofs["sms"] * DFMA_LANES_PER_CLK_PER_SM * 2 * mhz * 1e6 / 1e12  # TFLOP/s
     # DRAM bytes per launch from one ncu capture of this kernel source (null once it has changed)
     prof = measured_profile(args.side, "f32" if acc32 else "f64")
