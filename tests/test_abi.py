@@ -1,4 +1,5 @@
-"""The C-ABI library builds for sm_103a, loads, and exports every function include/mpk.h declares."""
+"""The C-ABI library builds for sm_103a, loads, and exports every function include/mpk.h declares;
+the binding's ctypes structs lay out exactly as the header's."""
 import os
 import re
 import subprocess
@@ -49,3 +50,47 @@ def test_status_strings_without_gpu(lib_path):
     lib = mpk.load()
     assert lib.mpk_status_string(0) == b"ok"
     assert lib.mpk_status_string(4) == b"device wait timed out"
+
+
+def _c_struct_fields(name: str):
+    """Field names, in order, of `typedef struct { ... } name;` in the header."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef\s+struct\s*\{([^{}]*)\}\s*" + name + r"\s*;", text).group(1)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        # "const int32_t *a, *b" -> a, b: the last identifier of each declarator
+        head, *rest = decl.split(",")
+        for d in [head] + rest:
+            names.append(re.findall(r"[A-Za-z_][A-Za-z0-9_]*", d)[-1])
+    return names
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    # the ctypes mirrors of the header's structs: same fields in the same order, and the offsets
+    # and sizes a C compiler gives them (a mismatch would pass wrong options without an error)
+    import ctypes
+    import paper_2405_12525_gb300 as mpk
+    structs = {"mpk_csr": mpk._Csr, "mpk_plan_opts": mpk._Opts, "mpk_plan_desc": mpk._Desc}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void) {"]
+    for cname, cls in structs.items():
+        assert _c_struct_fields(cname) == [f for f, _ in cls._fields_], cname
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname} {f} %zu %zu\\n", offsetof({cname}, {f}), sizeof((({cname} *)0)->{f}));')
+    lines += ["return 0;", "}"]
+    src, exe = tmp_path / "layout.c", tmp_path / "layout"
+    src.write_text("\n".join(lines))
+    subprocess.run(["gcc", "-std=c11", "-o", str(exe), str(src)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c = {}
+    for ln in filter(None, out):
+        parts = ln.split()
+        c[tuple(parts[:2])] = tuple(int(v) for v in parts[2:])
+    for cname, cls in structs.items():
+        assert c[(cname, "sizeof")] == (ctypes.sizeof(cls),), cname
+        for f, _ in cls._fields_:
+            field = getattr(cls, f)
+            assert c[(cname, f)] == (field.offset, field.size), (cname, f)
