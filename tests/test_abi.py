@@ -1,5 +1,6 @@
 """The C-ABI library builds for sm_103a, loads, and exports every function include/mpk.h declares;
-the binding's ctypes structs lay out exactly as the header's."""
+the binding's ctypes structs lay out exactly as the header's, and it declares every entry point
+with the header's argument and return types."""
 import os
 import re
 import subprocess
@@ -94,3 +95,41 @@ def test_binding_structs_match_the_header_layout(tmp_path):
         for f, _ in cls._fields_:
             field = getattr(cls, f)
             assert c[(cname, f)] == (field.offset, field.size), (cname, f)
+
+
+def _c_kind(decl: str) -> str:
+    """Kind of a C parameter or return type of the header: ptr, i32, i64, f64 or void."""
+    decl = decl.strip()
+    if "*" in decl or re.match(r"(const\s+)?mpk_stream\b", decl):
+        return "ptr"
+    t = re.findall(r"[A-Za-z_][A-Za-z0-9_]*", decl)
+    t = [w for w in t if w != "const"]
+    base = t[0]
+    return {"int32_t": "i32", "mpk_status": "i32", "int": "i32", "int64_t": "i64", "double": "f64",
+            "void": "void"}[base]
+
+
+def _ctypes_kind(t) -> str:
+    import ctypes
+    if t is None:
+        return "void"
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or hasattr(t, "_type_") and isinstance(t._type_, type):
+        return "ptr"  # POINTER(...) classes carry the pointee type in _type_
+    return {ctypes.c_int32: "i32", ctypes.c_int: "i32", ctypes.c_int64: "i64", ctypes.c_double: "f64"}[t]
+
+
+def test_binding_signatures_match_the_header_prototypes(lib_path):
+    # every entry point's argument and return kinds as the header declares them, so that no
+    # 32/64-bit integer, double or pointer is passed in the wrong register or width
+    import paper_2405_12525_gb300 as mpk
+    lib = mpk.load()
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    protos = re.findall(r"(mpk_status|int64_t|void|const\s+char\s*\*)\s*(mpk_[a-z0-9_]+)\s*\(([^)]*)\)\s*;", text)
+    assert {name for _, name, _ in protos} == set(_declared_functions())
+    for ret, name, params in protos:
+        f = getattr(lib, name)
+        params = params.strip()
+        want = [] if params in ("", "void") else [_c_kind(p) for p in params.split(",")]
+        assert f.argtypes is not None, f"{name}: argument types not set by the binding"
+        assert [_ctypes_kind(t) for t in f.argtypes] == want, name
+        assert _ctypes_kind(f.restype) == ("ptr" if "*" in ret else _c_kind(ret)), name
