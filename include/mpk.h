@@ -105,6 +105,8 @@ mpk_status mpk_levels_get(const mpk_levels *L, int32_t *n, int32_t *num_levels,
                           const int32_t **level_ptr_dev, const int32_t **perm_dev,
                           const int32_t **iperm_dev, const int32_t **level_of_dev);
 
+/* Frees a levels object (NULL: no-op).  Plans built from it keep their own copies of the
+ * permutation and stay valid. */
 void mpk_levels_destroy(mpk_levels *L);
 
 /* ---------------------------------------------------------------------------------------
@@ -240,6 +242,8 @@ mpk_status mpk_plan_describe(const mpk_plan_t *P, mpk_plan_desc *out);
 mpk_status mpk_plan_export_csr(const mpk_plan_t *P, int32_t *row_ptr, int32_t *col, double *val,
                                mpk_stream stream);
 
+/* Frees a plan and all device memory it holds (NULL: no-op).  Call it once the work queued
+ * on the plan has completed (after mpk_sync_status, or a synchronisation of its streams). */
 void mpk_plan_destroy(mpk_plan_t *P);
 
 /* ---------------------------------------------------------------------------------------

@@ -133,3 +133,19 @@ def test_binding_signatures_match_the_header_prototypes(lib_path):
         assert f.argtypes is not None, f"{name}: argument types not set by the binding"
         assert [_ctypes_kind(t) for t in f.argtypes] == want, name
         assert _ctypes_kind(f.restype) == ("ptr" if "*" in ret else _c_kind(ret)), name
+
+
+def test_readme_c_example_compiles_and_links(lib_path, tmp_path):
+    # the README's program that uses the C ABI without Python builds against the header and the
+    # library as shown there (it is not run: that needs a GPU)
+    readme = open(os.path.join(ROOT, "README.md")).read()
+    section = readme.split("## Use from C", 1)[1]
+    code = re.search(r"```c\n(.*?)```", section, flags=re.S).group(1)
+    src = tmp_path / "example.c"
+    src.write_text(code)
+    cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+    cmd = ["gcc", "-std=c11", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), "-I", os.path.join(cuda, "include"),
+           str(src), "-o", str(tmp_path / "example"), "-L", os.path.dirname(lib_path), "-lmpk",
+           "-L", os.path.join(cuda, "lib64"), "-lcudart"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
