@@ -137,6 +137,9 @@ class DlbMpk:
         self.torch = torch
         self.n, self.p_m, self.m = A.n, p_m, nrhs
         self.bounds = partition_rows(A.n, parts, A.row_ptr if balance == "nnz" else None)
+        empty = np.nonzero(np.diff(self.bounds) == 0)[0]
+        if empty.size:  # a process of Alg. 2 owns at least one row
+            raise ValueError(f"partition {int(empty[0])} of {parts} owns no row of the {A.n}: use fewer partitions")
         self.problems = [local_problem(A.row_ptr, A.col, A.val, int(self.bounds[i]), int(self.bounds[i + 1]), self.bounds)
                          for i in range(parts)]
         vt = MPK_F64 if value_type is None else value_type

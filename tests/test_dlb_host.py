@@ -37,6 +37,16 @@ def test_partition_rows_balance():
         dlb.partition_rows(10, 0)
 
 
+def test_partitions_without_rows_are_refused():
+    # more partitions than rows, or all entries in one row, leave a partition without rows; the
+    # emulation refuses that before any device work (no GPU is touched here)
+    from paper_2405_12525_gb300.dlb import DlbMpk
+    A = gen.laplacian_1d(3)
+    with pytest.raises(ValueError, match="owns no row"):
+        DlbMpk(A, 5, 2)
+    assert list(dlb.partition_rows(3, 5)) == [0, 1, 1, 2, 2, 3]
+
+
 def test_local_problem_reproduces_global_rows():
     A = gen.banded_random(2000, stream=32, per_row=7, band_frac=0.05)
     x = gen.vector(A.n, stream=33)[:, 0]
