@@ -2,7 +2,7 @@
 only while the kernel's sources hash to the recorded value, and only for its own accumulation
 and size; the algorithmic bytes and memory roofs of the line equal the byte counts of the
 level-blocked and plain MPK written out by hand; clock samples are parsed as nvidia-smi prints
-them."""
+them; the reference arm (the CPU oracle) prints its one line on rank 0 only."""
 import hashlib
 import importlib.util
 import json
@@ -122,3 +122,30 @@ def test_clock_summary_parses_samples_and_reasons(bench):
     clk.lines = []  # no nvidia-smi: no clock, the fallback maximum
     s = clk.summary()
     assert s["sm_mhz"] is None and s["samples"] == 0 and s["sm_max_mhz"] == bench.SM_MAX_MHZ_FALLBACK
+
+
+def _reference_run(env_extra):
+    import subprocess
+    env = dict(os.environ, **env_extra)
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--side", "16", "--steps", "3",
+           "--warmup", "3"]
+    return subprocess.run(cmd, capture_output=True, text=True, env=env, cwd=ROOT, timeout=600)
+
+
+def test_reference_arm_prints_one_line_on_rank_0_only():
+    # the reference arm times the CPU oracle: rank 0 prints one JSON line with the contract's
+    # keys; another rank of a multi-process launch exits 0 without work or output
+    r = _reference_run({"RANK": "0", "WORLD_SIZE": "1", "LOCAL_RANK": "0"})
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["unit"] == "Gflop/s" and d["higher_is_better"] is True
+    assert d["steps"] == 3 and d["value"] > 0 and d["config"]["n"] == 16 ** 3
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": "Gflop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    r = _reference_run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    assert r.returncode == 0 and r.stdout.strip() == "", r.stderr
